@@ -1,0 +1,207 @@
+/*
+ * qpe.h - C ABI of the GB300 (sm_103a) statevector emulator for the Quantum
+ * Phase Estimation circuit (QPE; Sec. 2 and Fig. 1 of "GPU benchmark through
+ * QPE emulator with cuQuantum for practical quantum applications").
+ *
+ * The circuit: Nmeas measurement qubits start in |0>, the Nmat-qubit target
+ * register holds psi. A Hadamard acts on every measurement qubit, measurement
+ * qubit k (k = 0 is the top wire of Fig. 1) controls U^(2^k) on the target
+ * register, QFT^-1 acts on the measurement register, and the measurement
+ * register is read out; the eigenphase phi of U (eigenvalue exp(2 pi i phi),
+ * Sec. 2) is estimated from the outcome distribution either by the most
+ * probable outcome or by the probability-weighted average (Sec. 4.2).
+ *
+ * Data layout (all device memory is caller-owned):
+ *   - d = 2^Nmat, N = 2^Nmeas.
+ *   - U: d x d complex128, row-major, interleaved (re, im) doubles.
+ *   - psi: d complex128.
+ *   - The state is an N x d row-major matrix S[m][t], flat index m*d + t
+ *     (measurement register = high bits); measurement qubit k is bit k of m.
+ *     Element type: complex128 for QPE_FP64 plans, complex64 otherwise.
+ *   - The histogram P[y], y in [0, N), is float64 in natural order of y.
+ *
+ * Conventions:
+ *   - QFT^-1 is F^dagger[y][m] = 2^(-n/2) exp(-2 pi i m y / N) including the
+ *     final swaps, so an eigenphase phi peaks at y = N phi.
+ *   - psi is not renormalised: sum_y P[y] = ||psi||^2.
+ *   - Every call returns a qpe_status; no C++ exception crosses the ABI. A
+ *     plan is not thread-safe; distinct plans are independent.
+ *   - The library never allocates device memory: qpe_plan reports the
+ *     workspace size, the caller allocates it and passes it to qpe_bind.
+ *     Host-side allocation happens only inside qpe_plan (the plan object) and
+ *     in qpe_state's host-output path (a temporary for the reordering).
+ *   - All device work is enqueued on the stream given to qpe_bind. Calls that
+ *     return data to host memory synchronise that stream.
+ */
+#ifndef QPE_H
+#define QPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qpe_plan_s* qpe_plan_t;
+
+typedef enum {
+  QPE_OK = 0,
+  QPE_ERR_ARG = 1,         /* null pointer, bad enum, argument out of range      */
+  QPE_ERR_SHAPE = 2,       /* nmat/nmeas/instance do not match the plan          */
+  QPE_ERR_WORKSPACE = 3,   /* workspace null, too small or not 256-byte aligned  */
+  QPE_ERR_UNSUPPORTED = 4, /* valid request this build does not implement        */
+  QPE_ERR_CUDA = 5,        /* a CUDA runtime call failed (see qpe_last_error)    */
+  QPE_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out                 */
+  QPE_ERR_NUMERIC = 7,     /* NaN/Inf detected in the histogram                  */
+  QPE_ERR_STATE = 8        /* call out of order (e.g. run before bind/load)      */
+} qpe_status;
+
+typedef enum {
+  QPE_FP64 = 0,       /* complex128 state, FP64 arithmetic everywhere           */
+  QPE_C64_FP32 = 1,   /* complex64 state, FP32 arithmetic for the controlled    */
+                      /* gates and QFT^-1; U^(2^k) squaring and the readout     */
+                      /* stay FP64                                              */
+  QPE_C64_BF16X3 = 2, /* reserved: split-BF16 tensor-core U-application         */
+  QPE_C64_FP16X2 = 3, /* reserved: split-FP16 tensor-core U-application         */
+  QPE_C64_TF32X3 = 4  /* reserved: split-TF32 tensor-core U-application         */
+} qpe_precision;
+
+/* Plan flags. */
+#define QPE_FLAG_GATE_SWEEP 0x1u /* schedule the controlled gates one per      */
+                                 /* measurement qubit over all rows whose bit  */
+                                 /* k is set (gate-faithful; d <= 64), instead */
+                                 /* of the default doubling schedule           */
+#define QPE_FLAG_GRAPH 0x2u      /* qpe_run captures its launches into a CUDA  */
+                                 /* graph on first use and replays it         */
+#define QPE_FLAG_TIMING 0x4u     /* record a CUDA event before each stage and  */
+                                 /* after the last one (read: qpe_stage_times) */
+
+typedef struct {
+  int32_t nmat;   /* target-register qubits, 1..12 (d = 2^nmat)                 */
+  int32_t nmeas;  /* measurement qubits, 1..30 (N = 2^nmeas)                    */
+  int32_t prec;   /* a qpe_precision                                           */
+  uint32_t flags; /* QPE_FLAG_*                                                */
+} qpe_plan_desc;
+
+/* Stages of one run, in order (Fig. 1 left to right). */
+typedef enum {
+  QPE_STAGE_POWERS = 1, /* P_k = U^(2^k), k < Nmeas, by FP64 repeated squaring  */
+  QPE_STAGE_SWEEP = 2,  /* Hadamard layer + all controlled-U^(2^k) gates: row m */
+                        /* of the state becomes 2^(-n/2) U^m psi               */
+  QPE_STAGE_FFT = 3,    /* QFT^-1 on the measurement register                   */
+  QPE_STAGE_REDUCE = 4  /* P[y] = sum_t |X[y][t]|^2, argmax, weighted mean      */
+} qpe_stage;
+
+/* Introspection keys for qpe_query. */
+typedef enum {
+  QPE_INFO_WORKSPACE_BYTES = 1,
+  QPE_INFO_STATE_BYTES = 2,     /* bytes of one instance's state                */
+  QPE_INFO_FFT_PASSES = 3,      /* passes over the state the QFT^-1 takes      */
+  QPE_INFO_LAST_LAUNCHES = 4,   /* kernels enqueued by the last qpe_run*       */
+  QPE_INFO_INSTANCES = 5
+} qpe_info;
+
+/*
+ * qpe_plan: validate a problem and size its workspace. Host only; touches no
+ * GPU. On success *out is a new plan and *workspace_bytes the device bytes
+ * qpe_bind needs. Errors: QPE_ERR_ARG for null pointers or nmat/nmeas/prec
+ * out of range; QPE_ERR_UNSUPPORTED for combinations not built (reserved
+ * precisions; QPE_FLAG_GATE_SWEEP with nmat > 6).
+ */
+qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan_t* out);
+
+/*
+ * qpe_bind: attach caller-owned device memory and a CUDA stream (a
+ * cudaStream_t, or NULL for the legacy default stream) to a plan. The
+ * workspace must stay allocated until qpe_destroy or the next qpe_bind, be
+ * 256-byte aligned and hold at least the size qpe_plan reported
+ * (QPE_ERR_WORKSPACE otherwise). Builds the plan's twiddle tables on the
+ * stream. QPE_FLAG_GRAPH plans need a non-NULL stream (QPE_ERR_ARG).
+ */
+qpe_status qpe_bind(qpe_plan_t plan, void* d_workspace, size_t bytes, void* cuda_stream);
+
+/*
+ * qpe_load: copy U (d x d complex128 row-major) and psi (d complex128) into
+ * the workspace (the paper's host-to-device transfer, Sec. 4.3). ptr_is_device
+ * = 0: host pointers; 1: device pointers. The caller keeps ownership of its
+ * buffers. nmat/nmeas must equal the plan's (QPE_ERR_SHAPE); instance must be
+ * 0 for single-problem plans.
+ */
+qpe_status qpe_load(qpe_plan_t plan, int32_t instance, const void* U, const void* psi,
+                    int32_t nmat, int32_t nmeas, int32_t ptr_is_device);
+
+/*
+ * qpe_run: enqueue one whole run (all four stages) on the bound stream.
+ * Asynchronous: no host synchronisation and no allocation. Requires bind and
+ * load (QPE_ERR_STATE).
+ */
+qpe_status qpe_run(qpe_plan_t plan);
+
+/*
+ * qpe_run_stages: enqueue stages first..last (qpe_stage values) only. Used to
+ * check one step at a time: e.g. (SWEEP, SWEEP) after qpe_load_state-free
+ * runs, or (FFT, REDUCE) after qpe_load_state. The POWERS stage must have run
+ * (in this or an earlier call since the last qpe_load) before SWEEP.
+ */
+qpe_status qpe_run_stages(qpe_plan_t plan, int32_t first, int32_t last);
+
+/*
+ * qpe_probs: read the measurement histogram and the readout. probs (N
+ * doubles, natural order of y) may be NULL to skip it; argmax is the most
+ * probable outcome (lowest y on exact ties), phase_argmax = argmax / N, and
+ * phase_mean = sum_y P[y] y / N (the weighted average of Sec. 4.2). Scalar
+ * outputs may be NULL. ptr_is_device applies to probs only; the scalars are
+ * always host pointers. Synchronises the stream and returns QPE_ERR_NUMERIC
+ * if the device flagged a non-finite histogram.
+ */
+qpe_status qpe_probs(qpe_plan_t plan, int32_t instance, double* probs, int64_t* argmax,
+                     double* phase_argmax, double* phase_mean, int32_t ptr_is_device);
+
+/*
+ * qpe_state: copy the current state (N x d, element type of the plan) in
+ * natural row order: after SWEEP, row m = 2^(-n/2) U^m psi; after FFT, row y
+ * is the final statevector (the paper's output file, Sec. 3). Host output
+ * synchronises and reorders on the host; device output is reordered by a
+ * kernel on the stream.
+ */
+qpe_status qpe_state(qpe_plan_t plan, int32_t instance, void* out, int32_t ptr_is_device);
+
+/*
+ * qpe_load_state: overwrite the state with N x d elements (plan element type,
+ * natural order); the next stage to run on it is FFT. For step-by-step checks.
+ */
+qpe_status qpe_load_state(qpe_plan_t plan, int32_t instance, const void* in, int32_t ptr_is_device);
+
+/*
+ * qpe_powers: copy P_k = U^(2^k) (d x d complex128) after the POWERS stage.
+ */
+qpe_status qpe_powers(qpe_plan_t plan, int32_t instance, int32_t k, void* out, int32_t ptr_is_device);
+
+/* qpe_query: integer facts about a plan (qpe_info keys); -1 on a bad key. */
+int64_t qpe_query(qpe_plan_t plan, int32_t key);
+
+/*
+ * qpe_stage_times: milliseconds each stage of the last qpe_run took on the
+ * bound stream (ms[0..3] = POWERS, SWEEP, FFT, REDUCE), from CUDA events the
+ * library records around its own launches. Needs QPE_FLAG_TIMING and a
+ * single-instance plan (QPE_ERR_STATE otherwise). Synchronises the stream.
+ */
+qpe_status qpe_stage_times(qpe_plan_t plan, double* ms);
+
+/* qpe_sync: wait for the bound stream and report device-side error flags. */
+qpe_status qpe_sync(qpe_plan_t plan);
+
+/* qpe_destroy: free the host-side plan (and its CUDA graph, if any). Does not
+ * touch the caller's workspace. NULL is accepted. */
+qpe_status qpe_destroy(qpe_plan_t plan);
+
+const char* qpe_status_string(qpe_status s);
+/* Last error message recorded on the plan ("" if none; static text for NULL). */
+const char* qpe_last_error(qpe_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QPE_H */

@@ -1,0 +1,134 @@
+// Internal declarations of the QPE emulator: complex helpers, workspace
+// layout, and the kernel launchers the C ABI calls. Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qpe.h"
+
+namespace qpe {
+
+// ---------------------------------------------------------------- complex
+template <typename C> struct real_of;
+template <> struct real_of<float2> { using type = float; };
+template <> struct real_of<double2> { using type = double; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C>
+__host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C>
+__host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C>
+__host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+template <typename C>
+__host__ __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename C, typename R>
+__host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+
+__device__ __forceinline__ float2 to_c(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 to_c(double2 v, double2*) { return v; }
+
+// ------------------------------------------------------------ fft plan
+constexpr int kMaxPasses = 8;
+
+struct FftPass {
+  int logr;      // this pass's DFT length R = 2^logr
+  int64_t B;     // independent blocks (N / (R * L))
+  int64_t L;     // row stride between the R elements of one DFT
+  int64_t Q;     // L * d: contiguous elements per (block, digit)
+  int64_t W;     // elements of Q each CTA takes
+};
+
+struct FftPlan {
+  int passes = 0;
+  FftPass p[kMaxPasses];
+  int logr_list[kMaxPasses];  // digit widths from the top of m downwards
+};
+
+// Device-side scalars of one instance (readout + error word).
+struct Scalars {
+  int64_t argmax;
+  double phase_argmax;
+  double phase_mean;
+  double total;      // sum_y P[y]
+  int32_t err;       // qpe_status raised on the device, 0 if none
+  int32_t pad;
+};
+
+// Per-block partial of the readout reduction.
+struct Partial {
+  double best;
+  int64_t besty;
+  double wsum;   // sum P[y] * y
+  double psum;   // sum P[y]
+};
+
+constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
+
+// One problem instance inside a plan: its shape and workspace offsets.
+struct Instance {
+  int nmat, nmeas;
+  int64_t d, N;
+  int htw;              // split point of the two-level twiddle table
+  size_t off_pow64;     // nmeas x d x d complex128
+  size_t off_pow32;     // nmeas x d x d complex64 (complex64 plans)
+  size_t off_psi;       // d complex128
+  size_t off_state;     // N x d elements
+  size_t off_hist;      // N doubles
+  size_t off_tw_lo64, off_tw_hi64, off_tw_lo32, off_tw_hi32;
+  size_t off_partials;  // kReduceBlocks Partials
+  size_t off_scalars;   // Scalars
+  size_t state_bytes;
+  FftPlan fft;
+  bool loaded = false;
+  bool powers_done = false;
+  int state_stage = 0;  // last stage whose output the state buffer holds
+};
+
+}  // namespace qpe
+
+struct qpe_plan_s {
+  int prec;
+  uint32_t flags;
+  std::vector<qpe::Instance> inst;
+  size_t ws_bytes = 0;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  int64_t last_launches = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // QPE_FLAG_TIMING
+  bool timed_run = false;  // the last enqueue recorded all five events
+  std::string last_error;
+};
+
+namespace qpe {
+
+// Launchers (qpe_kernels.cu). Each returns the number of kernels enqueued or
+// -1 on a launch error (cudaGetLastError is left for the caller to read).
+int launch_twiddles(const Instance& in, char* ws, cudaStream_t s);
+int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s);
+template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s);
+template <typename C> int launch_fft(const Instance& in, char* ws, cudaStream_t s);
+template <typename C> int launch_reduce(const Instance& in, char* ws, cudaStream_t s);
+template <typename C> int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s);
+
+// Host helpers shared with the ABI layer.
+int64_t fft_position_to_y(const FftPlan& f, int nmeas, int64_t p);
+FftPlan make_fft_plan(int nmeas, int64_t d, size_t esize);
+
+}  // namespace qpe

@@ -1,0 +1,653 @@
+// CUDA kernels of the QPE emulator (sm_103a).
+//
+// Stages (Fig. 1, left to right):
+//   powers   P_k = U^(2^k) by FP64 repeated squaring (P_{k+1} = P_k P_k).
+//   sweep    Hadamard layer + controlled-U^(2^k): row m of the N x d state
+//            becomes 2^(-n/2) U^m psi. Two schedules:
+//              doubling  S[m + 2^j] = P_j S[m] for m < 2^j, j = 0..n-1
+//                        (every row receives exactly the controlled gates of
+//                        its set bits, lowest bit first, as in the circuit;
+//                        each distinct row value is computed once);
+//              gate      for k = 0..n-1, every row with bit k set is
+//                        replaced by P_k times itself (one pass per gate).
+//   fft      QFT^-1 on the measurement register = a batched DFT along m with
+//            kernel exp(-2 pi i m y / N), decimation in frequency, in place,
+//            in passes of up to 2^9 points staged in shared memory.
+//   reduce   P[y] = sum_t |X[y][t]|^2 with digit-reversal undone, plus the
+//            readout: argmax (lowest y on ties) and sum_y P[y] y / N.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "qpe_internal.cuh"
+
+namespace qpe {
+
+namespace {
+
+__device__ __forceinline__ double2 ld(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld(const float2* p) { return __ldg(p); }
+
+// omega_N^e = exp(-2 pi i e / N) from the two-level table: e = hi * 2^h + lo.
+template <typename C>
+__device__ __forceinline__ C twiddle(const C* lo, const C* hi, int h, int64_t e) {
+  const int64_t mask = (int64_t(1) << h) - 1;
+  return cmul(ld(lo + (e & mask)), ld(hi + (e >> h)));
+}
+
+// ------------------------------------------------------------- twiddles
+__global__ void twiddle_tables_kernel(double2* lo64, double2* hi64, float2* lo32, float2* hi32,
+                                      int n, int h) {
+  const int64_t nlo = int64_t(1) << h;
+  const int64_t nhi = int64_t(1) << (n - h);
+  const double N = ldexp(1.0, n);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlo + nhi;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i < nlo ? i : ((i - nlo) << h);
+    double s, c;
+    sincospi(-2.0 * (double)e / N, &s, &c);  // exact argument: e < N = 2^n
+    const double2 v = make_double2(c, s);
+    const float2 f = make_float2((float)c, (float)s);
+    if (i < nlo) {
+      lo64[i] = v;
+      lo32[i] = f;
+    } else {
+      hi64[i - nlo] = v;
+      hi32[i - nlo] = f;
+    }
+  }
+}
+
+// --------------------------------------------------------------- powers
+// C = A * A for a d x d complex128 matrix, d <= 256. Each CTA owns a TS x TS
+// output tile; its KS thread layers split the inner index and are summed in
+// shared memory, so even d = 64 spreads over hundreds of CTAs.
+template <int TS, int KS>
+__global__ void __launch_bounds__(TS * TS * KS) square_small_kernel(const double2* __restrict__ A,
+                                                                    double2* __restrict__ C, int d) {
+  __shared__ double2 red[KS][TS][TS];
+  const int tx = threadIdx.x % TS;
+  const int ty = (threadIdx.x / TS) % TS;
+  const int tz = threadIdx.x / (TS * TS);
+  const int row = blockIdx.y * TS + ty;
+  const int col = blockIdx.x * TS + tx;
+  const int kper = d / KS;
+  double2 acc = make_double2(0.0, 0.0);
+  const double2* arow = A + (int64_t)row * d;
+  for (int k = tz * kper; k < (tz + 1) * kper; ++k) cfma(acc, ld(arow + k), ld(A + (int64_t)k * d + col));
+  red[tz][ty][tx] = acc;
+  __syncthreads();
+  if (tz == 0) {
+    double2 s = red[0][ty][tx];
+    for (int z = 1; z < KS; ++z) s = cadd(s, red[z][ty][tx]);
+    C[(int64_t)row * d + col] = s;
+  }
+}
+
+// C = A * A for d >= 512: 32 x 32 output tiles, 16-wide k slabs in shared
+// memory, 2 x 2 outputs per thread.
+__global__ void __launch_bounds__(256) square_tiled_kernel(const double2* __restrict__ A,
+                                                           double2* __restrict__ C, int d) {
+  constexpr int T = 32, BK = 16;
+  __shared__ double2 As[BK][T + 1];
+  __shared__ double2 Bs[BK][T + 1];
+  const int tid = threadIdx.x;
+  const int tc = tid % 16, tr = tid / 16;
+  const int r0 = blockIdx.y * T, c0 = blockIdx.x * T;
+  double2 acc[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < d; k0 += BK) {
+    for (int idx = tid; idx < T * BK; idx += 256) {
+      const int r = idx / BK, kk = idx % BK;
+      As[kk][r] = ld(A + (int64_t)(r0 + r) * d + k0 + kk);
+      const int kb = idx / T, cb = idx % T;
+      Bs[kb][cb] = ld(A + (int64_t)(k0 + kb) * d + c0 + cb);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const double2 a0 = As[kk][tr], a1 = As[kk][tr + 16];
+      const double2 b0 = Bs[kk][tc], b1 = Bs[kk][tc + 16];
+      cfma(acc[0][0], a0, b0);
+      cfma(acc[0][1], a0, b1);
+      cfma(acc[1][0], a1, b0);
+      cfma(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) C[(int64_t)(r0 + tr + 16 * i) * d + c0 + tc + 16 * j] = acc[i][j];
+}
+
+__global__ void convert_c128_to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out,
+                                           int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// ---------------------------------------------------------------- sweep
+// rows [0, rows) of S = scale * psi
+template <typename C>
+__global__ void init_rows_kernel(C* __restrict__ S, const double2* __restrict__ psi, int64_t rows, int logd,
+                                 double scale) {
+  const int64_t total = rows << logd;
+  const int64_t dmask = (int64_t(1) << logd) - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = psi[i & dmask];
+    S[i] = to_c(make_double2(v.x * scale, v.y * scale), (C*)nullptr);
+  }
+}
+
+// Logical row r of a controlled-gate GEMM -> physical rows read and written.
+struct DoublingRows {  // level j: read row r, write row r + 2^j
+  int64_t half;
+  __device__ __forceinline__ int64_t in(int64_t r) const { return r; }
+  __device__ __forceinline__ int64_t out(int64_t r) const { return r + half; }
+};
+struct GateRows {  // gate k: the r-th row with bit k set, in place
+  int k;
+  __device__ __forceinline__ int64_t in(int64_t r) const {
+    const int64_t low = r & ((int64_t(1) << k) - 1);
+    return ((r >> k) << (k + 1)) | (int64_t(1) << k) | low;
+  }
+  __device__ __forceinline__ int64_t out(int64_t r) const { return in(r); }
+};
+
+// out_row(r)[i] = sum_c P[i][c] * in_row(r)[c] for logical rows r < M:
+// a complex GEMM (M x d) * P^T with BM x BN tiles, BK-deep k slabs staged in
+// shared memory and TM x TN outputs per thread. When BN == d one CTA owns
+// whole rows, so in-place updates (GateRows) are safe: every read of a row
+// happens before the CTA's epilogue writes it.
+template <typename C, int BM, int BN, int BK, int TM, int TN, typename Rows>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    rows_times_pt_kernel(C* __restrict__ S, const C* __restrict__ P, int64_t M, int d, Rows rows) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int TCOLS = BN / TN;
+  __shared__ C As[BK][BM + 1];
+  __shared__ C Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tc = tid % TCOLS, tr = tid / TCOLS;
+  const int64_t r0 = (int64_t)blockIdx.x * BM;
+  const int c0 = blockIdx.y * BN;
+  C acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = mk((typename real_of<C>::type)0, (typename real_of<C>::type)0);
+
+  for (int k0 = 0; k0 < d; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      const int r = idx / BK, kk = idx % BK;
+      const int64_t lr = r0 + r;
+      C v = mk((typename real_of<C>::type)0, (typename real_of<C>::type)0);
+      if (lr < M) v = S[rows.in(lr) * d + k0 + kk];
+      As[kk][r] = v;
+    }
+    for (int idx = tid; idx < BN * BK; idx += NT) {
+      const int c = idx / BK, kk = idx % BK;
+      Bs[kk][c] = ld(P + (int64_t)(c0 + c) * d + k0 + kk);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tr + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tc + j * TCOLS];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t lr = r0 + tr + i * (BM / TM);
+    if (lr >= M) continue;
+    C* orow = S + rows.out(lr) * d + c0;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) orow[tc + j * TCOLS] = acc[i][j];
+  }
+}
+
+// ------------------------------------------------------------------ fft
+// One decimation-in-frequency pass over the middle axis of X viewed as
+// [B][R][Q] (Q = L * d contiguous elements): for each block and each of the Q
+// columns, a length-R DFT over the middle axis (kernel omega_R^(a y)), then
+// the twiddle omega_(R L)^(b y) with b = column / d the row offset inside the
+// block, stored in place at digit y. Each CTA stages an R x W slab in shared
+// memory and runs log2(R) radix-2 stages on it.
+struct FftArgs {
+  int logr;
+  int logw;    // W = 2^logw columns per CTA
+  int logq;    // Q = 2^logq
+  int logd;
+  int n;       // log2 N
+  int htw;
+  int logb;    // B = 2^logb blocks
+  int last;    // 1: no inter-pass twiddle
+  double scale;
+};
+
+__device__ __forceinline__ int bitrev(int x, int bits) { return bits ? (__brev(x) >> (32 - bits)) : 0; }
+
+template <typename C>
+__global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const C* __restrict__ tw_lo,
+                                                       const C* __restrict__ tw_hi, FftArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tile = reinterpret_cast<C*>(smem_raw);
+  using R_t = typename real_of<C>::type;
+  const int R = 1 << a.logr;
+  const int W = 1 << a.logw;
+  const int64_t slices_log = a.logq - a.logw;
+  const int64_t bid = blockIdx.x;
+  const int64_t blk = bid >> slices_log;
+  const int64_t qs = bid & ((int64_t(1) << slices_log) - 1);
+  C* base = X + (blk << (a.logr + a.logq)) + (qs << a.logw);
+  const int RW = R * W;
+  for (int idx = threadIdx.x; idx < RW; idx += blockDim.x) {
+    const int r = idx >> a.logw, w = idx & (W - 1);
+    tile[idx] = base[((int64_t)r << a.logq) + w];
+  }
+  __syncthreads();
+  for (int s = 0; s < a.logr; ++s) {
+    const int logh = a.logr - s - 1;
+    const int h = 1 << logh;
+    const int tshift = a.n - logh - 1;  // omega_(2h)^pos = omega_N^(pos << (n - log2(2h)))
+    for (int idx = threadIdx.x; idx < (RW >> 1); idx += blockDim.x) {
+      const int p = idx >> a.logw, w = idx & (W - 1);
+      const int grp = p >> logh, pos = p & (h - 1);
+      const int i0 = ((grp << (logh + 1)) + pos) * W + w;
+      const int i1 = i0 + h * W;
+      const C x0 = tile[i0], x1 = tile[i1];
+      tile[i0] = cadd(x0, x1);
+      const C dlt = csub(x0, x1);
+      tile[i1] = pos ? cmul(dlt, twiddle(tw_lo, tw_hi, a.htw, (int64_t)pos << tshift)) : dlt;
+    }
+    __syncthreads();
+  }
+  const int64_t rl_mask = (int64_t(1) << (a.logr + a.logq - a.logd)) - 1;  // R*L - 1
+  for (int idx = threadIdx.x; idx < RW; idx += blockDim.x) {
+    const int i = idx >> a.logw, w = idx & (W - 1);
+    const int ya = bitrev(i, a.logr);
+    C v = tile[idx];
+    if (!a.last) {
+      const int64_t q = (qs << a.logw) + w;
+      const int64_t b = q >> a.logd;
+      const int64_t e = ((b * ya) & rl_mask) << a.logb;  // omega_(RL)^(b ya) = omega_N^(b ya B)
+      if (e) v = cmul(v, twiddle(tw_lo, tw_hi, a.htw, e));
+    }
+    if (a.scale != 1.0) v = cscale(v, (R_t)a.scale);
+    base[((int64_t)ya << a.logq) + w] = v;
+  }
+}
+
+// --------------------------------------------------------------- reduce
+struct Digits {
+  int count;
+  int logr[kMaxPasses];
+};
+
+// Position p of the in-place DIF output -> outcome y: the pass that ran
+// first (top bits of p) produced the least significant digit of y.
+__device__ __forceinline__ int64_t pos_to_y(const Digits& g, int n, int64_t p) {
+  int64_t y = 0;
+  int rem = n, sh = 0;
+  for (int i = 0; i < g.count; ++i) {
+    rem -= g.logr[i];
+    const int64_t dig = (p >> rem) & ((int64_t(1) << g.logr[i]) - 1);
+    y |= dig << sh;
+    sh += g.logr[i];
+  }
+  return y;
+}
+
+__device__ __forceinline__ int64_t y_to_pos(const Digits& g, int n, int64_t y) {
+  int64_t p = 0;
+  int rem = n, sh = 0;
+  for (int i = 0; i < g.count; ++i) {
+    rem -= g.logr[i];
+    const int64_t dig = (y >> sh) & ((int64_t(1) << g.logr[i]) - 1);
+    p |= dig << rem;
+    sh += g.logr[i];
+  }
+  return p;
+}
+
+__device__ __forceinline__ void better(double& best, int64_t& by, double v, int64_t y) {
+  if (v > best || (v == best && y < by) || (best != best)) {
+    best = v;
+    by = y;
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, double* __restrict__ hist,
+                                                     Partial* __restrict__ parts, int64_t N, int logd, int n,
+                                                     Digits g, double scale) {
+  const int d = 1 << logd;
+  const int lpr = d < 32 ? d : 32;  // lanes per row
+  const int rpw = 32 / lpr;         // rows per warp step
+  const int per = d / lpr;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + warp;
+  const int64_t tw = (int64_t)gridDim.x * 8;
+  double best = -1.0, wsum = 0.0, psum = 0.0;
+  int64_t by = INT64_MAX;
+  for (int64_t p0 = gw * rpw; p0 < N; p0 += tw * rpw) {
+    const int64_t p = p0 + lane / lpr;
+    const int sub = lane % lpr;
+    double acc = 0.0;
+    if (p < N) {
+      const C* row = X + (p << logd);
+      for (int k = 0; k < per; ++k) {
+        const C v = row[sub + k * lpr];
+        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      }
+    }
+    for (int off = lpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (sub == 0 && p < N) {
+      const double v = acc * scale;
+      const int64_t y = pos_to_y(g, n, p);
+      hist[y] = v;
+      better(best, by, v, y);
+      wsum += v * (double)y;
+      psum += v;
+    }
+  }
+  // warp then block reduction (fixed order: deterministic)
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int64_t oy = __shfl_xor_sync(0xffffffffu, by, off);
+    better(best, by, ob, oy);
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+    psum += __shfl_xor_sync(0xffffffffu, psum, off);
+  }
+  __shared__ Partial sp[8];
+  if (lane == 0) sp[warp] = Partial{best, by, wsum, psum};
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial r = sp[0];
+    for (int w = 1; w < 8; ++w) {
+      better(r.best, r.besty, sp[w].best, sp[w].besty);
+      r.wsum += sp[w].wsum;
+      r.psum += sp[w].psum;
+    }
+    parts[blockIdx.x] = r;
+  }
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict__ parts, int count,
+                                                       Scalars* __restrict__ out, int n) {
+  __shared__ Partial sp[256];
+  Partial r{-1.0, INT64_MAX, 0.0, 0.0};
+  for (int i = threadIdx.x; i < count; i += 256) {
+    better(r.best, r.besty, parts[i].best, parts[i].besty);
+    r.wsum += parts[i].wsum;
+    r.psum += parts[i].psum;
+  }
+  sp[threadIdx.x] = r;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      Partial o = sp[threadIdx.x + s];
+      Partial& m = sp[threadIdx.x];
+      better(m.best, m.besty, o.best, o.besty);
+      m.wsum += o.wsum;
+      m.psum += o.psum;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double N = ldexp(1.0, n);
+    Partial m = sp[0];
+    Scalars s;
+    s.argmax = m.besty;
+    s.phase_argmax = (double)m.besty / N;
+    s.phase_mean = m.wsum / N;
+    s.total = m.psum;
+    s.err = isfinite(m.psum) && isfinite(m.wsum) && isfinite(m.best) ? 0 : (int)QPE_ERR_NUMERIC;
+    s.pad = 0;
+    *out = s;
+  }
+}
+
+template <typename C>
+__global__ void unpermute_kernel(const C* __restrict__ X, C* __restrict__ out, int64_t N, int logd, int n,
+                                 Digits g) {
+  const int64_t total = N << logd;
+  const int64_t dmask = (int64_t(1) << logd) - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i >> logd;
+    out[i] = X[(y_to_pos(g, n, y) << logd) | (i & dmask)];
+  }
+}
+
+inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+inline int ilog2(int64_t v) {
+  int r = 0;
+  while ((int64_t(1) << r) < v) ++r;
+  return r;
+}
+
+template <typename C>
+C* at(char* ws, size_t off) {
+  return reinterpret_cast<C*>(ws + off);
+}
+
+Digits digits_of(const FftPlan& f) {
+  Digits g;
+  g.count = f.passes;
+  for (int i = 0; i < kMaxPasses; ++i) g.logr[i] = i < f.passes ? f.logr_list[i] : 0;
+  return g;
+}
+
+}  // namespace
+
+// ============================================================ launchers
+int launch_twiddles(const Instance& in, char* ws, cudaStream_t s) {
+  const int64_t total = (int64_t(1) << in.htw) + (int64_t(1) << (in.nmeas - in.htw));
+  twiddle_tables_kernel<<<grid_for(total, 256), 256, 0, s>>>(
+      at<double2>(ws, in.off_tw_lo64), at<double2>(ws, in.off_tw_hi64), at<float2>(ws, in.off_tw_lo32),
+      at<float2>(ws, in.off_tw_hi32), in.nmeas, in.htw);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+static int launch_square(const double2* A, double2* C, int d, cudaStream_t s) {
+  switch (d) {
+    case 2: square_small_kernel<2, 2><<<dim3(1, 1), 8, 0, s>>>(A, C, d); break;
+    case 4: square_small_kernel<4, 4><<<dim3(1, 1), 64, 0, s>>>(A, C, d); break;
+    case 8: square_small_kernel<4, 8><<<dim3(2, 2), 128, 0, s>>>(A, C, d); break;
+    case 16: square_small_kernel<4, 16><<<dim3(4, 4), 256, 0, s>>>(A, C, d); break;
+    case 32: square_small_kernel<4, 16><<<dim3(8, 8), 256, 0, s>>>(A, C, d); break;
+    case 64: square_small_kernel<4, 16><<<dim3(16, 16), 256, 0, s>>>(A, C, d); break;
+    case 128: square_small_kernel<8, 4><<<dim3(16, 16), 256, 0, s>>>(A, C, d); break;
+    case 256: square_small_kernel<8, 4><<<dim3(32, 32), 256, 0, s>>>(A, C, d); break;
+    default: square_tiled_kernel<<<dim3(d / 32, d / 32), 256, 0, s>>>(A, C, d); break;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s) {
+  const int64_t dd = in.d * in.d;
+  double2* P = at<double2>(ws, in.off_pow64);
+  int launches = 0;
+  for (int k = 1; k < in.nmeas; ++k) {
+    if (launch_square(P + (k - 1) * dd, P + k * dd, (int)in.d, s) < 0) return -1;
+    ++launches;
+  }
+  if (want_c64) {
+    const int64_t count = dd * in.nmeas;
+    convert_c128_to_c64_kernel<<<grid_for(count, 256), 256, 0, s>>>(P, at<float2>(ws, in.off_pow32), count);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    ++launches;
+  }
+  return launches;
+}
+
+template <typename C, typename Rows>
+static int launch_rows_times_pt(C* S, const C* P, int64_t M, int d, Rows rows, cudaStream_t s) {
+  if (M <= 0) return 0;
+#define QPE_GEMM(BM, BN, BK, TM, TN)                                                          \
+  do {                                                                                        \
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)(d / BN));                              \
+    rows_times_pt_kernel<C, BM, BN, BK, TM, TN, Rows><<<grid, (BM / TM) * (BN / TN), 0, s>>>( \
+        S, P, M, d, rows);                                                                    \
+  } while (0)
+  switch (d) {
+    case 2: QPE_GEMM(256, 2, 2, 2, 1); break;
+    case 4: QPE_GEMM(256, 4, 4, 4, 1); break;
+    case 8: QPE_GEMM(256, 8, 8, 4, 2); break;
+    case 16: QPE_GEMM(256, 16, 8, 4, 4); break;
+    case 32: QPE_GEMM(128, 32, 8, 4, 4); break;
+    default: QPE_GEMM(64, 64, 8, 4, 4); break;
+  }
+#undef QPE_GEMM
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <typename C>
+int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s) {
+  C* S = at<C>(ws, in.off_state);
+  const C* P = (sizeof(C) == 16) ? at<C>(ws, in.off_pow64) : at<C>(ws, in.off_pow32);
+  const int64_t dd = in.d * in.d;
+  const int logd = in.nmat;
+  const double scale = 1.0 / sqrt(ldexp(1.0, in.nmeas));  // Hadamard layer: 2^(-n/2)
+  int launches = 0;
+  const int64_t init_rows = gate_mode ? in.N : 1;
+  init_rows_kernel<C><<<grid_for(init_rows << logd, 256), 256, 0, s>>>(S, at<double2>(ws, in.off_psi), init_rows,
+                                                                        logd, scale);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  ++launches;
+  for (int j = 0; j < in.nmeas; ++j) {
+    int r;
+    if (gate_mode)
+      r = launch_rows_times_pt<C>(S, P + j * dd, in.N / 2, (int)in.d, GateRows{j}, s);
+    else
+      r = launch_rows_times_pt<C>(S, P + j * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j}, s);
+    if (r < 0) return -1;
+    launches += r;
+  }
+  return launches;
+}
+
+FftPlan make_fft_plan(int nmeas, int64_t d, size_t esize) {
+  FftPlan f;
+  const int logd = ilog2(d);
+  const int logwmax = ilog2((int64_t)(128 / esize));  // 128-byte column slabs
+  const int max_bits = 9;                            // R * W * esize <= 64 KiB
+  const int passes = (nmeas + max_bits - 1) / max_bits;
+  f.passes = passes;
+  int used = 0;
+  for (int i = 0; i < passes; ++i) {
+    const int r = nmeas / passes + (i < nmeas % passes ? 1 : 0);
+    FftPass& p = f.p[i];
+    p.logr = r;
+    p.B = int64_t(1) << used;
+    used += r;
+    p.L = int64_t(1) << (nmeas - used);
+    p.Q = p.L * d;
+    const int logq = ilog2(p.Q);
+    const int logw = logq < logwmax ? logq : logwmax;
+    p.W = int64_t(1) << logw;
+    f.logr_list[i] = r;
+    (void)logd;
+  }
+  return f;
+}
+
+int64_t fft_position_to_y(const FftPlan& f, int nmeas, int64_t p) {
+  int64_t y = 0;
+  int rem = nmeas, sh = 0;
+  for (int i = 0; i < f.passes; ++i) {
+    rem -= f.logr_list[i];
+    const int64_t dig = (p >> rem) & ((int64_t(1) << f.logr_list[i]) - 1);
+    y |= dig << sh;
+    sh += f.logr_list[i];
+  }
+  return y;
+}
+
+template <typename C>
+int launch_fft(const Instance& in, char* ws, cudaStream_t s) {
+  C* X = at<C>(ws, in.off_state);
+  const C* lo = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_lo64) : at<C>(ws, in.off_tw_lo32);
+  const C* hi = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_hi64) : at<C>(ws, in.off_tw_hi32);
+  const double final_scale = 1.0 / sqrt(ldexp(1.0, in.nmeas));  // QFT^-1 normalisation 2^(-n/2)
+  int launches = 0;
+  for (int i = 0; i < in.fft.passes; ++i) {
+    const FftPass& p = in.fft.p[i];
+    FftArgs a;
+    a.logr = p.logr;
+    a.logw = ilog2(p.W);
+    a.logq = ilog2(p.Q);
+    a.logd = in.nmat;
+    a.n = in.nmeas;
+    a.htw = in.htw;
+    a.logb = ilog2(p.B);
+    a.last = (i == in.fft.passes - 1);
+    a.scale = a.last ? final_scale : 1.0;
+    const int64_t blocks = p.B * (p.Q / p.W);
+    const size_t smem = (size_t)(int64_t(1) << p.logr) * p.W * sizeof(C);
+    fft_pass_kernel<C><<<(unsigned)blocks, 256, smem, s>>>(X, lo, hi, a);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    ++launches;
+  }
+  return launches;
+}
+
+template <typename C>
+int launch_reduce(const Instance& in, char* ws, cudaStream_t s) {
+  const Digits g = digits_of(in.fft);
+  const int64_t rows_per_block_step = 8 * (32 / (in.d < 32 ? in.d : 32));
+  int blocks = (int)std::min<int64_t>(kReduceBlocks, (in.N + rows_per_block_step - 1) / rows_per_block_step);
+  if (blocks < 1) blocks = 1;
+  reduce_kernel<C><<<blocks, 256, 0, s>>>(at<C>(ws, in.off_state), at<double>(ws, in.off_hist),
+                                          at<Partial>(ws, in.off_partials), in.N, in.nmat, in.nmeas, g, 1.0);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  finalize_kernel<<<1, 256, 0, s>>>(at<Partial>(ws, in.off_partials), blocks, at<Scalars>(ws, in.off_scalars),
+                                    in.nmeas);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  return 2;
+}
+
+template <typename C>
+int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s) {
+  const Digits g = digits_of(in.fft);
+  unpermute_kernel<C><<<grid_for(in.N * in.d, 256), 256, 0, s>>>(
+      reinterpret_cast<const C*>(ws + in.off_state), reinterpret_cast<C*>(out), in.N, in.nmat, in.nmeas, g);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// Dynamic shared memory above 48 KiB needs an opt-in per kernel.
+cudaError_t configure_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       64 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fft_pass_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+}
+
+template int launch_sweep<float2>(const Instance&, char*, bool, cudaStream_t);
+template int launch_sweep<double2>(const Instance&, char*, bool, cudaStream_t);
+template int launch_fft<float2>(const Instance&, char*, cudaStream_t);
+template int launch_fft<double2>(const Instance&, char*, cudaStream_t);
+template int launch_reduce<float2>(const Instance&, char*, cudaStream_t);
+template int launch_reduce<double2>(const Instance&, char*, cudaStream_t);
+template int launch_unpermute<float2>(const Instance&, const char*, void*, cudaStream_t);
+template int launch_unpermute<double2>(const Instance&, const char*, void*, cudaStream_t);
+
+}  // namespace qpe

@@ -1,0 +1,217 @@
+"""Python binding of libqpe.so (include/qpe.h): argument marshalling only.
+
+Every step of a QPE run executes in the library's CUDA kernels. PyTorch
+supplies device memory (the workspace and any device-side outputs) and the
+CUDA stream; this module never computes any part of the circuit itself and
+has no CPU fallback: importing it fails if libqpe.so is missing.
+
+Typical use::
+
+    plan = Plan(nmat=6, nmeas=16, prec=C64_FP32)
+    plan.load(U, psi)              # numpy complex128 (host) or torch cuda tensors
+    plan.run()
+    probs, argmax, phi_max, phi_mean = plan.probs()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libqpe.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"libqpe.so not found at {_LIB_PATH}: build it first "
+        "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+# ----------------------------------------------------------------- constants
+OK, ERR_ARG, ERR_SHAPE, ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_STATE = range(9)
+FP64, C64_FP32, C64_BF16X3, C64_FP16X2, C64_TF32X3 = range(5)
+FLAG_GATE_SWEEP = 0x1
+FLAG_GRAPH = 0x2
+FLAG_TIMING = 0x4
+STAGE_POWERS, STAGE_SWEEP, STAGE_FFT, STAGE_REDUCE = 1, 2, 3, 4
+INFO_WORKSPACE_BYTES, INFO_STATE_BYTES, INFO_FFT_PASSES, INFO_LAST_LAUNCHES, INFO_INSTANCES = 1, 2, 3, 4, 5
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("nmat", ctypes.c_int32), ("nmeas", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_sig = {
+    "qpe_plan": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_vp)]),
+    "qpe_bind": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "qpe_load": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _i32]),
+    "qpe_run": (ctypes.c_int, [_vp]),
+    "qpe_run_stages": (ctypes.c_int, [_vp, _i32, _i32]),
+    "qpe_probs": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), _i32]),
+    "qpe_state": (ctypes.c_int, [_vp, _i32, _vp, _i32]),
+    "qpe_load_state": (ctypes.c_int, [_vp, _i32, _vp, _i32]),
+    "qpe_powers": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32]),
+    "qpe_query": (ctypes.c_int64, [_vp, _i32]),
+    "qpe_sync": (ctypes.c_int, [_vp]),
+    "qpe_stage_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "qpe_destroy": (ctypes.c_int, [_vp]),
+    "qpe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "qpe_last_error": (ctypes.c_char_p, [_vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+LIB = _lib
+LIB_PATH = _LIB_PATH
+
+
+class QpeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def status_string(st: int) -> str:
+    return _lib.qpe_status_string(st).decode()
+
+
+def plan_workspace(nmat: int, nmeas: int, prec: int = C64_FP32, flags: int = 0):
+    """Host-only: (status, workspace_bytes, raw plan handle)."""
+    desc = PlanDesc(nmat, nmeas, prec, flags)
+    ws = ctypes.c_size_t(0)
+    h = _vp()
+    st = _lib.qpe_plan(ctypes.byref(desc), ctypes.byref(ws), ctypes.byref(h))
+    return st, ws.value, h
+
+
+def _ptr(x):
+    """(address, is_device) of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+class Plan:
+    """One QPE problem bound to a torch-allocated workspace and stream."""
+
+    def __init__(self, nmat: int, nmeas: int, prec: int = C64_FP32, flags: int = 0,
+                 device=None, stream=None, workspace=None):
+        import torch
+        self.nmat, self.nmeas, self.prec, self.flags = nmat, nmeas, prec, flags
+        self.d, self.N = 1 << nmat, 1 << nmeas
+        st, self.ws_bytes, self._h = plan_workspace(nmat, nmeas, prec, flags)
+        if st != OK:
+            raise QpeError(st, f"qpe_plan: {status_string(st)}")
+        self.device = torch.device(device if device is not None else "cuda")
+        if stream is None:
+            stream = torch.cuda.Stream(device=self.device) if (flags & FLAG_GRAPH) else \
+                torch.cuda.current_stream(self.device)
+        self.stream = stream
+        if workspace is None:
+            workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.workspace = workspace
+        self._check(_lib.qpe_bind(self._h, workspace.data_ptr(), self.ws_bytes, stream.cuda_stream), "qpe_bind")
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, st: int, what: str):
+        if st != OK:
+            msg = _lib.qpe_last_error(self._h).decode() if self._h else ""
+            raise QpeError(st, f"{what}: {status_string(st)} {msg}")
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def state_dtype(self):
+        return np.complex128 if self.prec == FP64 else np.complex64
+
+    def query(self, key: int) -> int:
+        return int(_lib.qpe_query(self._h, key))
+
+    # ------------------------------------------------------------------ API
+    def load(self, U, psi, instance: int = 0):
+        """Copy U (d x d complex128) and psi (d complex128) in; numpy arrays
+        are host buffers, CUDA tensors device buffers."""
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+            psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        pu, du = _ptr(U)
+        pp, dp = _ptr(psi)
+        if du != dp:
+            raise ValueError("U and psi must both be host or both be device buffers")
+        self._keep = (U, psi)
+        self._check(_lib.qpe_load(self._h, instance, pu, pp, self.nmat, self.nmeas, du), "qpe_load")
+
+    def run(self):
+        self._check(_lib.qpe_run(self._h), "qpe_run")
+
+    def run_stages(self, first: int, last: int):
+        self._check(_lib.qpe_run_stages(self._h, first, last), "qpe_run_stages")
+
+    def sync(self):
+        self._check(_lib.qpe_sync(self._h), "qpe_sync")
+
+    def probs(self, out=None, instance: int = 0, want_hist: bool = True):
+        """(histogram or None, argmax, phase_argmax, phase_mean). ``out`` may be
+        a float64 numpy array or CUDA tensor of N elements."""
+        am = ctypes.c_int64(0)
+        pa = ctypes.c_double(0.0)
+        pm = ctypes.c_double(0.0)
+        if want_hist and out is None:
+            out = np.empty(self.N, dtype=np.float64)
+        ptr, dev = (0, 0) if out is None else _ptr(out)
+        self._check(_lib.qpe_probs(self._h, instance, ptr or None, ctypes.byref(am), ctypes.byref(pa),
+                                   ctypes.byref(pm), dev), "qpe_probs")
+        return out, am.value, pa.value, pm.value
+
+    def state(self, out=None, instance: int = 0):
+        if out is None:
+            out = np.empty((self.N, self.d), dtype=self.state_dtype)
+        ptr, dev = _ptr(out)
+        self._check(_lib.qpe_state(self._h, instance, ptr, dev), "qpe_state")
+        return out
+
+    def load_state(self, S, instance: int = 0):
+        if isinstance(S, np.ndarray):
+            S = np.ascontiguousarray(S, dtype=self.state_dtype)
+        ptr, dev = _ptr(S)
+        self._keep_state = S
+        self._check(_lib.qpe_load_state(self._h, instance, ptr, dev), "qpe_load_state")
+
+    def power(self, k: int, instance: int = 0) -> np.ndarray:
+        out = np.empty((self.d, self.d), dtype=np.complex128)
+        self._check(_lib.qpe_powers(self._h, instance, k, out.ctypes.data, 0), "qpe_powers")
+        return out
+
+    def stage_times(self):
+        """ms of (powers, sweep, fft, reduce) in the last qpe_run (FLAG_TIMING)."""
+        ms = (ctypes.c_double * 4)()
+        self._check(_lib.qpe_stage_times(self._h, ms), "qpe_stage_times")
+        return list(ms)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qpe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+include/qpe.h declares, and qpe_plan (host only, no GPU) validates its
+arguments and sizes the workspace. No compute call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def q():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2507_17175_gb300 import qpe
+    return qpe
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(qpe_[a-z_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(q):
+    names = header_functions()
+    assert "qpe_run" in names and "qpe_plan" in names
+    lib = ctypes.CDLL(q.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_plan_sizes_workspace(q):
+    st, ws, h = q.plan_workspace(6, 16, q.C64_FP32)
+    assert st == q.OK
+    N, d = 1 << 16, 64
+    assert ws >= N * d * 8 + N * 8 + 16 * d * d * 16
+    assert q.LIB.qpe_query(h, q.INFO_STATE_BYTES) == N * d * 8
+    assert q.LIB.qpe_query(h, q.INFO_FFT_PASSES) == 2
+    q.LIB.qpe_destroy(h)
+    st, ws64, h = q.plan_workspace(6, 16, q.FP64)
+    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_STATE_BYTES) == N * d * 16
+    q.LIB.qpe_destroy(h)
+
+
+@pytest.mark.parametrize("nmat,nmeas,prec,flags,want", [
+    (0, 4, 0, 0, "ERR_ARG"),
+    (13, 4, 0, 0, "ERR_ARG"),
+    (2, 0, 0, 0, "ERR_ARG"),
+    (2, 31, 0, 0, "ERR_ARG"),
+    (2, 4, 7, 0, "ERR_ARG"),
+    (2, 4, -1, 0, "ERR_ARG"),
+    (2, 4, 0, 0x80, "ERR_ARG"),
+    (2, 4, 2, 0, "ERR_UNSUPPORTED"),
+    (7, 4, 1, 1, "ERR_UNSUPPORTED"),
+    (12, 30, 1, 0, "OK"),
+    (1, 1, 0, 0, "OK"),
+])
+def test_plan_validation(q, nmat, nmeas, prec, flags, want):
+    st, ws, h = q.plan_workspace(nmat, nmeas, prec, flags)
+    assert st == getattr(q, want), q.status_string(st)
+    if st == q.OK:
+        assert ws > 0
+        q.LIB.qpe_destroy(h)
+    else:
+        assert not h.value
+
+
+def test_null_arguments(q):
+    assert q.LIB.qpe_plan(None, None, None) == q.ERR_ARG
+    assert q.LIB.qpe_run(None) == q.ERR_ARG
+    assert q.LIB.qpe_destroy(None) == q.OK
+    assert q.LIB.qpe_query(None, 1) == -1
+    assert q.LIB.qpe_last_error(None) == b"null plan"
+
+
+def test_calls_before_bind_are_state_errors(q):
+    st, ws, h = q.plan_workspace(2, 4, q.FP64)
+    assert st == q.OK
+    assert q.LIB.qpe_run(h) == q.ERR_STATE
+    assert q.LIB.qpe_run_stages(h, 1, 4) == q.ERR_STATE
+    assert q.LIB.qpe_sync(h) == q.ERR_STATE
+    assert q.LIB.qpe_bind(h, None, ws, None) == q.ERR_WORKSPACE
+    assert q.LIB.qpe_bind(h, 0x1001, ws, None) == q.ERR_WORKSPACE  # misaligned: rejected before any CUDA call
+    assert q.LIB.qpe_bind(h, 0x1000, ws - 1, None) == q.ERR_WORKSPACE  # too small
+    assert b"256-byte" in q.LIB.qpe_last_error(h)
+    q.LIB.qpe_destroy(h)
+
+
+def test_status_strings(q):
+    for st in range(9):
+        assert q.status_string(st).startswith("QPE_")
