@@ -76,6 +76,13 @@ typedef enum {
                                  /* graph on first use and replays it         */
 #define QPE_FLAG_TIMING 0x4u     /* record a CUDA event before each stage and  */
                                  /* after the last one (read: qpe_stage_times) */
+#define QPE_FLAG_PLAIN 0x8u      /* materialise the N x d state after the      */
+                                 /* controlled gates and run QFT^-1 and the    */
+                                 /* reduction as separate passes over it; the  */
+                                 /* default for nmat <= 6 is the fused         */
+                                 /* schedule (see qpe_run)                     */
+#define QPE_FLAG_KEEP_STATE 0x10u /* fused schedule: also write the final     */
+                                  /* statevector (one extra state write)      */
 
 typedef struct {
   int32_t nmat;   /* target-register qubits, 1..12 (d = 2^nmat)                 */
@@ -135,6 +142,15 @@ qpe_status qpe_load(qpe_plan_t plan, int32_t instance, const void* U, const void
  * qpe_run: enqueue one whole run (all four stages) on the bound stream.
  * Asynchronous: no host synchronisation and no allocation. Requires bind and
  * load (QPE_ERR_STATE).
+ *
+ * Schedules. For nmat <= 6, unless QPE_FLAG_PLAIN or QPE_FLAG_GATE_SWEEP is
+ * set, the controlled gates, QFT^-1 and the histogram run fused: with
+ * m = m_b + 2^r m_a, X[y] = sum_{m_b} w_N^(m_b y) U^(m_b) Z[y mod N/2^r] where
+ * Z is the same QPE for U^(2^r) on the high measurement qubits, so the work
+ * recurses over levels of r <= 10 bits and the N x d state is never written
+ * unless QPE_FLAG_KEEP_STATE asks for the final statevector. Otherwise the
+ * state is materialised after the controlled gates (doubling or gate-by-gate
+ * schedule) and transformed and reduced in separate passes.
  */
 qpe_status qpe_run(qpe_plan_t plan);
 
@@ -163,7 +179,8 @@ qpe_status qpe_probs(qpe_plan_t plan, int32_t instance, double* probs, int64_t* 
  * natural row order: after SWEEP, row m = 2^(-n/2) U^m psi; after FFT, row y
  * is the final statevector (the paper's output file, Sec. 3). Host output
  * synchronises and reorders on the host; device output is reordered by a
- * kernel on the stream.
+ * kernel on the stream. After a fused qpe_run the final state exists only
+ * with QPE_FLAG_KEEP_STATE (QPE_ERR_STATE otherwise).
  */
 qpe_status qpe_state(qpe_plan_t plan, int32_t instance, void* out, int32_t ptr_is_device);
 

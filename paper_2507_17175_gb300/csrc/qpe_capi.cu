@@ -15,6 +15,10 @@ namespace qpe {
 cudaError_t configure_kernels();
 }
 
+#ifndef QPE_MAX_FUSED_NMAT
+#define QPE_MAX_FUSED_NMAT 6
+#endif
+
 using qpe::Instance;
 
 namespace {
@@ -38,7 +42,7 @@ qpe_status cuda_fail(qpe_plan_t p, cudaError_t e, const char* where) {
 }
 
 // Lays out one instance starting at byte offset `base`; returns the end.
-size_t layout_instance(Instance& in, int prec, size_t base) {
+size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   const int64_t d = in.d, N = in.N;
   size_t off = align_up(base);
   auto take = [&](size_t bytes) {
@@ -61,6 +65,23 @@ size_t layout_instance(Instance& in, int prec, size_t base) {
   in.off_partials = take(sizeof(qpe::Partial) * qpe::kReduceBlocks);
   in.off_scalars = take(sizeof(qpe::Scalars));
   in.fft = qpe::make_fft_plan(in.nmeas, d, elem_size(prec));
+  in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP));
+  in.keep_state = (flags & QPE_FLAG_KEEP_STATE) != 0;
+  if (in.nmat <= QPE_MAX_FUSED_NMAT) {
+    // level buffers for the fused schedule (also allotted to plain plans so a
+    // plan's layout does not depend on its schedule flags)
+    in.levels = qpe::make_levels(in.nmeas, in.nmat, elem_size(prec), 0);
+    size_t zb[2] = {0, 0};
+    for (size_t li = 1; li < in.levels.size(); ++li) {
+      const qpe::Level& L = in.levels[li];
+      const size_t bytes = ((size_t)1 << (L.logna + L.r)) * d * elem_size(prec);
+      zb[li & 1] = std::max(zb[li & 1], bytes);
+    }
+    in.off_zbuf[0] = take(zb[0] ? zb[0] : 16);
+    in.off_zbuf[1] = take(zb[1] ? zb[1] : 16);
+    in.zbuf_seed_off = take((size_t)d * elem_size(prec));
+    for (qpe::Level& L : in.levels) L.tab_off = take(((size_t)d << L.r) * d * elem_size(prec));
+  }
   return off;
 }
 
@@ -69,7 +90,8 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
   if (desc->nmat < 1 || desc->nmat > kMaxNmat) return QPE_ERR_ARG;
   if (desc->nmeas < 1 || desc->nmeas > kMaxNmeas) return QPE_ERR_ARG;
   if (desc->prec < QPE_FP64 || desc->prec > QPE_C64_TF32X3) return QPE_ERR_ARG;
-  if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING)) return QPE_ERR_ARG;
+  if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE))
+    return QPE_ERR_ARG;
   if (desc->prec > QPE_C64_FP32) return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
   return QPE_OK;
@@ -89,6 +111,17 @@ cudaMemcpyKind kind_from_device(int32_t ptr_is_device) {
   return ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
 }
 
+// Records a timing event; inside stream capture it must become an event
+// record node of the graph (cudaEventRecordExternal), outside it is a plain
+// record (the external flag is rejected on a stream that is not capturing).
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, s);
+}
+
 // Enqueue stages first..last for every instance; returns launches or sets error.
 qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) {
   int64_t n = 0;
@@ -98,9 +131,37 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
   p->timed_run = timing && first == QPE_STAGE_POWERS && last == QPE_STAGE_REDUCE;
   for (Instance& in : p->inst) {
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
+    if (in.fused && first <= QPE_STAGE_SWEEP && last == QPE_STAGE_REDUCE) {
+      // fused schedule: POWERS, then the levels (gates + QFT^-1 + histogram)
+      for (int st = first; st <= QPE_STAGE_REDUCE; ++st) {
+        if (timing) {
+          cudaError_t e = record_event(p->ev[st - 1], p->stream);
+          if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventRecord");
+        }
+        int r = 0;
+        if (st == QPE_STAGE_POWERS) {
+          r = qpe::launch_powers(in, p->ws, c64, p->stream);
+          in.powers_done = true;
+        } else if (st == QPE_STAGE_SWEEP) {
+          if (!in.powers_done) return fail(p, QPE_ERR_STATE, "SWEEP before POWERS");
+          r = c64 ? qpe::launch_levels<float2>(in, p->ws, in.keep_state, p->stream)
+                  : qpe::launch_levels<double2>(in, p->ws, in.keep_state, p->stream);
+        }
+        if (r < 0) return cuda_fail(p, cudaGetLastError(), "kernel launch");
+        n += r;
+      }
+      if (timing) {
+        cudaError_t e = record_event(p->ev[QPE_STAGE_REDUCE], p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventRecord");
+      }
+      in.state_stage = QPE_STAGE_REDUCE;
+      in.state_natural = true;
+      in.state_valid = in.keep_state;
+      continue;
+    }
     for (int st = first; st <= last; ++st) {
       if (timing) {
-        cudaError_t e = cudaEventRecordWithFlags(p->ev[st - 1], p->stream, cudaEventRecordExternal);
+        cudaError_t e = record_event(p->ev[st - 1], p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventRecord");
       }
       int r = 0;
@@ -114,14 +175,19 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
           r = c64 ? qpe::launch_sweep<float2>(in, p->ws, gate, p->stream)
                   : qpe::launch_sweep<double2>(in, p->ws, gate, p->stream);
           in.state_stage = QPE_STAGE_SWEEP;
+          in.state_natural = true;
+          in.state_valid = true;
           break;
         case QPE_STAGE_FFT:
           if (in.state_stage != QPE_STAGE_SWEEP) return fail(p, QPE_ERR_STATE, "FFT needs the state after SWEEP");
+          if (!in.state_valid) return fail(p, QPE_ERR_STATE, "no materialised state to transform");
           r = c64 ? qpe::launch_fft<float2>(in, p->ws, p->stream) : qpe::launch_fft<double2>(in, p->ws, p->stream);
           in.state_stage = QPE_STAGE_FFT;
+          in.state_natural = false;
           break;
         case QPE_STAGE_REDUCE:
-          if (in.state_stage != QPE_STAGE_FFT && in.state_stage != QPE_STAGE_REDUCE)
+          if ((in.state_stage != QPE_STAGE_FFT && in.state_stage != QPE_STAGE_REDUCE) || in.state_natural ||
+              !in.state_valid)
             return fail(p, QPE_ERR_STATE, "REDUCE needs the state after FFT");
           r = c64 ? qpe::launch_reduce<float2>(in, p->ws, p->stream)
                   : qpe::launch_reduce<double2>(in, p->ws, p->stream);
@@ -134,7 +200,7 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
       n += r;
     }
     if (timing) {
-      cudaError_t e = cudaEventRecordWithFlags(p->ev[last], p->stream, cudaEventRecordExternal);
+      cudaError_t e = record_event(p->ev[last], p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventRecord");
     }
   }
@@ -177,7 +243,7 @@ qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan
   in.nmeas = desc->nmeas;
   in.d = int64_t(1) << desc->nmat;
   in.N = int64_t(1) << desc->nmeas;
-  p->ws_bytes = layout_instance(in, p->prec, 0);
+  p->ws_bytes = layout_instance(in, p->prec, p->flags, 0);
   p->inst.push_back(in);
   *workspace_bytes = p->ws_bytes;
   *out = p;
@@ -204,7 +270,20 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
       if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventCreate");
     }
   }
+  int nsm = 0, dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(p, e, "device query");
   for (Instance& in : p->inst) {
+    if (!in.levels.empty()) {
+      int occ = 1;
+      for (const qpe::Level& L : in.levels) {
+        const int o = is_c64(p->prec) ? qpe::level_occupancy<float2>(in.nmat, L.r)
+                                      : qpe::level_occupancy<double2>(in.nmat, L.r);
+        occ = std::max(occ, o);
+      }
+      in.level_grid = (int64_t)nsm * occ;
+    }
     in.loaded = false;
     in.powers_done = false;
     in.state_stage = 0;
@@ -326,8 +405,10 @@ qpe_status qpe_state(qpe_plan_t p, int32_t instance, void* out, int32_t ptr_is_d
   qpe_status st = get_instance(p, instance, &in);
   if (st != QPE_OK) return st;
   if (in->state_stage == 0) return fail(p, QPE_ERR_STATE, "no state computed yet");
+  if (!in->state_valid)
+    return fail(p, QPE_ERR_STATE, "the fused schedule keeps the final state only with QPE_FLAG_KEEP_STATE");
   const bool c64 = is_c64(p->prec);
-  const bool permuted = in->state_stage == QPE_STAGE_FFT || in->state_stage == QPE_STAGE_REDUCE;
+  const bool permuted = !in->state_natural;
   cudaError_t e;
   if (!permuted) {
     e = cudaMemcpyAsync(out, p->ws + in->off_state, in->state_bytes, kind_from_device(ptr_is_device), p->stream);
@@ -370,6 +451,8 @@ qpe_status qpe_load_state(qpe_plan_t p, int32_t instance, const void* src, int32
   if (e != cudaSuccess) return cuda_fail(p, e, "qpe_load_state copy");
   in->loaded = true;
   in->state_stage = QPE_STAGE_SWEEP;
+  in->state_natural = true;
+  in->state_valid = true;
   return QPE_OK;
 }
 

@@ -79,6 +79,39 @@ struct Partial {
 
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
 
+// One level of the fused small-d schedule: the controlled gates of
+// measurement qubits off .. off + r - 1 and a length-2^r DFT, for N_a = 2^logna
+// seeds.
+struct Level {
+  int off, r, logna;
+  size_t tab_off;  // workspace offset of this level's table U_l^(m_b), m_b < 2^r
+};
+
+constexpr int kMaxLevels = 32;
+struct TableJobs {
+  int count;
+  int off[kMaxLevels];
+  int r[kMaxLevels];
+  size_t tab_off[kMaxLevels];
+};
+
+constexpr size_t kLevelSmemCap = 110 * 1024;  // two CTAs per SM
+
+template <typename C>
+struct LevelArgs {
+  const C* seeds;  // N_a x d: Z of the level below (psi for the deepest level)
+  const C* tab;    // [k][m_b d + i] = (U_l^(m_b))[i][k]
+  int off, r, logna, logd, nmeas, htw;
+  const C* tw_lo;
+  const C* tw_hi;
+  C* xout;         // MODE 0: X of this level; MODE 2: physical final state
+  double* hist;    // MODE 1/2
+  Partial* parts;  // MODE 1/2
+  double pscale;   // 1 / N^2
+  double inv_n;    // 1 / N
+  double xscale;
+};
+
 // One problem instance inside a plan: its shape and workspace offsets.
 struct Instance {
   int nmat, nmeas;
@@ -94,9 +127,18 @@ struct Instance {
   size_t off_scalars;   // Scalars
   size_t state_bytes;
   FftPlan fft;
+  // fused small-d schedule
+  bool fused = false;
+  std::vector<Level> levels;  // top level first
+  size_t off_zbuf[2] = {0, 0};
+  size_t zbuf_seed_off = 0;
+  int64_t level_grid = 0;     // persistent grid (set at bind)
+  bool keep_state = false;
   bool loaded = false;
   bool powers_done = false;
   int state_stage = 0;  // last stage whose output the state buffer holds
+  bool state_natural = false;  // state buffer rows are in natural order of y
+  bool state_valid = true;     // false after a fused run without KEEP_STATE
 };
 
 }  // namespace qpe
@@ -126,6 +168,17 @@ template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_m
 template <typename C> int launch_fft(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_reduce(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s);
+
+template <typename C> int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s);
+int launch_finalize(const Instance& in, char* ws, int count, cudaStream_t s);
+inline void finalize_readout(const Instance& in, char* ws, int count, cudaStream_t s) {
+  launch_finalize(in, ws, count, s);
+}
+size_t level_smem_bytes(int logd, int r, size_t esize);
+int level_max_bits(int logd, size_t esize, size_t smem_cap);
+std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
+cudaError_t configure_level_kernels();
+template <typename C> int level_occupancy(int logd, int r);
 
 // Host helpers shared with the ABI layer.
 int64_t fft_position_to_y(const FftPlan& f, int nmeas, int64_t p);

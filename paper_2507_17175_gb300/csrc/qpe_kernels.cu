@@ -625,6 +625,12 @@ int launch_reduce(const Instance& in, char* ws, cudaStream_t s) {
   return 2;
 }
 
+int launch_finalize(const Instance& in, char* ws, int count, cudaStream_t s) {
+  finalize_kernel<<<1, 256, 0, s>>>(at<Partial>(ws, in.off_partials), count, at<Scalars>(ws, in.off_scalars),
+                                    in.nmeas);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 template <typename C>
 int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s) {
   const Digits g = digits_of(in.fft);
@@ -635,7 +641,9 @@ int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t
 
 // Dynamic shared memory above 48 KiB needs an opt-in per kernel.
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = configure_level_kernels();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fft_pass_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        64 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(fft_pass_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);

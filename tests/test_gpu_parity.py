@@ -47,8 +47,11 @@ def run_plan(q, inst, prec, flags=0):
 
 
 # ------------------------------------------------------------ end to end
+PLAIN, KEEP = 0x8, 0x10
+
+
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("flags", [0, 1, 2])
+@pytest.mark.parametrize("flags", [0, 1, 2, PLAIN, PLAIN | 2])
 def test_c1_exact_phase(q, prec, flags):
     inst = W.c1()
     plan, P, am, pa, pm = run_plan(q, inst, prec, flags)
@@ -63,7 +66,7 @@ def test_c1_exact_phase(q, prec, flags):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, PLAIN])
 def test_c2_vs_gate_by_gate_and_fejer(q, prec, flags):
     inst = W.c2()
     plan, P, am, pa, pm = run_plan(q, inst, prec, flags)
@@ -184,10 +187,11 @@ def test_reduce_ties_go_to_lowest_index(q):
     assert pm == pytest.approx((0 + 1 + 2 + 3) / 4 / 4)
 
 
-def test_state_readback_device_matches_host(q):
+@pytest.mark.parametrize("flags", [KEEP, PLAIN])
+def test_state_readback_device_matches_host(q, flags):
     import torch
     inst = W.c1()
-    plan, *_ = run_plan(q, inst, q.FP64)
+    plan, *_ = run_plan(q, inst, q.FP64, flags)
     host = plan.state()
     dev = torch.empty((64, 4), dtype=torch.complex128, device="cuda")
     plan.state(dev)
@@ -195,6 +199,41 @@ def test_state_readback_device_matches_host(q):
     assert np.array_equal(host, dev.cpu().numpy())
     ref = gates.qpe_final_state(inst.U, inst.psi, inst.nmeas)
     assert np.abs(host - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nmat,nmeas", [(1, 12), (2, 14), (3, 11), (4, 13), (5, 10), (6, 9), (2, 20), (4, 19),
+                                        (6, 17), (1, 1), (3, 2)])
+def test_fused_levels_vs_oracle(q, prec, nmat, nmeas):
+    """The fused schedule (levels of r <= 10 measurement qubits, recursing
+    through Z tables) against the gate-by-gate oracle: histogram, readout and
+    the kept final statevector. Sizes cover one, two and three levels."""
+    rng = np.random.default_rng(1000 * nmat + nmeas)
+    inst = W.haar_instance(rng, nmat, nmeas, superposition=True)
+    plan = q.Plan(nmat, nmeas, prec, KEEP)
+    plan.load(inst.U, inst.psi)
+    plan.run()
+    P, am, pa, pm = plan.probs()
+    X = plan.state()
+    ref_state = gates.qpe_final_state(inst.U, inst.psi, nmeas)
+    ref = gates.probabilities(ref_state)
+    assert np.abs(P - ref).max() <= TOL[prec]
+    top2 = np.sort(ref)[-2:]
+    if top2[1] - top2[0] > 10 * TOL[prec]:
+        assert am == readout.argmax_lowest(ref)
+    assert abs(pm - readout.phase_weighted_mean(ref)) <= (1e-9 if prec == 0 else 2e-5)
+    # FP64: U^(2^(n-1)) carries ~2^(n-1) u of rounding on both sides
+    amp_tol = max(1e-12, 16 * (1 << nmeas) * U64) if prec == 0 else 3e-6
+    assert np.abs(X - ref_state).max() <= amp_tol
+    # without KEEP_STATE the same histogram, and the state is not available
+    plan2 = q.Plan(nmat, nmeas, prec)
+    plan2.load(inst.U, inst.psi)
+    plan2.run()
+    P2, am2, _, _ = plan2.probs()
+    assert np.array_equal(P, P2) and am == am2
+    with pytest.raises(q.QpeError) as e:
+        plan2.state()
+    assert e.value.status == q.ERR_STATE
 
 
 def test_device_inputs(q):
