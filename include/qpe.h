@@ -206,6 +206,17 @@ int64_t qpe_query(qpe_plan_t plan, int32_t key);
  */
 qpe_status qpe_stage_times(qpe_plan_t plan, double* ms);
 
+/*
+ * qpe_kernel_time: milliseconds of the last qpe_run's dominant kernel on the
+ * bound stream, from a CUDA event pair around that launch (QPE_FLAG_TIMING,
+ * single instance): the top level of the fused schedule (the launch that
+ * applies the controlled gates of the low measurement qubits to every row,
+ * runs its QFT^-1 digit and writes the histogram). *kernel_id receives 1 for
+ * that kernel, or 0 (and *ms = 0) when the last run used another schedule.
+ * Synchronises the stream.
+ */
+qpe_status qpe_kernel_time(qpe_plan_t plan, double* ms, int32_t* kernel_id);
+
 /* qpe_sync: wait for the bound stream and report device-side error flags. */
 qpe_status qpe_sync(qpe_plan_t plan);
 

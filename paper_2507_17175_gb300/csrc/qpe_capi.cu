@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -13,6 +14,7 @@
 
 namespace qpe {
 cudaError_t configure_kernels();
+bool g_pdl_enabled = false;
 }
 
 #ifndef QPE_MAX_FUSED_NMAT
@@ -111,6 +113,9 @@ cudaMemcpyKind kind_from_device(int32_t ptr_is_device) {
   return ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
 }
 
+}  // namespace
+
+namespace qpe {
 // Records a timing event; inside stream capture it must become an event
 // record node of the graph (cudaEventRecordExternal), outside it is a plain
 // record (the external flag is rejected on a stream that is not capturing).
@@ -121,6 +126,10 @@ cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
   return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
                                              : cudaEventRecord(ev, s);
 }
+}  // namespace qpe
+
+namespace {
+using qpe::record_event;
 
 // Enqueue stages first..last for every instance; returns launches or sets error.
 qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) {
@@ -129,6 +138,7 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
   const bool gate = (p->flags & QPE_FLAG_GATE_SWEEP) != 0;
   const bool timing = (p->flags & QPE_FLAG_TIMING) && p->inst.size() == 1 && p->ev[0];
   p->timed_run = timing && first == QPE_STAGE_POWERS && last == QPE_STAGE_REDUCE;
+  p->timed_kernel = false;
   for (Instance& in : p->inst) {
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
     if (in.fused && first <= QPE_STAGE_SWEEP && last == QPE_STAGE_REDUCE) {
@@ -144,8 +154,10 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
           in.powers_done = true;
         } else if (st == QPE_STAGE_SWEEP) {
           if (!in.powers_done) return fail(p, QPE_ERR_STATE, "SWEEP before POWERS");
-          r = c64 ? qpe::launch_levels<float2>(in, p->ws, in.keep_state, p->stream)
-                  : qpe::launch_levels<double2>(in, p->ws, in.keep_state, p->stream);
+          cudaEvent_t* kev = timing ? &p->ev[5] : nullptr;
+          r = c64 ? qpe::launch_levels<float2>(in, p->ws, in.keep_state, p->stream, kev)
+                  : qpe::launch_levels<double2>(in, p->ws, in.keep_state, p->stream, kev);
+          p->timed_kernel = timing;
         }
         if (r < 0) return cuda_fail(p, cudaGetLastError(), "kernel launch");
         n += r;
@@ -258,6 +270,10 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
     return fail(p, QPE_ERR_ARG, "QPE_FLAG_GRAPH needs a non-default stream");
   cudaError_t e = qpe::configure_kernels();
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute");
+  {
+    const char* v = getenv("QPE_PDL");
+    qpe::g_pdl_enabled = !(v && v[0] == '0');
+  }
   if (p->graph_exec) {
     cudaGraphExecDestroy(p->graph_exec);
     p->graph_exec = nullptr;
@@ -497,6 +513,23 @@ qpe_status qpe_stage_times(qpe_plan_t p, double* ms) {
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventElapsedTime");
     ms[i] = t;
   }
+  return QPE_OK;
+}
+
+qpe_status qpe_kernel_time(qpe_plan_t p, double* ms, int32_t* kernel_id) {
+  if (!p || !ms || !kernel_id) return fail(p, QPE_ERR_ARG, "null pointer");
+  if (!(p->flags & QPE_FLAG_TIMING) || p->inst.size() != 1 || !p->ev[0])
+    return fail(p, QPE_ERR_STATE, "plan was not created with QPE_FLAG_TIMING (single instance) and bound");
+  *ms = 0.0;
+  *kernel_id = 0;
+  if (!p->timed_kernel) return QPE_OK;
+  cudaError_t e = cudaEventSynchronize(p->ev[6]);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventSynchronize");
+  float t = 0.f;
+  e = cudaEventElapsedTime(&t, p->ev[5], p->ev[6]);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventElapsedTime");
+  *ms = t;
+  *kernel_id = 1;
   return QPE_OK;
 }
 

@@ -12,6 +12,36 @@
 
 namespace qpe {
 
+// ------------------------------------------------ programmatic dependent launch
+// Every kernel of a run starts with pdl_wait(), which returns once the
+// previous grid in the stream has completed and its writes are visible, and
+// ends by letting its successor be scheduled (pdl_trigger(), or implicitly at
+// exit). With programmatic launches enabled (the default; QPE_PDL=0 in the
+// environment at qpe_bind turns them off), a dependent kernel's launch
+// overlaps the tail of its predecessor; otherwise launch_k() is an ordinary
+// launch and both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_begin() { pdl_wait(); }
+
+extern bool g_pdl_enabled;
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = g_pdl_enabled ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------- complex
 template <typename C> struct real_of;
 template <> struct real_of<float2> { using type = float; };
@@ -153,7 +183,8 @@ struct qpe_plan_s {
   bool bound = false;
   int64_t last_launches = 0;
   cudaGraphExec_t graph_exec = nullptr;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // QPE_FLAG_TIMING
+  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // QPE_FLAG_TIMING
+  bool timed_kernel = false;  // ev[5], ev[6] bracket the top-level fused kernel of the last run
   bool timed_run = false;  // the last enqueue recorded all five events
   std::string last_error;
 };
@@ -169,12 +200,14 @@ template <typename C> int launch_fft(const Instance& in, char* ws, cudaStream_t 
 template <typename C> int launch_reduce(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s);
 
-template <typename C> int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s);
+template <typename C>
+int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s, cudaEvent_t* top_ev = nullptr);
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s);
 int launch_finalize(const Instance& in, char* ws, int count, cudaStream_t s);
 inline void finalize_readout(const Instance& in, char* ws, int count, cudaStream_t s) {
   launch_finalize(in, ws, count, s);
 }
-size_t level_smem_bytes(int logd, int r, size_t esize);
+size_t level_smem_bytes(int logd, int mode, size_t esize);
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 cudaError_t configure_level_kernels();

@@ -37,6 +37,7 @@ __device__ __forceinline__ C twiddle(const C* lo, const C* hi, int h, int64_t e)
 // ------------------------------------------------------------- twiddles
 __global__ void twiddle_tables_kernel(double2* lo64, double2* hi64, float2* lo32, float2* hi32,
                                       int n, int h) {
+  pdl_begin();
   const int64_t nlo = int64_t(1) << h;
   const int64_t nhi = int64_t(1) << (n - h);
   const double N = ldexp(1.0, n);
@@ -61,9 +62,14 @@ __global__ void twiddle_tables_kernel(double2* lo64, double2* hi64, float2* lo32
 // C = A * A for a d x d complex128 matrix, d <= 256. Each CTA owns a TS x TS
 // output tile; its KS thread layers split the inner index and are summed in
 // shared memory, so even d = 64 spreads over hundreds of CTAs.
+// C32 / A32 (optional): complex64 copies of the result / of the input, each
+// element written by the thread that owns that output position.
 template <int TS, int KS>
 __global__ void __launch_bounds__(TS * TS * KS) square_small_kernel(const double2* __restrict__ A,
-                                                                    double2* __restrict__ C, int d) {
+                                                                    double2* __restrict__ C, int d,
+                                                                    float2* __restrict__ C32,
+                                                                    float2* __restrict__ A32) {
+  pdl_begin();
   __shared__ double2 red[KS][TS][TS];
   const int tx = threadIdx.x % TS;
   const int ty = (threadIdx.x / TS) % TS;
@@ -79,14 +85,23 @@ __global__ void __launch_bounds__(TS * TS * KS) square_small_kernel(const double
   if (tz == 0) {
     double2 s = red[0][ty][tx];
     for (int z = 1; z < KS; ++z) s = cadd(s, red[z][ty][tx]);
-    C[(int64_t)row * d + col] = s;
+    const int64_t o = (int64_t)row * d + col;
+    C[o] = s;
+    if (C32) C32[o] = make_float2((float)s.x, (float)s.y);
+    if (A32) {
+      const double2 v = A[o];
+      A32[o] = make_float2((float)v.x, (float)v.y);
+    }
   }
+  pdl_trigger();
 }
 
 // C = A * A for d >= 512: 32 x 32 output tiles, 16-wide k slabs in shared
 // memory, 2 x 2 outputs per thread.
 __global__ void __launch_bounds__(256) square_tiled_kernel(const double2* __restrict__ A,
-                                                           double2* __restrict__ C, int d) {
+                                                           double2* __restrict__ C, int d,
+                                                           float2* __restrict__ C32, float2* __restrict__ A32) {
+  pdl_begin();
   constexpr int T = 32, BK = 16;
   __shared__ double2 As[BK][T + 1];
   __shared__ double2 Bs[BK][T + 1];
@@ -116,11 +131,21 @@ __global__ void __launch_bounds__(256) square_tiled_kernel(const double2* __rest
     __syncthreads();
   }
   for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 2; ++j) C[(int64_t)(r0 + tr + 16 * i) * d + c0 + tc + 16 * j] = acc[i][j];
+    for (int j = 0; j < 2; ++j) {
+      const int64_t o = (int64_t)(r0 + tr + 16 * i) * d + c0 + tc + 16 * j;
+      C[o] = acc[i][j];
+      if (C32) C32[o] = make_float2((float)acc[i][j].x, (float)acc[i][j].y);
+      if (A32) {
+        const double2 v = A[o];
+        A32[o] = make_float2((float)v.x, (float)v.y);
+      }
+    }
+  pdl_trigger();
 }
 
 __global__ void convert_c128_to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out,
                                            int64_t count) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = in[i];
@@ -133,6 +158,7 @@ __global__ void convert_c128_to_c64_kernel(const double2* __restrict__ in, float
 template <typename C>
 __global__ void init_rows_kernel(C* __restrict__ S, const double2* __restrict__ psi, int64_t rows, int logd,
                                  double scale) {
+  pdl_begin();
   const int64_t total = rows << logd;
   const int64_t dmask = (int64_t(1) << logd) - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -165,6 +191,7 @@ struct GateRows {  // gate k: the r-th row with bit k set, in place
 template <typename C, int BM, int BN, int BK, int TM, int TN, typename Rows>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     rows_times_pt_kernel(C* __restrict__ S, const C* __restrict__ P, int64_t M, int d, Rows rows) {
+  pdl_begin();
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TCOLS = BN / TN;
   __shared__ C As[BK][BM + 1];
@@ -240,6 +267,7 @@ __device__ __forceinline__ int bitrev(int x, int bits) { return bits ? (__brev(x
 template <typename C>
 __global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const C* __restrict__ tw_lo,
                                                        const C* __restrict__ tw_hi, FftArgs a) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tile = reinterpret_cast<C*>(smem_raw);
   using R_t = typename real_of<C>::type;
@@ -331,6 +359,7 @@ template <typename C>
 __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, double* __restrict__ hist,
                                                      Partial* __restrict__ parts, int64_t N, int logd, int n,
                                                      Digits g, double scale) {
+  pdl_begin();
   const int d = 1 << logd;
   const int lpr = d < 32 ? d : 32;  // lanes per row
   const int rpw = 32 / lpr;         // rows per warp step
@@ -386,6 +415,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
 
 __global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict__ parts, int count,
                                                        Scalars* __restrict__ out, int n) {
+  pdl_begin();
   __shared__ Partial sp[256];
   Partial r{-1.0, INT64_MAX, 0.0, 0.0};
   for (int i = threadIdx.x; i < count; i += 256) {
@@ -422,6 +452,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict
 template <typename C>
 __global__ void unpermute_kernel(const C* __restrict__ X, C* __restrict__ out, int64_t N, int logd, int n,
                                  Digits g) {
+  pdl_begin();
   const int64_t total = N << logd;
   const int64_t dmask = (int64_t(1) << logd) - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -461,39 +492,44 @@ Digits digits_of(const FftPlan& f) {
 // ============================================================ launchers
 int launch_twiddles(const Instance& in, char* ws, cudaStream_t s) {
   const int64_t total = (int64_t(1) << in.htw) + (int64_t(1) << (in.nmeas - in.htw));
-  twiddle_tables_kernel<<<grid_for(total, 256), 256, 0, s>>>(
-      at<double2>(ws, in.off_tw_lo64), at<double2>(ws, in.off_tw_hi64), at<float2>(ws, in.off_tw_lo32),
-      at<float2>(ws, in.off_tw_hi32), in.nmeas, in.htw);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  const cudaError_t e = launch_k(twiddle_tables_kernel, dim3(grid_for(total, 256)), dim3(256), 0, s,
+                                 at<double2>(ws, in.off_tw_lo64), at<double2>(ws, in.off_tw_hi64),
+                                 at<float2>(ws, in.off_tw_lo32), at<float2>(ws, in.off_tw_hi32), in.nmeas, in.htw);
+  return e == cudaSuccess ? 1 : -1;
 }
 
-static int launch_square(const double2* A, double2* C, int d, cudaStream_t s) {
+static int launch_square(const double2* A, double2* C, int d, float2* C32, float2* A32, cudaStream_t s) {
+  cudaError_t e;
   switch (d) {
-    case 2: square_small_kernel<2, 2><<<dim3(1, 1), 8, 0, s>>>(A, C, d); break;
-    case 4: square_small_kernel<4, 4><<<dim3(1, 1), 64, 0, s>>>(A, C, d); break;
-    case 8: square_small_kernel<4, 8><<<dim3(2, 2), 128, 0, s>>>(A, C, d); break;
-    case 16: square_small_kernel<4, 16><<<dim3(4, 4), 256, 0, s>>>(A, C, d); break;
-    case 32: square_small_kernel<4, 16><<<dim3(8, 8), 256, 0, s>>>(A, C, d); break;
-    case 64: square_small_kernel<4, 16><<<dim3(16, 16), 256, 0, s>>>(A, C, d); break;
-    case 128: square_small_kernel<8, 4><<<dim3(16, 16), 256, 0, s>>>(A, C, d); break;
-    case 256: square_small_kernel<8, 4><<<dim3(32, 32), 256, 0, s>>>(A, C, d); break;
-    default: square_tiled_kernel<<<dim3(d / 32, d / 32), 256, 0, s>>>(A, C, d); break;
+    case 2: e = launch_k(square_small_kernel<2, 2>, dim3(1, 1), dim3(8), 0, s, A, C, d, C32, A32); break;
+    case 4: e = launch_k(square_small_kernel<4, 4>, dim3(1, 1), dim3(64), 0, s, A, C, d, C32, A32); break;
+    case 8: e = launch_k(square_small_kernel<4, 8>, dim3(2, 2), dim3(128), 0, s, A, C, d, C32, A32); break;
+    case 16: e = launch_k(square_small_kernel<4, 16>, dim3(4, 4), dim3(256), 0, s, A, C, d, C32, A32); break;
+    case 32: e = launch_k(square_small_kernel<4, 16>, dim3(8, 8), dim3(256), 0, s, A, C, d, C32, A32); break;
+    case 64: e = launch_k(square_small_kernel<4, 16>, dim3(16, 16), dim3(256), 0, s, A, C, d, C32, A32); break;
+    case 128: e = launch_k(square_small_kernel<8, 4>, dim3(16, 16), dim3(256), 0, s, A, C, d, C32, A32); break;
+    case 256: e = launch_k(square_small_kernel<8, 4>, dim3(32, 32), dim3(256), 0, s, A, C, d, C32, A32); break;
+    default: e = launch_k(square_tiled_kernel, dim3(d / 32, d / 32), dim3(256), 0, s, A, C, d, C32, A32); break;
   }
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return e == cudaSuccess ? 1 : -1;
 }
 
 int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s) {
   const int64_t dd = in.d * in.d;
   double2* P = at<double2>(ws, in.off_pow64);
+  float2* P32 = want_c64 ? at<float2>(ws, in.off_pow32) : nullptr;
   int launches = 0;
   for (int k = 1; k < in.nmeas; ++k) {
-    if (launch_square(P + (k - 1) * dd, P + k * dd, (int)in.d, s) < 0) return -1;
+    // complex64 copies ride along: P_k from the squaring that makes it, P_0 from the first one
+    if (launch_square(P + (k - 1) * dd, P + k * dd, (int)in.d, P32 ? P32 + k * dd : nullptr,
+                      (P32 && k == 1) ? P32 : nullptr, s) < 0)
+      return -1;
     ++launches;
   }
-  if (want_c64) {
-    const int64_t count = dd * in.nmeas;
-    convert_c128_to_c64_kernel<<<grid_for(count, 256), 256, 0, s>>>(P, at<float2>(ws, in.off_pow32), count);
-    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (want_c64 && in.nmeas == 1) {
+    if (launch_k(convert_c128_to_c64_kernel, dim3(grid_for(dd, 256)), dim3(256), 0, s, (const double2*)P, P32,
+                 dd) != cudaSuccess)
+      return -1;
     ++launches;
   }
   return launches;
@@ -502,11 +538,12 @@ int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s) {
 template <typename C, typename Rows>
 static int launch_rows_times_pt(C* S, const C* P, int64_t M, int d, Rows rows, cudaStream_t s) {
   if (M <= 0) return 0;
+  cudaError_t err = cudaSuccess;
 #define QPE_GEMM(BM, BN, BK, TM, TN)                                                          \
   do {                                                                                        \
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)(d / BN));                              \
-    rows_times_pt_kernel<C, BM, BN, BK, TM, TN, Rows><<<grid, (BM / TM) * (BN / TN), 0, s>>>( \
-        S, P, M, d, rows);                                                                    \
+    err = launch_k(rows_times_pt_kernel<C, BM, BN, BK, TM, TN, Rows>, grid, dim3((BM / TM) * (BN / TN)), 0, s, \
+                   S, P, M, d, rows);                                                                      \
   } while (0)
   switch (d) {
     case 2: QPE_GEMM(256, 2, 2, 2, 1); break;
@@ -517,7 +554,7 @@ static int launch_rows_times_pt(C* S, const C* P, int64_t M, int d, Rows rows, c
     default: QPE_GEMM(64, 64, 8, 4, 4); break;
   }
 #undef QPE_GEMM
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return err == cudaSuccess ? 1 : -1;
 }
 
 template <typename C>
@@ -529,9 +566,9 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s) {
   const double scale = 1.0 / sqrt(ldexp(1.0, in.nmeas));  // Hadamard layer: 2^(-n/2)
   int launches = 0;
   const int64_t init_rows = gate_mode ? in.N : 1;
-  init_rows_kernel<C><<<grid_for(init_rows << logd, 256), 256, 0, s>>>(S, at<double2>(ws, in.off_psi), init_rows,
-                                                                        logd, scale);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (launch_k(init_rows_kernel<C>, dim3(grid_for(init_rows << logd, 256)), dim3(256), 0, s, S,
+               (const double2*)at<double2>(ws, in.off_psi), init_rows, logd, scale) != cudaSuccess)
+    return -1;
   ++launches;
   for (int j = 0; j < in.nmeas; ++j) {
     int r;
@@ -603,8 +640,8 @@ int launch_fft(const Instance& in, char* ws, cudaStream_t s) {
     a.scale = a.last ? final_scale : 1.0;
     const int64_t blocks = p.B * (p.Q / p.W);
     const size_t smem = (size_t)(int64_t(1) << p.logr) * p.W * sizeof(C);
-    fft_pass_kernel<C><<<(unsigned)blocks, 256, smem, s>>>(X, lo, hi, a);
-    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    if (launch_k(fft_pass_kernel<C>, dim3((unsigned)blocks), dim3(256), smem, s, X, lo, hi, a) != cudaSuccess)
+      return -1;
     ++launches;
   }
   return launches;
@@ -616,27 +653,29 @@ int launch_reduce(const Instance& in, char* ws, cudaStream_t s) {
   const int64_t rows_per_block_step = 8 * (32 / (in.d < 32 ? in.d : 32));
   int blocks = (int)std::min<int64_t>(kReduceBlocks, (in.N + rows_per_block_step - 1) / rows_per_block_step);
   if (blocks < 1) blocks = 1;
-  reduce_kernel<C><<<blocks, 256, 0, s>>>(at<C>(ws, in.off_state), at<double>(ws, in.off_hist),
-                                          at<Partial>(ws, in.off_partials), in.N, in.nmat, in.nmeas, g, 1.0);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  finalize_kernel<<<1, 256, 0, s>>>(at<Partial>(ws, in.off_partials), blocks, at<Scalars>(ws, in.off_scalars),
-                                    in.nmeas);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (launch_k(reduce_kernel<C>, dim3(blocks), dim3(256), 0, s, (const C*)at<C>(ws, in.off_state),
+               at<double>(ws, in.off_hist), at<Partial>(ws, in.off_partials), in.N, in.nmat, in.nmeas, g,
+               1.0) != cudaSuccess)
+    return -1;
+  if (launch_finalize(in, ws, blocks, s) < 0) return -1;
   return 2;
 }
 
 int launch_finalize(const Instance& in, char* ws, int count, cudaStream_t s) {
-  finalize_kernel<<<1, 256, 0, s>>>(at<Partial>(ws, in.off_partials), count, at<Scalars>(ws, in.off_scalars),
-                                    in.nmeas);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_k(finalize_kernel, dim3(1), dim3(256), 0, s, (const Partial*)at<Partial>(ws, in.off_partials), count,
+                  at<Scalars>(ws, in.off_scalars), in.nmeas) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 template <typename C>
 int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s) {
   const Digits g = digits_of(in.fft);
-  unpermute_kernel<C><<<grid_for(in.N * in.d, 256), 256, 0, s>>>(
-      reinterpret_cast<const C*>(ws + in.off_state), reinterpret_cast<C*>(out), in.N, in.nmat, in.nmeas, g);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_k(unpermute_kernel<C>, dim3(grid_for(in.N * in.d, 256)), dim3(256), 0, s,
+                  reinterpret_cast<const C*>(ws + in.off_state), reinterpret_cast<C*>(out), in.N, in.nmat, in.nmeas,
+                  g) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 // Dynamic shared memory above 48 KiB needs an opt-in per kernel.

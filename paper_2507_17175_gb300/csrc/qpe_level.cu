@@ -186,22 +186,76 @@ struct Acc<double2> {
 // gives (L_max d / TR) (G / TG) = 256 GEMM units and stays under ~100 KiB.
 struct LvCfg {
   int logl, G, TR, TG;
-  bool tab_smem;
+  bool tab_smem;  // final level: whole table resident in shared memory
+  int DI0, G0;    // other levels: columns per CTA (table slice in shared memory), pencils per iteration
 };
 
 __host__ __device__ constexpr LvCfg lv_cfg(int logd, bool dbl) {
-  return dbl ? (logd == 1   ? LvCfg{5, 32, 2, 4, true}
-                : logd == 2 ? LvCfg{5, 16, 4, 2, true}
-                : logd == 3 ? LvCfg{4, 16, 4, 2, true}
-                : logd == 4 ? LvCfg{3, 16, 4, 2, true}
-                : logd == 5 ? LvCfg{3, 8, 4, 2, false}
-                            : LvCfg{2, 8, 4, 2, false})
-             : (logd == 1   ? LvCfg{5, 64, 2, 8, true}
-                : logd == 2 ? LvCfg{5, 32, 4, 4, true}
-                : logd == 3 ? LvCfg{5, 16, 4, 4, true}
-                : logd == 4 ? LvCfg{4, 16, 4, 4, true}
-                : logd == 5 ? LvCfg{3, 16, 4, 4, false}
-                            : LvCfg{3, 8, 4, 4, false});
+  return dbl ? (logd == 1   ? LvCfg{5, 32, 2, 4, true, 2, 32}
+                : logd == 2 ? LvCfg{5, 16, 4, 2, true, 4, 16}
+                : logd == 3 ? LvCfg{4, 16, 4, 2, true, 8, 16}
+                : logd == 4 ? LvCfg{3, 16, 4, 2, true, 8, 32}
+                : logd == 5 ? LvCfg{3, 8, 4, 2, false, 8, 32}
+                            : LvCfg{2, 8, 4, 2, false, 8, 32})
+             : (logd == 1   ? LvCfg{5, 64, 2, 8, true, 2, 64}
+                : logd == 2 ? LvCfg{5, 32, 4, 4, true, 4, 32}
+                : logd == 3 ? LvCfg{5, 16, 4, 4, true, 8, 16}
+                : logd == 4 ? LvCfg{4, 16, 4, 4, true, 8, 32}
+                : logd == 5 ? LvCfg{3, 16, 4, 4, false, 8, 64}
+                            : LvCfg{4, 8, 4, 4, false, 8, 32});
+}
+
+// Per-MODE view of the configuration: the final level (MODE 1/2) takes whole
+// rows (the histogram sums over all d columns); the others take DI0 columns.
+template <int LOGD, bool DBL, int MODE>
+struct LvShape {
+  static constexpr LvCfg c = lv_cfg(LOGD, DBL);
+  static constexpr int D = 1 << LOGD;
+  static constexpr int DI = MODE == 0 ? c.DI0 : D;
+  static constexpr int G = MODE == 0 ? c.G0 : c.G;
+  static constexpr int LMAX = 1 << c.logl;
+  static constexpr bool TAB_SMEM = MODE == 0 ? true : c.tab_smem;
+  static constexpr size_t smem(size_t esize) {
+    const size_t acc = esize == 8 ? 4 : 8;
+    size_t b = (size_t)G * LMAX * DI * esize + (size_t)G * D * esize + (size_t)G * LMAX * esize;
+    if (TAB_SMEM) b += (size_t)D * LMAX * DI * esize;
+    if (MODE != 0) b += (size_t)LMAX * D * (G + 1) * acc;
+    return b;
+  }
+};
+
+// 4 consecutive complex values through 16-byte accesses
+__device__ __forceinline__ void load4(const float2* p, float2 (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 2);
+  v[0] = make_float2(a.x, a.y);
+  v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y);
+  v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const double2* p, double2 (&v)[4]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) v[t] = p[t];
+}
+__device__ __forceinline__ void ldg4(const float2* p, float2 (&v)[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p + 2));
+  v[0] = make_float2(a.x, a.y);
+  v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y);
+  v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void ldg4(const double2* p, double2 (&v)[4]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) v[t] = __ldg(p + t);
+}
+__device__ __forceinline__ void store4(float2* p, const float2 (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  *reinterpret_cast<float4*>(p + 2) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+__device__ __forceinline__ void store4(double2* p, const double2 (&v)[4]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) p[t] = v[t];
 }
 
 template <typename C, int K, int N>
@@ -250,25 +304,37 @@ __device__ __forceinline__ void dft_r(C (&x)[N], int r) {
 // ------------------------------------------------------------------ kernel
 template <typename C, int LOGD, int MODE>
 __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(LevelArgs<C> a) {
+  pdl_begin();
   using R_t = typename real_of<C>::type;
   using A_t = typename Acc<C>::T;
-  constexpr LvCfg cfg = lv_cfg(LOGD, sizeof(C) == 16);
-  constexpr int D = 1 << LOGD, G = cfg.G, TR = cfg.TR, TG = cfg.TG;
-  constexpr int LMAX = 1 << cfg.logl;
+  using S = LvShape<LOGD, sizeof(C) == 16, MODE>;
+  constexpr LvCfg cfg = S::c;
+  constexpr int D = S::D, DI = S::DI, G = S::G, TR = cfg.TR, TG = cfg.TG, LMAX = S::LMAX;
+  constexpr int NCG = D / DI;  // column groups
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = a.r;
   const int L = 1 << r;
-  const int ROWS = L * D;
-  C* T = reinterpret_cast<C*>(smem_raw);        // [G][L][D]
-  C* Zs = T + G * LMAX * D;                      // [G][D]
-  C* twS = Zs + G * D;                           // [G][L]
-  C* tabS = twS + G * LMAX;                      // [D][L D] (tab_smem)
-  A_t* sq = reinterpret_cast<A_t*>(tabS + (cfg.tab_smem ? D * LMAX * D : 0));  // [L][D][G+1]
-  const C* tab = cfg.tab_smem ? tabS : a.tab;
+  const int ROWS = L * DI;  // GEMM rows of this CTA: (m_b, column in group)
+  C* T = reinterpret_cast<C*>(smem_raw);  // [G][L][DI]
+  C* ZsT = T + G * LMAX * DI;             // [D][G]  (k-major: seeds of the G pencils)
+  C* twS = ZsT + G * D;                   // [G][L]
+  C* tabS = twS + G * LMAX;               // [D][L DI] (TAB_SMEM)
+  A_t* sq = reinterpret_cast<A_t*>(tabS + (S::TAB_SMEM ? D * LMAX * DI : 0));  // [L][D][G+1] (MODE != 0)
+  const C* tab = S::TAB_SMEM ? tabS : a.tab;
+  const int tab_ld = S::TAB_SMEM ? ROWS : L * D;  // row stride (per k) of the table in use
   const int tid = threadIdx.x;
 
-  if (cfg.tab_smem)
-    for (int e = tid; e < D * ROWS; e += blockDim.x) tabS[e] = ldg(a.tab + e);
+  const int cg = (int)(blockIdx.x % NCG);  // this CTA's column group
+  const int i_base = cg * DI;
+  const int tab_col0 = S::TAB_SMEM ? 0 : i_base;
+  if (S::TAB_SMEM) {
+    // slice: tabS[k][m_b DI + ii] = tab[k][m_b D + i_base + ii]
+    for (int e = tid; e < D * ROWS; e += blockDim.x) {
+      const int k = e / ROWS, rr = e - k * ROWS;
+      const int mb = rr / DI, ii = rr - mb * DI;
+      tabS[e] = ldg(a.tab + (int64_t)k * (L * D) + mb * D + i_base + ii);
+    }
+  }
 
   const int64_t Na = int64_t(1) << a.logna;
   const int64_t iters = (Na + G - 1) / G;
@@ -279,12 +345,14 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
   int64_t besty = INT64_MAX;
   float wsum_f = 0.f, wcomp_f = 0.f, psum_f = 0.f, pcomp_f = 0.f;
 
-  for (int64_t it = blockIdx.x; it < iters; it += gridDim.x) {
+  const int64_t it0 = blockIdx.x / NCG, itstep = gridDim.x / NCG;
+  for (int64_t it = it0; it < iters; it += itstep) {
     const int64_t ya0 = it * G;
-    __syncthreads();  // previous iteration's buffers consumed
+    const int gvalid = (int)(Na - ya0 < G ? Na - ya0 : G);
+    __syncthreads();  // previous iteration's buffers consumed (and the table slice loaded)
     for (int e = tid; e < G * D; e += blockDim.x) {
-      const int g = e >> LOGD;
-      Zs[e] = (ya0 + g < Na) ? ldg(a.seeds + ((ya0 + g) << LOGD) + (e & (D - 1))) : czero<C>();
+      const int g = e / D, k = e - g * D;
+      ZsT[k * G + g] = (g < gvalid) ? ldg(a.seeds + ((ya0 + g) << LOGD) + k) : czero<C>();
     }
     for (int e = tid; e < G * L; e += blockDim.x) {
       const int g = e >> r, mb = e & (L - 1);
@@ -294,14 +362,17 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
       twS[e] = w;
     }
     __syncthreads();
-    // T[g][m_b][i] = w^(m_b y_a) sum_k M[m_b][i][k] Z[g][k]
+    // T[g][m_b][ii] = w^(m_b y_a) sum_k M[m_b][i_base + ii][k] Z[g][k]
     {
       const int nrg = ROWS / TR;
-      const int units = nrg * (G / TG);
+      const int ngg = (gvalid + TG - 1) / TG;
+      const int units = nrg * ngg;
       for (int u = tid; u < units; u += blockDim.x) {
         const int rg = u % nrg, gg = u / nrg;
-        const int row0 = rg * TR;
-        const int mb = row0 >> LOGD;
+        const int row0 = rg * TR;  // (m_b, ii) row in this CTA's numbering
+        const int mb = row0 / DI;
+        const int ii0 = row0 - mb * DI;
+        const int trow = S::TAB_SMEM ? row0 : mb * D + tab_col0 + ii0;
         C acc[TR][TG];
 #pragma unroll
         for (int t = 0; t < TR; ++t)
@@ -310,11 +381,23 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
 #pragma unroll 4
         for (int k = 0; k < D; ++k) {
           C av[TR], zv[TG];
-          const C* tp = tab + k * ROWS + row0;
+          const C* tp = tab + k * tab_ld + trow;
+          if constexpr (TR == 4) {
+            if (S::TAB_SMEM)
+              load4(tp, av);
+            else
+              ldg4(tp, av);
+          } else {
 #pragma unroll
-          for (int t = 0; t < TR; ++t) av[t] = cfg.tab_smem ? tp[t] : ldg(tp + t);
+            for (int t = 0; t < TR; ++t) av[t] = S::TAB_SMEM ? tp[t] : ldg(tp + t);
+          }
+          const C* zp = ZsT + k * G + gg * TG;
+          if constexpr (TG == 4) {
+            load4(zp, zv);
+          } else {
 #pragma unroll
-          for (int g = 0; g < TG; ++g) zv[g] = Zs[(gg * TG + g) * D + k];
+            for (int g = 0; g < TG; ++g) zv[g] = zp[g];
+          }
 #pragma unroll
           for (int t = 0; t < TR; ++t)
 #pragma unroll
@@ -324,33 +407,39 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
         for (int g = 0; g < TG; ++g) {
           const int gi = gg * TG + g;
           const C w = twS[gi * L + mb];
-          C* out = T + (gi * L) * D + row0;
+          C* out = T + (gi * L + mb) * DI + ii0;
+          if constexpr (TR == 4) {
+            C ov[4];
 #pragma unroll
-          for (int t = 0; t < TR; ++t) out[t] = cmul(acc[t][g], w);
+            for (int t = 0; t < 4; ++t) ov[t] = cmul(acc[t][g], w);
+            store4(out, ov);
+          } else {
+#pragma unroll
+            for (int t = 0; t < TR; ++t) out[t] = cmul(acc[t][g], w);
+          }
         }
       }
     }
     __syncthreads();
     // length-L DFT over m_b for every (g, column)
-    for (int p = tid; p < G * D; p += blockDim.x) {
-      const int g = p >> LOGD, i = p & (D - 1);
+    for (int p = tid; p < gvalid * DI; p += blockDim.x) {
+      const int g = p / DI, ii = p - g * DI;
       C x[LMAX];
 #pragma unroll
       for (int m = 0; m < LMAX; ++m)
-        if (m < L) x[m] = T[(g * L + m) * D + i];
+        if (m < L) x[m] = T[(g * L + m) * DI + ii];
       dft_r<C, LMAX>(x, r);
       const int64_t ya = ya0 + g;
+      const int i = i_base + ii;
       if (MODE == 0) {
-        if (ya < Na) {
 #pragma unroll
-          for (int yb = 0; yb < LMAX; ++yb)
-            if (yb < L) a.xout[((ya + ((int64_t)yb << a.logna)) << LOGD) + i] = x[yb];
-        }
+        for (int yb = 0; yb < LMAX; ++yb)
+          if (yb < L) a.xout[((ya + ((int64_t)yb << a.logna)) << LOGD) + i] = x[yb];
       } else {
 #pragma unroll
         for (int yb = 0; yb < LMAX; ++yb)
           if (yb < L) sq[(yb * D + i) * (G + 1) + g] = (A_t)x[yb].x * (A_t)x[yb].x + (A_t)x[yb].y * (A_t)x[yb].y;
-        if (MODE == 2 && ya < Na) {
+        if (MODE == 2) {
 #pragma unroll
           for (int yb = 0; yb < LMAX; ++yb)
             if (yb < L) a.xout[((ya + ((int64_t)yb << a.logna)) << LOGD) + i] = cscale(x[yb], (R_t)a.xscale);
@@ -361,8 +450,8 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
       __syncthreads();
       for (int q = tid; q < G * L; q += blockDim.x) {
         const int g = q % G, yb = q / G;
+        if (g >= gvalid) continue;
         const int64_t ya = ya0 + g;
-        if (ya >= Na) continue;
         A_t s = 0;
 #pragma unroll 8
         for (int i = 0; i < D; ++i) s += sq[(yb * D + i) * (G + 1) + g];
@@ -429,79 +518,112 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
       a.parts[blockIdx.x] = res;
     }
   }
+  pdl_trigger();
 }
 
 // Level tables: tab_l[k][m_b d + i] = (U_l^(m_b))[i][k], U_l = P_(off_l), for
-// m_b < 2^(r_l). One warp per (level, m_b, i): the row e_i^T prod P_(off+j)
-// over the set bits j of m_b, as a chain of vector-matrix products.
+// m_b < 2^(r_l). One CTA per (level, m_b, block of TB rows): the rows
+// e_i^T prod_{j in bits(m_b)} P_(off+j) as a chain of (TB x d) x (d x d)
+// products, each factor staged in shared memory.
 template <typename C>
 __global__ void __launch_bounds__(256) level_table_kernel(const C* __restrict__ P, char* __restrict__ ws,
                                                           TableJobs jobs, int logd) {
+  pdl_begin();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int D = 1 << logd;
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t base = 0;
+  const int TB = D < 16 ? D : 16;  // rows per CTA
+  const int nrb = D / TB;
+  C* Pb = reinterpret_cast<C*>(smem_raw);  // D x D factor
+  C* V = Pb + D * D;                        // TB x D running rows
+  C* Vn = V + TB * D;
+  // locate (level, m_b, row block)
+  int64_t b = blockIdx.x;
   int li = -1;
   for (int l = 0; l < jobs.count; ++l) {
-    const int64_t rows = (int64_t(1) << jobs.r[l]) << logd;
-    if (w < base + rows) {
+    const int64_t cnt = (int64_t(1) << jobs.r[l]) * nrb;
+    if (b < cnt) {
       li = l;
       break;
     }
-    base += rows;
+    b -= cnt;
   }
   if (li < 0) return;
-  const int row = (int)(w - base);
-  const int mb = row >> logd, i = row & (D - 1);
-  const int L = 1 << jobs.r[li];
-  C* tab = reinterpret_cast<C*>(ws + jobs.tab_off[li]);
+  const int mb = (int)(b / nrb), rb = (int)(b % nrb);
+  const int i0 = rb * TB;
   const int64_t DD = (int64_t)D * D;
-  // v: lane holds columns k = lane, lane + 32 (D <= 64)
-  C v0 = czero<C>(), v1 = czero<C>();
+  const int tid = threadIdx.x;
   bool started = false;
   for (int j = 0; j < jobs.r[li]; ++j) {
     if (!((mb >> j) & 1)) continue;
     const C* Pj = P + (int64_t)(jobs.off[li] + j) * DD;
     if (!started) {
-      if (lane < D) v0 = ldg(Pj + (int64_t)i * D + lane);
-      if (lane + 32 < D) v1 = ldg(Pj + (int64_t)i * D + lane + 32);
+      for (int e = tid; e < TB * D; e += blockDim.x) V[e] = ldg(Pj + (int64_t)i0 * D + e);
       started = true;
       continue;
     }
-    C n0 = czero<C>(), n1 = czero<C>();
-    for (int l = 0; l < D; ++l) {
-      const C vl = l < 32 ? mk(__shfl_sync(0xffffffffu, v0.x, l), __shfl_sync(0xffffffffu, v0.y, l))
-                          : mk(__shfl_sync(0xffffffffu, v1.x, l - 32), __shfl_sync(0xffffffffu, v1.y, l - 32));
-      if (lane < D) cfma(n0, vl, ldg(Pj + (int64_t)l * D + lane));
-      if (lane + 32 < D) cfma(n1, vl, ldg(Pj + (int64_t)l * D + lane + 32));
+    __syncthreads();
+    for (int e = tid; e < D * D; e += blockDim.x) Pb[e] = ldg(Pj + e);
+    __syncthreads();
+    // each thread: 4 outputs (row rr, columns k0..k0+3 spaced by D/4), 4 independent chains
+    const int q4 = D >= 4 ? D / 4 : 1;
+    for (int e = tid; e < TB * q4; e += blockDim.x) {
+      const int rr = e / q4, k0 = e - rr * q4;
+      const int nk = D >= 4 ? 4 : D;
+      C acc[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
+#pragma unroll 4
+      for (int l = 0; l < D; ++l) {
+        const C v = V[rr * D + l];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < nk) cfma(acc[t], v, Pb[l * D + k0 + t * q4]);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nk) Vn[rr * D + k0 + t * q4] = acc[t];
     }
-    v0 = n0;
-    v1 = n1;
+    __syncthreads();
+    for (int e = tid; e < TB * D; e += blockDim.x) V[e] = Vn[e];
   }
-  if (!started) {  // m_b = 0: identity row
-    v0 = (lane == i) ? mk((typename real_of<C>::type)1, (typename real_of<C>::type)0) : czero<C>();
-    v1 = (lane + 32 == i) ? mk((typename real_of<C>::type)1, (typename real_of<C>::type)0) : czero<C>();
+  if (!started) {  // m_b = 0: identity rows
+    for (int e = tid; e < TB * D; e += blockDim.x) {
+      const int rr = e / D, k = e - rr * D;
+      V[e] = (k == i0 + rr) ? mk((typename real_of<C>::type)1, (typename real_of<C>::type)0) : czero<C>();
+    }
   }
+  __syncthreads();
+  const int L = 1 << jobs.r[li];
   const int ROWS = L << logd;
-  if (lane < D) tab[(int64_t)lane * ROWS + row] = v0;
-  if (lane + 32 < D) tab[(int64_t)(lane + 32) * ROWS + row] = v1;
+  C* tab = reinterpret_cast<C*>(ws + jobs.tab_off[li]);
+  for (int e = tid; e < TB * D; e += blockDim.x) {
+    const int k = e / TB, rr = e - k * TB;  // consecutive threads: consecutive rows (contiguous in tab)
+    tab[(int64_t)k * ROWS + mb * D + i0 + rr] = V[rr * D + k];
+  }
+  pdl_trigger();
 }
 
 template <typename C>
 __global__ void seed_psi_kernel(const double2* __restrict__ psi, C* __restrict__ out, int d) {
+  pdl_begin();
   for (int i = threadIdx.x; i < d; i += blockDim.x) out[i] = to_c(psi[i], (C*)nullptr);
+  pdl_trigger();
 }
 
 // --------------------------------------------------------------- host side
-size_t level_smem_bytes(int logd, int r, size_t esize) {
-  (void)r;
-  const LvCfg c = lv_cfg(logd, esize == 16);
-  const size_t D = size_t(1) << logd, L = size_t(1) << c.logl;
-  const size_t acc = esize == 8 ? 4 : 8;
-  size_t b = (size_t)c.G * L * D * esize + (size_t)c.G * D * esize + (size_t)c.G * L * esize;
-  if (c.tab_smem) b += D * L * D * esize;
-  b += L * D * (c.G + 1) * acc;
-  return b;
+template <int LD, int M>
+static size_t smem_of(size_t esize) {
+  return esize == 16 ? LvShape<LD, true, M>::smem(esize) : LvShape<LD, false, M>::smem(esize);
+}
+
+size_t level_smem_bytes(int logd, int mode, size_t esize) {
+  const int m = mode == 0 ? 0 : 1;
+  switch (logd) {
+    case 1: return m ? smem_of<1, 1>(esize) : smem_of<1, 0>(esize);
+    case 2: return m ? smem_of<2, 1>(esize) : smem_of<2, 0>(esize);
+    case 3: return m ? smem_of<3, 1>(esize) : smem_of<3, 0>(esize);
+    case 4: return m ? smem_of<4, 1>(esize) : smem_of<4, 0>(esize);
+    case 5: return m ? smem_of<5, 1>(esize) : smem_of<5, 0>(esize);
+    default: return m ? smem_of<6, 1>(esize) : smem_of<6, 0>(esize);
+  }
 }
 
 int level_max_bits(int logd, size_t esize, size_t smem_cap) {
@@ -538,7 +660,7 @@ static cudaError_t set_level_attrs() {
   cudaError_t e;
 #define QPE_ATTR(C, LD, M)                                                                                  \
   e = cudaFuncSetAttribute(level2_kernel<C, LD, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                           (int)level_smem_bytes(LD, 0, sizeof(C)));                                        \
+                           (int)level_smem_bytes(LD, M, sizeof(C)));                                        \
   if (e != cudaSuccess) return e;
   QPE_LV_ALL(QPE_ATTR, float2)
   QPE_LV_ALL(QPE_ATTR, double2)
@@ -547,6 +669,11 @@ static cudaError_t set_level_attrs() {
 }
 
 cudaError_t configure_level_kernels() {
+  {
+    cudaError_t e0 = cudaFuncSetAttribute(level_table_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (64 * 64 + 2 * 16 * 64) * 16);
+    if (e0 != cudaSuccess) return e0;
+  }
   double2 w64[32];
   float2 w32v[32];
   for (int k = 0; k < 32; ++k) {
@@ -565,17 +692,17 @@ cudaError_t configure_level_kernels() {
 template <typename C, int M>
 static void launch_level2(int logd, unsigned grid, size_t smem, cudaStream_t s, const LevelArgs<C>& a) {
   switch (logd) {
-    case 1: level2_kernel<C, 1, M><<<grid, 256, smem, s>>>(a); break;
-    case 2: level2_kernel<C, 2, M><<<grid, 256, smem, s>>>(a); break;
-    case 3: level2_kernel<C, 3, M><<<grid, 256, smem, s>>>(a); break;
-    case 4: level2_kernel<C, 4, M><<<grid, 256, smem, s>>>(a); break;
-    case 5: level2_kernel<C, 5, M><<<grid, 256, smem, s>>>(a); break;
-    default: level2_kernel<C, 6, M><<<grid, 256, smem, s>>>(a); break;
+    case 1: launch_k(level2_kernel<C, 1, M>, dim3(grid), dim3(256), smem, s, a); break;
+    case 2: launch_k(level2_kernel<C, 2, M>, dim3(grid), dim3(256), smem, s, a); break;
+    case 3: launch_k(level2_kernel<C, 3, M>, dim3(grid), dim3(256), smem, s, a); break;
+    case 4: launch_k(level2_kernel<C, 4, M>, dim3(grid), dim3(256), smem, s, a); break;
+    case 5: launch_k(level2_kernel<C, 5, M>, dim3(grid), dim3(256), smem, s, a); break;
+    default: launch_k(level2_kernel<C, 6, M>, dim3(grid), dim3(256), smem, s, a); break;
   }
 }
 
 template <typename C>
-int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s) {
+int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s, cudaEvent_t* top_ev) {
   const size_t esize = sizeof(C);
   const C* P = reinterpret_cast<const C*>(ws + (esize == 16 ? in.off_pow64 : in.off_pow32));
   const C* tlo = reinterpret_cast<const C*>(ws + (esize == 16 ? in.off_tw_lo64 : in.off_tw_lo32));
@@ -586,24 +713,27 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s)
   {
     TableJobs jobs{};
     jobs.count = nl;
-    int64_t warps = 0;
+    const int D = (int)in.d;
+    const int TB = D < 16 ? D : 16;
+    int64_t blocks = 0;
     for (int li = 0; li < nl; ++li) {
       jobs.off[li] = in.levels[li].off;
       jobs.r[li] = in.levels[li].r;
       jobs.tab_off[li] = in.levels[li].tab_off;
-      warps += (int64_t(1) << in.levels[li].r) << in.nmat;
+      blocks += (int64_t(1) << in.levels[li].r) * (D / TB);
     }
-    const int64_t blocks = (warps * 32 + 255) / 256;
-    level_table_kernel<C><<<(unsigned)blocks, 256, 0, s>>>(P, ws, jobs, in.nmat);
-    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    const size_t smem = ((size_t)D * D + 2 * (size_t)TB * D) * esize;
+    if (launch_k(level_table_kernel<C>, dim3((unsigned)blocks), dim3(256), smem, s, P, ws, jobs, in.nmat) !=
+        cudaSuccess)
+      return -1;
     ++launches;
   }
   C* seed = reinterpret_cast<C*>(ws + in.zbuf_seed_off);
-  seed_psi_kernel<C><<<1, 64, 0, s>>>(reinterpret_cast<const double2*>(ws + in.off_psi), seed, (int)in.d);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (launch_k(seed_psi_kernel<C>, dim3(1), dim3(64), 0, s, reinterpret_cast<const double2*>(ws + in.off_psi), seed,
+               (int)in.d) != cudaSuccess)
+    return -1;
   ++launches;
   const LvCfg cfg = lv_cfg(in.nmat, esize == 16);
-  const size_t smem = level_smem_bytes(in.nmat, 0, esize);
   const C* cur_seed = seed;
   for (int li = nl - 1; li >= 0; --li) {
     const Level& L = in.levels[li];
@@ -622,17 +752,25 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s)
     a.inv_n = ldexp(1.0, -in.nmeas);
     a.xscale = 1.0;
     const int64_t Na = int64_t(1) << L.logna;
-    const int64_t iters = (Na + cfg.G - 1) / cfg.G;
-    int64_t grid = iters < in.level_grid ? iters : in.level_grid;
     if (li > 0) {
+      // column groups x pencil groups; the grid is a multiple of the group count
+      const int64_t ncg = in.d / cfg.DI0;
+      const int64_t iters = (Na + cfg.G0 - 1) / cfg.G0;
+      int64_t per = in.level_grid / ncg;
+      if (per < 1) per = 1;
+      if (per > iters) per = iters;
       C* out = reinterpret_cast<C*>(ws + in.off_zbuf[li & 1]);
       a.xout = out;
-      launch_level2<C, 0>(in.nmat, (unsigned)grid, smem, s, a);
+      launch_level2<C, 0>(in.nmat, (unsigned)(per * ncg), level_smem_bytes(in.nmat, 0, esize), s, a);
       cur_seed = out;
     } else {
+      const size_t smem = level_smem_bytes(in.nmat, 1, esize);
+      const int64_t iters = (Na + cfg.G - 1) / cfg.G;
+      int64_t grid = iters < in.level_grid ? iters : in.level_grid;
       a.hist = reinterpret_cast<double*>(ws + in.off_hist);
       a.parts = reinterpret_cast<Partial*>(ws + in.off_partials);
       if (grid > kReduceBlocks) grid = kReduceBlocks;
+      if (top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
       if (keep_state) {
         a.xout = reinterpret_cast<C*>(ws + in.off_state);
         a.xscale = ldexp(1.0, -in.nmeas);  // physical final state: X / N
@@ -642,6 +780,7 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s)
       }
       if (cudaPeekAtLastError() != cudaSuccess) return -1;
       ++launches;
+      if (top_ev && record_event(top_ev[1], s) != cudaSuccess) return -1;
       finalize_readout(in, ws, (int)grid, s);
       if (cudaPeekAtLastError() != cudaSuccess) return -1;
       ++launches;
@@ -657,7 +796,7 @@ template <typename C>
 int level_occupancy(int logd, int r) {
   (void)r;
   int blocks = 0;
-  const size_t smem = level_smem_bytes(logd, 0, sizeof(C));
+  const size_t smem = level_smem_bytes(logd, 1, sizeof(C));
   cudaError_t e;
   switch (logd) {
     case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, level2_kernel<C, 1, 1>, 256, smem); break;
@@ -673,7 +812,7 @@ int level_occupancy(int logd, int r) {
 template int level_occupancy<float2>(int, int);
 template int level_occupancy<double2>(int, int);
 
-template int launch_levels<float2>(const Instance&, char*, bool, cudaStream_t);
-template int launch_levels<double2>(const Instance&, char*, bool, cudaStream_t);
+template int launch_levels<float2>(const Instance&, char*, bool, cudaStream_t, cudaEvent_t*);
+template int launch_levels<double2>(const Instance&, char*, bool, cudaStream_t, cudaEvent_t*);
 
 }  // namespace qpe

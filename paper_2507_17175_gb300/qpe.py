@@ -60,6 +60,7 @@ _sig = {
     "qpe_query": (ctypes.c_int64, [_vp, _i32]),
     "qpe_sync": (ctypes.c_int, [_vp]),
     "qpe_stage_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "qpe_kernel_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "qpe_destroy": (ctypes.c_int, [_vp]),
     "qpe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qpe_last_error": (ctypes.c_char_p, [_vp]),
@@ -204,6 +205,14 @@ class Plan:
         ms = (ctypes.c_double * 4)()
         self._check(_lib.qpe_stage_times(self._h, ms), "qpe_stage_times")
         return list(ms)
+
+    def kernel_time(self):
+        """(ms, kernel id) of the last run's dominant kernel (FLAG_TIMING);
+        id 1 = the top level of the fused schedule, 0 = not timed."""
+        ms = ctypes.c_double(0.0)
+        kid = ctypes.c_int32(0)
+        self._check(_lib.qpe_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(kid)), "qpe_kernel_time")
+        return ms.value, kid.value
 
     def close(self):
         if getattr(self, "_h", None):
