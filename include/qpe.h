@@ -119,6 +119,20 @@ typedef enum {
 qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan_t* out);
 
 /*
+ * qpe_plan_batched: one plan for `count` independent problems of uneven
+ * nmat/nmeas (descs[i]; all with the same prec and flags; GATE_SWEEP and
+ * TIMING are not available here, QPE_ERR_UNSUPPORTED). Instances are
+ * addressed by index 0..count-1 in qpe_load / qpe_probs / qpe_state. A run
+ * groups the work across instances: one launch per U^(2^k) squaring step for
+ * every instance that needs it, and for nmat <= 6 grouped table, level and
+ * readout launches whose CTAs walk a work list of (instance, level, column
+ * group, pencil range) items built at qpe_bind; nmat > 6 instances run the
+ * plain schedule one after another in the same stream (and graph). Only whole
+ * runs (qpe_run) are supported. Host only, like qpe_plan.
+ */
+qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* workspace_bytes, qpe_plan_t* out);
+
+/*
  * qpe_bind: attach caller-owned device memory and a CUDA stream (a
  * cudaStream_t, or NULL for the legacy default stream) to a plan. The
  * workspace must stay allocated until qpe_destroy or the next qpe_bind, be

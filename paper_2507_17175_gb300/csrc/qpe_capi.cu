@@ -132,7 +132,14 @@ namespace {
 using qpe::record_event;
 
 // Enqueue stages first..last for every instance; returns launches or sets error.
+qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches);
+
 qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) {
+  if (p->batched) {
+    if (first != QPE_STAGE_POWERS || last != QPE_STAGE_REDUCE)
+      return fail(p, QPE_ERR_UNSUPPORTED, "batched plans run whole (POWERS..REDUCE) only");
+    return enqueue_batched(p, launches);
+  }
   int64_t n = 0;
   const bool c64 = is_c64(p->prec);
   const bool gate = (p->flags & QPE_FLAG_GATE_SWEEP) != 0;
@@ -220,6 +227,316 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
   return QPE_OK;
 }
 
+
+// (Re)builds a batched plan's work lists. With ws == nullptr only the counts
+// matter (plan time, for sizing); at bind the device pointers are filled in.
+void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
+  qpe::BatchMeta& bm = p->bm;
+  const bool c64 = is_c64(p->prec);
+  const size_t esize = elem_size(p->prec);
+  bm.sq.clear();
+  bm.conv.clear();
+  bm.fused.clear();
+  bm.plain.clear();
+  bm.tab_items.clear();
+  bm.seed_items.clear();
+  bm.level_args.clear();
+  bm.items.clear();
+  bm.launches.clear();
+  bm.fin.clear();
+  bm.maxn = 0;
+  for (const Instance& in : p->inst) bm.maxn = std::max(bm.maxn, in.nmeas);
+  bm.sq_begin.assign(bm.maxn + 1, 0);
+  bm.sq_count.assign(bm.maxn + 1, 0);
+  bm.sq_tiles.assign(bm.maxn + 1, 0);
+  for (int k = 1; k < bm.maxn; ++k) {
+    bm.sq_begin[k] = (int)bm.sq.size();
+    int64_t tiles = 0;
+    for (Instance& in : p->inst) {
+      if (in.nmeas <= k) continue;
+      const int64_t dd = in.d * in.d;
+      double2* P = reinterpret_cast<double2*>(ws + in.off_pow64);
+      float2* P32 = c64 ? reinterpret_cast<float2*>(ws + in.off_pow32) : nullptr;
+      qpe::SqItem it{};
+      it.A = P + (k - 1) * dd;
+      it.C = P + k * dd;
+      it.C32 = P32 ? P32 + k * dd : nullptr;
+      it.A32 = (P32 && k == 1) ? P32 : nullptr;
+      it.d = (int)in.d;
+      it.tile0 = tiles;
+      tiles += ((in.d + 7) / 8) * ((in.d + 7) / 8);
+      bm.sq.push_back(it);
+    }
+    bm.sq_count[k] = (int)bm.sq.size() - bm.sq_begin[k];
+    bm.sq_tiles[k] = tiles;
+  }
+  bm.conv_tiles = 0;
+  if (c64)
+    for (Instance& in : p->inst)
+      if (in.nmeas == 1) {
+        qpe::SqItem it{};
+        it.A = reinterpret_cast<double2*>(ws + in.off_pow64);
+        it.A32 = reinterpret_cast<float2*>(ws + in.off_pow32);
+        it.d = (int)in.d;
+        it.tile0 = bm.conv_tiles;
+        bm.conv_tiles += (in.d * in.d + 255) / 256;
+        bm.conv.push_back(it);
+      }
+  for (size_t i = 0; i < p->inst.size(); ++i) (p->inst[i].fused ? bm.fused : bm.plain).push_back((int)i);
+  // tables and seeds of the fused instances
+  bm.ntab = 0;
+  bm.tab_blocks = 0;
+  bm.max_logd = 1;
+  bm.nseed = 0;
+  auto push_bytes = [](std::vector<char>& v, const void* src, size_t n) {
+    const size_t o = v.size();
+    v.resize(o + n);
+    std::memcpy(v.data() + o, src, n);
+  };
+  for (int i : bm.fused) {
+    const Instance& in = p->inst[i];
+    bm.max_logd = std::max(bm.max_logd, in.nmat);
+    const int D = (int)in.d, TB = D < 16 ? D : 16;
+    for (const qpe::Level& L : in.levels) {
+      if (c64) {
+        qpe::TabItem<float2> t{};
+        t.P = reinterpret_cast<const float2*>(ws + in.off_pow32);
+        t.tab = reinterpret_cast<float2*>(ws + L.tab_off);
+        t.off = L.off;
+        t.r = L.r;
+        t.logd = in.nmat;
+        t.tile0 = bm.tab_blocks;
+        push_bytes(bm.tab_items, &t, sizeof(t));
+      } else {
+        qpe::TabItem<double2> t{};
+        t.P = reinterpret_cast<const double2*>(ws + in.off_pow64);
+        t.tab = reinterpret_cast<double2*>(ws + L.tab_off);
+        t.off = L.off;
+        t.r = L.r;
+        t.logd = in.nmat;
+        t.tile0 = bm.tab_blocks;
+        push_bytes(bm.tab_items, &t, sizeof(t));
+      }
+      bm.tab_blocks += (int64_t(1) << L.r) * (D / TB);
+      ++bm.ntab;
+    }
+    if (c64) {
+      qpe::SeedItem<float2> sd{reinterpret_cast<const double2*>(ws + in.off_psi),
+                               reinterpret_cast<float2*>(ws + in.zbuf_seed_off), D, 0};
+      push_bytes(bm.seed_items, &sd, sizeof(sd));
+    } else {
+      qpe::SeedItem<double2> sd{reinterpret_cast<const double2*>(ws + in.off_psi),
+                                reinterpret_cast<double2*>(ws + in.zbuf_seed_off), D, 0};
+      push_bytes(bm.seed_items, &sd, sizeof(sd));
+    }
+    ++bm.nseed;
+  }
+  // level rounds, deepest first; one grouped launch per (round, d, top/other)
+  int maxl = 0;
+  for (int i : bm.fused) maxl = std::max(maxl, (int)p->inst[i].levels.size());
+  std::vector<int> part_count(p->inst.size(), 0);
+  const size_t asz = c64 ? sizeof(qpe::LevelArgs<float2>) : sizeof(qpe::LevelArgs<double2>);
+  for (int t = 0; t < maxl; ++t) {
+    for (int top = 0; top < 2; ++top) {
+      for (int logd = 1; logd <= QPE_MAX_FUSED_NMAT; ++logd) {
+        qpe::LevelLaunch LL{};
+        LL.logd = logd;
+        LL.arg_off = (int)(bm.level_args.size() / asz);
+        LL.item_off = (int)bm.items.size();
+        int nargs = 0;
+        for (int i : bm.fused) {
+          Instance& in = p->inst[i];
+          const int nl = (int)in.levels.size();
+          if (in.nmat != logd || t >= nl) continue;
+          const int li = nl - 1 - t;
+          if ((li == 0) != (top == 1)) continue;
+          const int mode = li == 0 ? (in.keep_state ? 2 : 1) : 0;
+          LL.mode = mode;
+          const qpe::Level& L = in.levels[li];
+          char* seeds = (li == nl - 1) ? ws + in.zbuf_seed_off : ws + in.off_zbuf[(li + 1) & 1];
+          char* P = ws + (c64 ? in.off_tw_lo32 : in.off_tw_lo64);
+          char* Ph = ws + (c64 ? in.off_tw_hi32 : in.off_tw_hi64);
+          char* xout = li > 0 ? ws + in.off_zbuf[li & 1] : (in.keep_state ? ws + in.off_state : nullptr);
+          const double xscale = (li == 0 && in.keep_state) ? ldexp(1.0, -in.nmeas) : 1.0;
+#define QPE_FILL_ARGS(CT)                                                   \
+  {                                                                         \
+    qpe::LevelArgs<CT> a{};                                                 \
+    a.seeds = reinterpret_cast<const CT*>(seeds);                           \
+    a.tab = reinterpret_cast<const CT*>(ws + L.tab_off);                    \
+    a.off = L.off;                                                          \
+    a.r = L.r;                                                              \
+    a.logna = L.logna;                                                      \
+    a.logd = in.nmat;                                                       \
+    a.nmeas = in.nmeas;                                                     \
+    a.htw = in.htw;                                                         \
+    a.tw_lo = reinterpret_cast<const CT*>(P);                               \
+    a.tw_hi = reinterpret_cast<const CT*>(Ph);                              \
+    a.xout = reinterpret_cast<CT*>(xout);                                   \
+    a.hist = reinterpret_cast<double*>(ws + in.off_hist);                   \
+    a.parts = reinterpret_cast<qpe::Partial*>(ws + in.off_partials);        \
+    a.pscale = ldexp(1.0, -2 * in.nmeas);                                   \
+    a.inv_n = ldexp(1.0, -in.nmeas);                                        \
+    a.xscale = xscale;                                                      \
+    push_bytes(bm.level_args, &a, sizeof(a));                               \
+  }
+          if (c64)
+            QPE_FILL_ARGS(float2)
+          else
+            QPE_FILL_ARGS(double2)
+#undef QPE_FILL_ARGS
+          int DI = 0, G = 0;
+          qpe::level_shape(logd, mode, elem_size(p->prec), &DI, &G);
+          const int ncg = (int)(in.d / DI);
+          const int64_t iters = ((int64_t(1) << L.logna) + G - 1) / G;
+          int64_t ch = 4;
+          if (mode != 0) ch = std::max<int64_t>(4, (iters + qpe::kReduceBlocks - 1) / qpe::kReduceBlocks);
+          for (int cg = 0; cg < ncg; ++cg)
+            for (int64_t c0 = 0; c0 < iters; c0 += ch) {
+              qpe::GroupItem gi{};
+              gi.arg = nargs;
+              gi.cg = cg;
+              gi.it_begin = c0;
+              gi.it_end = std::min(iters, c0 + ch);
+              gi.part = mode != 0 ? part_count[i]++ : 0;
+              bm.items.push_back(gi);
+            }
+          if (mode != 0) {
+            qpe::FinItem f{};
+            f.parts = reinterpret_cast<const qpe::Partial*>(ws + in.off_partials);
+            f.out = reinterpret_cast<qpe::Scalars*>(ws + in.off_scalars);
+            f.count = part_count[i];
+            f.nmeas = in.nmeas;
+            bm.fin.push_back(f);
+          }
+          ++nargs;
+        }
+        LL.nitems = (int)bm.items.size() - LL.item_off;
+        if (LL.nitems > 0) {
+          int occ = 1;
+          if (nsm > 0)
+            occ = c64 ? qpe::level_grouped_occupancy<float2>(logd, LL.mode)
+                      : qpe::level_grouped_occupancy<double2>(logd, LL.mode);
+          LL.grid = std::min<int64_t>(LL.nitems, (int64_t)std::max(nsm, 1) * occ);
+          bm.launches.push_back(LL);
+        }
+      }
+    }
+  }
+}
+
+// Workspace offsets of the uploaded lists, after the instances' regions.
+size_t place_batch_meta(qpe::BatchMeta& bm, size_t off) {
+  auto take = [&](size_t bytes) {
+    const size_t o = align_up(off);
+    off = align_up(o + std::max<size_t>(bytes, 16));
+    return o;
+  };
+  bm.off_sq = take(bm.sq.size() * sizeof(qpe::SqItem));
+  bm.off_conv = take(bm.conv.size() * sizeof(qpe::SqItem));
+  bm.off_tab = take(bm.tab_items.size());
+  bm.off_seed = take(bm.seed_items.size());
+  bm.off_args = take(bm.level_args.size());
+  bm.off_items = take(bm.items.size() * sizeof(qpe::GroupItem));
+  bm.off_fin = take(bm.fin.size() * sizeof(qpe::FinItem));
+  return off;
+}
+
+qpe_status upload_batch_meta(qpe_plan_t p) {
+  qpe::BatchMeta& bm = p->bm;
+  struct Blk {
+    size_t off;
+    const void* src;
+    size_t n;
+  } blks[] = {{bm.off_sq, bm.sq.data(), bm.sq.size() * sizeof(qpe::SqItem)},
+              {bm.off_conv, bm.conv.data(), bm.conv.size() * sizeof(qpe::SqItem)},
+              {bm.off_tab, bm.tab_items.data(), bm.tab_items.size()},
+              {bm.off_seed, bm.seed_items.data(), bm.seed_items.size()},
+              {bm.off_args, bm.level_args.data(), bm.level_args.size()},
+              {bm.off_items, bm.items.data(), bm.items.size() * sizeof(qpe::GroupItem)},
+              {bm.off_fin, bm.fin.data(), bm.fin.size() * sizeof(qpe::FinItem)}};
+  for (const Blk& b : blks) {
+    if (!b.n) continue;
+    cudaError_t e = cudaMemcpyAsync(p->ws + b.off, b.src, b.n, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "upload of batched work lists");
+  }
+  return QPE_OK;
+}
+
+// One whole batched run: grouped squaring steps, grouped fused levels, then
+// the plain schedule instance by instance.
+qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
+  qpe::BatchMeta& bm = p->bm;
+  const bool c64 = is_c64(p->prec);
+  char* ws = p->ws;
+  int64_t n = 0;
+  auto chk = [&](int r) {
+    if (r < 0) return false;
+    n += r;
+    return true;
+  };
+  for (Instance& in : p->inst)
+    if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
+  for (int k = 1; k < bm.maxn; ++k)
+    if (!chk(qpe::launch_square_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_sq) + bm.sq_begin[k],
+                                        bm.sq_count[k], bm.sq_tiles[k], p->stream)))
+      return cuda_fail(p, cudaGetLastError(), "grouped squaring");
+  if (!chk(qpe::launch_convert_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_conv), (int)bm.conv.size(),
+                                       bm.conv_tiles, p->stream)))
+    return cuda_fail(p, cudaGetLastError(), "grouped conversion");
+  if (!bm.fused.empty()) {
+    int r;
+    if (c64)
+      r = qpe::launch_table_grouped<float2>(reinterpret_cast<const qpe::TabItem<float2>*>(ws + bm.off_tab), bm.ntab,
+                                            bm.tab_blocks, bm.max_logd, p->stream);
+    else
+      r = qpe::launch_table_grouped<double2>(reinterpret_cast<const qpe::TabItem<double2>*>(ws + bm.off_tab),
+                                             bm.ntab, bm.tab_blocks, bm.max_logd, p->stream);
+    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "grouped tables");
+    r = c64 ? qpe::launch_seed_grouped<float2>(reinterpret_cast<const qpe::SeedItem<float2>*>(ws + bm.off_seed),
+                                               bm.nseed, p->stream)
+            : qpe::launch_seed_grouped<double2>(reinterpret_cast<const qpe::SeedItem<double2>*>(ws + bm.off_seed),
+                                                bm.nseed, p->stream);
+    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "grouped seeds");
+    const qpe::GroupItem* items = reinterpret_cast<const qpe::GroupItem*>(ws + bm.off_items);
+    for (const qpe::LevelLaunch& L : bm.launches) {
+      if (c64)
+        r = qpe::launch_level_grouped<float2>(
+            L, reinterpret_cast<const qpe::LevelArgs<float2>*>(ws + bm.off_args) + L.arg_off, items + L.item_off,
+            p->stream);
+      else
+        r = qpe::launch_level_grouped<double2>(
+            L, reinterpret_cast<const qpe::LevelArgs<double2>*>(ws + bm.off_args) + L.arg_off, items + L.item_off,
+            p->stream);
+      if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "grouped level");
+    }
+    if (!chk(qpe::launch_finalize_grouped(reinterpret_cast<const qpe::FinItem*>(ws + bm.off_fin), (int)bm.fin.size(),
+                                          p->stream)))
+      return cuda_fail(p, cudaGetLastError(), "grouped finalize");
+    for (int i : bm.fused) {
+      Instance& in = p->inst[i];
+      in.powers_done = true;
+      in.state_stage = QPE_STAGE_REDUCE;
+      in.state_natural = true;
+      in.state_valid = in.keep_state;
+    }
+  }
+  for (int i : bm.plain) {
+    Instance& in = p->inst[i];
+    in.powers_done = true;
+    int r = c64 ? qpe::launch_sweep<float2>(in, ws, false, p->stream) : qpe::launch_sweep<double2>(in, ws, false, p->stream);
+    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain sweep");
+    r = c64 ? qpe::launch_fft<float2>(in, ws, p->stream) : qpe::launch_fft<double2>(in, ws, p->stream);
+    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain fft");
+    r = c64 ? qpe::launch_reduce<float2>(in, ws, p->stream) : qpe::launch_reduce<double2>(in, ws, p->stream);
+    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain reduce");
+    in.state_stage = QPE_STAGE_REDUCE;
+    in.state_natural = false;
+    in.state_valid = true;
+  }
+  *launches = n;
+  return QPE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -262,6 +579,42 @@ qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan
   return QPE_OK;
 }
 
+qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* workspace_bytes, qpe_plan_t* out) {
+  if (!descs || !workspace_bytes || !out || count < 1) return QPE_ERR_ARG;
+  *out = nullptr;
+  for (int32_t i = 0; i < count; ++i) {
+    const qpe_status st = check_desc(&descs[i]);
+    if (st != QPE_OK) return st;
+    if (descs[i].prec != descs[0].prec || descs[i].flags != descs[0].flags) return QPE_ERR_ARG;
+  }
+  if (descs[0].flags & (QPE_FLAG_GATE_SWEEP | QPE_FLAG_TIMING)) return QPE_ERR_UNSUPPORTED;
+  qpe_plan_s* p = new (std::nothrow) qpe_plan_s();
+  if (!p) return QPE_ERR_ARG;
+  p->prec = descs[0].prec;
+  p->flags = descs[0].flags;
+  p->batched = true;
+  size_t off = 0;
+  try {
+    for (int32_t i = 0; i < count; ++i) {
+      Instance in{};
+      in.nmat = descs[i].nmat;
+      in.nmeas = descs[i].nmeas;
+      in.d = int64_t(1) << in.nmat;
+      in.N = int64_t(1) << in.nmeas;
+      off = layout_instance(in, p->prec, p->flags, off);
+      p->inst.push_back(in);
+    }
+    build_batch_meta(p, nullptr, 0);
+  } catch (...) {
+    delete p;
+    return QPE_ERR_ARG;
+  }
+  p->ws_bytes = place_batch_meta(p->bm, off);
+  *workspace_bytes = p->ws_bytes;
+  *out = p;
+  return QPE_OK;
+}
+
 qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
   if (!p) return QPE_ERR_ARG;
   if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) % kAlign) != 0 || bytes < p->ws_bytes)
@@ -269,6 +622,7 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
   if ((p->flags & QPE_FLAG_GRAPH) && !stream)
     return fail(p, QPE_ERR_ARG, "QPE_FLAG_GRAPH needs a non-default stream");
   cudaError_t e = qpe::configure_kernels();
+  if (e == cudaSuccess) e = qpe::configure_batched_kernels();
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute");
   {
     const char* v = getenv("QPE_PDL");
@@ -304,6 +658,11 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
     in.powers_done = false;
     in.state_stage = 0;
     if (qpe::launch_twiddles(in, p->ws, p->stream) < 0) return cuda_fail(p, cudaGetLastError(), "twiddle tables");
+  }
+  if (p->batched) {
+    build_batch_meta(p, p->ws, nsm);
+    const qpe_status st = upload_batch_meta(p);
+    if (st != QPE_OK) return st;
   }
   p->bound = true;
   return QPE_OK;

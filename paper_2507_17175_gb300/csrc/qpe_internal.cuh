@@ -127,6 +127,15 @@ struct TableJobs {
 
 constexpr size_t kLevelSmemCap = 110 * 1024;  // two CTAs per SM
 
+// A share of a grouped level launch: LevelArgs index, column group, a range
+// of pencil-group iterations, and the slot of its readout partial.
+struct GroupItem {
+  int arg;
+  int cg;
+  int64_t it_begin, it_end;
+  int64_t part;
+};
+
 template <typename C>
 struct LevelArgs {
   const C* seeds;  // N_a x d: Z of the level below (psi for the deepest level)
@@ -171,6 +180,76 @@ struct Instance {
   bool state_valid = true;     // false after a fused run without KEEP_STATE
 };
 
+// ---------------------------------------------------------- batched plans
+struct SqItem {  // one instance's squaring step: C = A^2 (FP64), complex64 copies
+  const double2* A;
+  double2* C;
+  float2* C32;
+  float2* A32;
+  int d, pad;
+  int64_t tile0;  // first CTA of this item in the grouped launch
+};
+template <typename C>
+struct TabItem {  // one (instance, level) table
+  const C* P;
+  C* tab;
+  int off, r, logd, pad;
+  int64_t tile0;
+};
+template <typename C>
+struct SeedItem {
+  const double2* psi;
+  C* seed;
+  int d, pad;
+};
+struct FinItem {
+  const Partial* parts;
+  Scalars* out;
+  int count, nmeas;
+};
+
+struct LevelLaunch {  // one grouped level launch
+  int logd, mode;
+  int arg_off, item_off, nitems;
+  int64_t grid;
+};
+
+struct BatchMeta {
+  int maxn = 0;
+  // squaring: items of step k at [sq_begin[k], sq_begin[k] + sq_count[k])
+  std::vector<SqItem> sq;
+  std::vector<int> sq_begin, sq_count;
+  std::vector<int64_t> sq_tiles;
+  std::vector<SqItem> conv;
+  int64_t conv_tiles = 0;
+  // fused instances
+  std::vector<int> fused, plain;
+  std::vector<char> tab_items, seed_items, level_args;  // typed by the plan's precision
+  int ntab = 0, nseed = 0, max_logd = 1;
+  int64_t tab_blocks = 0;
+  std::vector<GroupItem> items;
+  std::vector<LevelLaunch> launches;
+  std::vector<FinItem> fin;
+  // workspace offsets of the uploaded lists
+  size_t off_sq = 0, off_conv = 0, off_tab = 0, off_seed = 0, off_args = 0, off_items = 0, off_fin = 0;
+  size_t bytes = 0;
+};
+
+int launch_square_grouped(const SqItem* items, int nitems, int64_t tiles, cudaStream_t s);
+int launch_convert_grouped(const SqItem* items, int nitems, int64_t tiles, cudaStream_t s);
+template <typename C>
+int launch_table_grouped(const TabItem<C>* items, int nitems, int64_t blocks, int max_logd, cudaStream_t s);
+template <typename C>
+int launch_seed_grouped(const SeedItem<C>* items, int nitems, cudaStream_t s);
+int launch_finalize_grouped(const FinItem* items, int nitems, cudaStream_t s);
+template <typename C>
+int launch_level_grouped(const LevelLaunch& L, const LevelArgs<C>* args, const GroupItem* items, cudaStream_t s);
+template <typename C>
+int level_grouped_occupancy(int logd, int mode);
+cudaError_t configure_batched_kernels();
+// host view of the level configuration: (columns per CTA, pencils per iteration)
+void level_shape(int logd, int mode, size_t esize, int* DI, int* G);
+
 }  // namespace qpe
 
 struct qpe_plan_s {
@@ -185,6 +264,8 @@ struct qpe_plan_s {
   cudaGraphExec_t graph_exec = nullptr;
   cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // QPE_FLAG_TIMING
   bool timed_kernel = false;  // ev[5], ev[6] bracket the top-level fused kernel of the last run
+  bool batched = false;
+  qpe::BatchMeta bm;
   bool timed_run = false;  // the last enqueue recorded all five events
   std::string last_error;
 };

@@ -302,9 +302,12 @@ __device__ __forceinline__ void dft_r(C (&x)[N], int r) {
 }
 
 // ------------------------------------------------------------------ kernel
+// One CTA's share of a level: column group cg, pencil-group iterations
+// it_begin, it_begin + it_step, ... < it_end. MODE != 0 writes this share's
+// readout partial to *part_out.
 template <typename C, int LOGD, int MODE>
-__global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(LevelArgs<C> a) {
-  pdl_begin();
+__device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_t it_begin, int64_t it_end,
+                                           int64_t it_step, Partial* part_out) {
   using R_t = typename real_of<C>::type;
   using A_t = typename Acc<C>::T;
   using S = LvShape<LOGD, sizeof(C) == 16, MODE>;
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
   const int tab_ld = S::TAB_SMEM ? ROWS : L * D;  // row stride (per k) of the table in use
   const int tid = threadIdx.x;
 
-  const int cg = (int)(blockIdx.x % NCG);  // this CTA's column group
+  __syncthreads();  // shared memory of a previous share (grouped launches) fully consumed
   const int i_base = cg * DI;
   const int tab_col0 = S::TAB_SMEM ? 0 : i_base;
   if (S::TAB_SMEM) {
@@ -337,7 +340,6 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
   }
 
   const int64_t Na = int64_t(1) << a.logna;
-  const int64_t iters = (Na + G - 1) / G;
   const int lvl_shift = a.nmeas - a.logna - r;
   const int64_t lvl_mask = (int64_t(1) << (a.logna + r)) - 1;
 
@@ -345,8 +347,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
   int64_t besty = INT64_MAX;
   float wsum_f = 0.f, wcomp_f = 0.f, psum_f = 0.f, pcomp_f = 0.f;
 
-  const int64_t it0 = blockIdx.x / NCG, itstep = gridDim.x / NCG;
-  for (int64_t it = it0; it < iters; it += itstep) {
+  for (int64_t it = it_begin; it < it_end; it += it_step) {
     const int64_t ya0 = it * G;
     const int gvalid = (int)(Na - ya0 < G ? Na - ya0 : G);
     __syncthreads();  // previous iteration's buffers consumed (and the table slice loaded)
@@ -515,8 +516,32 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
         res.wsum += sp[w].wsum;
         res.psum += sp[w].psum;
       }
-      a.parts[blockIdx.x] = res;
+      *part_out = res;
     }
+  }
+}
+
+template <typename C, int LOGD, int MODE>
+__global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(LevelArgs<C> a) {
+  pdl_begin();
+  using S = LvShape<LOGD, sizeof(C) == 16, MODE>;
+  constexpr int NCG = S::D / S::DI;
+  const int64_t iters = ((int64_t(1) << a.logna) + S::G - 1) / S::G;
+  level_body<C, LOGD, MODE>(a, (int)(blockIdx.x % NCG), blockIdx.x / NCG, iters, gridDim.x / NCG,
+                            a.parts + blockIdx.x);
+  pdl_trigger();
+}
+
+// Grouped form: one launch runs many (instance, level) shares listed in
+// items[]; each CTA walks the list with a grid stride.
+template <typename C, int LOGD, int MODE>
+__global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1)
+    level2_grouped_kernel(const LevelArgs<C>* __restrict__ args, const GroupItem* __restrict__ items, int nitems) {
+  pdl_begin();
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const GroupItem it = items[w];
+    const LevelArgs<C> a = args[it.arg];
+    level_body<C, LOGD, MODE>(a, it.cg, it.it_begin, it.it_end, 1, a.parts + it.part);
   }
   pdl_trigger();
 }
@@ -660,6 +685,9 @@ static cudaError_t set_level_attrs() {
   cudaError_t e;
 #define QPE_ATTR(C, LD, M)                                                                                  \
   e = cudaFuncSetAttribute(level2_kernel<C, LD, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                           (int)level_smem_bytes(LD, M, sizeof(C)));                                        \
+  if (e != cudaSuccess) return e;                                                                           \
+  e = cudaFuncSetAttribute(level2_grouped_kernel<C, LD, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                            (int)level_smem_bytes(LD, M, sizeof(C)));                                        \
   if (e != cudaSuccess) return e;
   QPE_LV_ALL(QPE_ATTR, float2)
@@ -811,6 +839,65 @@ int level_occupancy(int logd, int r) {
 }
 template int level_occupancy<float2>(int, int);
 template int level_occupancy<double2>(int, int);
+
+void level_shape(int logd, int mode, size_t esize, int* DI, int* G) {
+  const LvCfg c = lv_cfg(logd, esize == 16);
+  *DI = mode == 0 ? c.DI0 : (1 << logd);
+  *G = mode == 0 ? c.G0 : c.G;
+}
+
+template <typename C, int M>
+static cudaError_t launch_grouped_m(int logd, unsigned grid, size_t smem, cudaStream_t s, const LevelArgs<C>* args,
+                                    const GroupItem* items, int n) {
+  switch (logd) {
+    case 1: return launch_k(level2_grouped_kernel<C, 1, M>, dim3(grid), dim3(256), smem, s, args, items, n);
+    case 2: return launch_k(level2_grouped_kernel<C, 2, M>, dim3(grid), dim3(256), smem, s, args, items, n);
+    case 3: return launch_k(level2_grouped_kernel<C, 3, M>, dim3(grid), dim3(256), smem, s, args, items, n);
+    case 4: return launch_k(level2_grouped_kernel<C, 4, M>, dim3(grid), dim3(256), smem, s, args, items, n);
+    case 5: return launch_k(level2_grouped_kernel<C, 5, M>, dim3(grid), dim3(256), smem, s, args, items, n);
+    default: return launch_k(level2_grouped_kernel<C, 6, M>, dim3(grid), dim3(256), smem, s, args, items, n);
+  }
+}
+
+template <typename C>
+int launch_level_grouped(const LevelLaunch& L, const LevelArgs<C>* args, const GroupItem* items, cudaStream_t s) {
+  if (L.nitems <= 0) return 0;
+  const size_t smem = level_smem_bytes(L.logd, L.mode, sizeof(C));
+  cudaError_t e;
+  if (L.mode == 0)
+    e = launch_grouped_m<C, 0>(L.logd, (unsigned)L.grid, smem, s, args, items, L.nitems);
+  else if (L.mode == 1)
+    e = launch_grouped_m<C, 1>(L.logd, (unsigned)L.grid, smem, s, args, items, L.nitems);
+  else
+    e = launch_grouped_m<C, 2>(L.logd, (unsigned)L.grid, smem, s, args, items, L.nitems);
+  return e == cudaSuccess ? 1 : -1;
+}
+template int launch_level_grouped<float2>(const LevelLaunch&, const LevelArgs<float2>*, const GroupItem*, cudaStream_t);
+template int launch_level_grouped<double2>(const LevelLaunch&, const LevelArgs<double2>*, const GroupItem*,
+                                           cudaStream_t);
+
+template <typename C, int M>
+static int occ_m(int logd) {
+  int blocks = 0;
+  const size_t smem = level_smem_bytes(logd, M, sizeof(C));
+  cudaError_t e;
+  switch (logd) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, level2_grouped_kernel<C, 1, M>, 256, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, level2_grouped_kernel<C, 2, M>, 256, smem); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, level2_grouped_kernel<C, 3, M>, 256, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, level2_grouped_kernel<C, 4, M>, 256, smem); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, level2_grouped_kernel<C, 5, M>, 256, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, level2_grouped_kernel<C, 6, M>, 256, smem); break;
+  }
+  return (e == cudaSuccess && blocks > 0) ? blocks : 1;
+}
+
+template <typename C>
+int level_grouped_occupancy(int logd, int mode) {
+  return mode == 0 ? occ_m<C, 0>(logd) : (mode == 1 ? occ_m<C, 1>(logd) : occ_m<C, 2>(logd));
+}
+template int level_grouped_occupancy<float2>(int, int);
+template int level_grouped_occupancy<double2>(int, int);
 
 template int launch_levels<float2>(const Instance&, char*, bool, cudaStream_t, cudaEvent_t*);
 template int launch_levels<double2>(const Instance&, char*, bool, cudaStream_t, cudaEvent_t*);

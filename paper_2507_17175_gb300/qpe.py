@@ -48,6 +48,8 @@ _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _sig = {
     "qpe_plan": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_vp)]),
+    "qpe_plan_batched": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t),
+                                        ctypes.POINTER(_vp)]),
     "qpe_bind": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "qpe_load": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _i32]),
     "qpe_run": (ctypes.c_int, [_vp]),
@@ -90,6 +92,15 @@ def plan_workspace(nmat: int, nmeas: int, prec: int = C64_FP32, flags: int = 0):
     ws = ctypes.c_size_t(0)
     h = _vp()
     st = _lib.qpe_plan(ctypes.byref(desc), ctypes.byref(ws), ctypes.byref(h))
+    return st, ws.value, h
+
+
+def plan_batched_workspace(shapes, prec: int = C64_FP32, flags: int = 0):
+    """Host-only: (status, workspace_bytes, raw handle) for [(nmat, nmeas), ...]."""
+    arr = (PlanDesc * len(shapes))(*[PlanDesc(a, b, prec, flags) for a, b in shapes])
+    ws = ctypes.c_size_t(0)
+    h = _vp()
+    st = _lib.qpe_plan_batched(arr, len(shapes), ctypes.byref(ws), ctypes.byref(h))
     return st, ws.value, h
 
 
@@ -224,3 +235,56 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class BatchedPlan(Plan):
+    """Many independent QPE problems of uneven shape in one plan (grouped
+    launches per step across instances). ``shapes`` = [(nmat, nmeas), ...]."""
+
+    def __init__(self, shapes, prec: int = C64_FP32, flags: int = 0, device=None, stream=None, workspace=None):
+        import torch
+        self.shapes = [(int(a), int(b)) for a, b in shapes]
+        self.prec, self.flags = prec, flags
+        st, self.ws_bytes, self._h = plan_batched_workspace(self.shapes, prec, flags)
+        if st != OK:
+            raise QpeError(st, f"qpe_plan_batched: {status_string(st)}")
+        self.device = torch.device(device if device is not None else "cuda")
+        if stream is None:
+            stream = torch.cuda.Stream(device=self.device) if (flags & FLAG_GRAPH) else \
+                torch.cuda.current_stream(self.device)
+        self.stream = stream
+        if workspace is None:
+            workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.workspace = workspace
+        self._keep_inputs = {}
+        self._check(_lib.qpe_bind(self._h, workspace.data_ptr(), self.ws_bytes, stream.cuda_stream), "qpe_bind")
+
+    def load(self, instance: int, U, psi):
+        nmat, nmeas = self.shapes[instance]
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+            psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        pu, du = _ptr(U)
+        pp, dp = _ptr(psi)
+        self._keep_inputs[instance] = (U, psi)
+        self._check(_lib.qpe_load(self._h, instance, pu, pp, nmat, nmeas, du), "qpe_load")
+
+    def probs(self, instance: int = 0, out=None, want_hist: bool = True):
+        nmat, nmeas = self.shapes[instance]
+        am = ctypes.c_int64(0)
+        pa = ctypes.c_double(0.0)
+        pm = ctypes.c_double(0.0)
+        if want_hist and out is None:
+            out = np.empty(1 << nmeas, dtype=np.float64)
+        ptr, dev = (0, 0) if out is None else _ptr(out)
+        self._check(_lib.qpe_probs(self._h, instance, ptr or None, ctypes.byref(am), ctypes.byref(pa),
+                                   ctypes.byref(pm), dev), "qpe_probs")
+        return out, am.value, pa.value, pm.value
+
+    def state(self, instance: int = 0, out=None):
+        nmat, nmeas = self.shapes[instance]
+        if out is None:
+            out = np.empty((1 << nmeas, 1 << nmat), dtype=self.state_dtype)
+        ptr, dev = _ptr(out)
+        self._check(_lib.qpe_state(self._h, instance, ptr, dev), "qpe_state")
+        return out

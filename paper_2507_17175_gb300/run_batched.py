@@ -1,0 +1,77 @@
+"""Time the batched form on the 512-instance workload (Nmat uniform in
+{3..10}, Nmeas in {8..18}, seeded Haar eigenbases) and compare it with running
+the same instances one plan at a time.
+
+    python -m paper_2507_17175_gb300.run_batched --prec c64 --count 512 --repeat 3
+
+Prints one JSON line: batched runs/s (all instances per run), the one-by-one
+time, and launch counts. Inputs are resident on the device before timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--prec", choices=["fp64", "c64"], default="c64")
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--single", action="store_true", help="also time one plan per instance")
+    args = ap.parse_args(argv)
+
+    import torch
+    from . import qpe, workloads
+    insts = workloads.c4(args.count)
+    prec = qpe.FP64 if args.prec == "fp64" else qpe.C64_FP32
+    shapes = [(i.nmat, i.nmeas) for i in insts]
+    stream = torch.cuda.Stream()
+    bp = qpe.BatchedPlan(shapes, prec, qpe.FLAG_GRAPH, stream=stream)
+    dev_inputs = [(torch.from_numpy(i.U).cuda(), torch.from_numpy(i.psi).cuda()) for i in insts]
+    for k, (U, psi) in enumerate(dev_inputs):
+        bp.load(k, U, psi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    with torch.cuda.stream(stream):
+        bp.run()  # capture + first replay
+        stream.synchronize()
+        for _ in range(args.repeat):
+            e0.record(stream)
+            bp.run()
+            e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1))
+    res = {"workload": f"{args.count} instances, Nmat 3..10, Nmeas 8..18", "prec": args.prec,
+           "batched_ms": min(times), "batched_runs_per_s": 1e3 / min(times),
+           "launches_per_run": bp.query(qpe.INFO_LAST_LAUNCHES),
+           "workspace_gib": bp.ws_bytes / 2 ** 30}
+    del bp
+    torch.cuda.empty_cache()
+    if args.single:
+        plans = []
+        total_launches = 0
+        t_single = 0.0
+        for inst, (U, psi) in zip(insts, dev_inputs):
+            p = qpe.Plan(inst.nmat, inst.nmeas, prec, 0, stream=stream)
+            p.load(U, psi)
+            with torch.cuda.stream(stream):
+                p.run()
+                stream.synchronize()
+                t0 = time.perf_counter()
+                e0.record(stream)
+                p.run()
+                e1.record(stream)
+                stream.synchronize()
+                t_single += e0.elapsed_time(e1)
+            total_launches += p.query(qpe.INFO_LAST_LAUNCHES)
+            del p
+        res["one_by_one_ms"] = t_single
+        res["one_by_one_launches"] = total_launches
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -97,3 +97,17 @@ def test_calls_before_bind_are_state_errors(q):
 def test_status_strings(q):
     for st in range(9):
         assert q.status_string(st).startswith("QPE_")
+
+
+def test_plan_batched_validation(q):
+    st, ws, h = q.plan_batched_workspace([(3, 8), (10, 18), (1, 1), (6, 12)], q.C64_FP32)
+    assert st == q.OK and ws > 0
+    assert q.LIB.qpe_query(h, q.INFO_INSTANCES) == 4
+    q.LIB.qpe_destroy(h)
+    # per-instance layout: at least the sum of the single plans' states
+    singles = sum(q.plan_workspace(a, b, q.C64_FP32)[1] for a, b in [(3, 8), (10, 18), (1, 1), (6, 12)])
+    assert ws >= 0.9 * singles
+    assert q.plan_batched_workspace([], q.C64_FP32)[0] == q.ERR_ARG
+    assert q.plan_batched_workspace([(0, 4)], q.C64_FP32)[0] == q.ERR_ARG
+    assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_GATE_SWEEP)[0] == q.ERR_UNSUPPORTED
+    assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_TIMING)[0] == q.ERR_UNSUPPORTED
