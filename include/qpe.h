@@ -62,9 +62,12 @@ typedef enum {
   QPE_C64_FP32 = 1,   /* complex64 state, FP32 arithmetic for the controlled    */
                       /* gates and QFT^-1; U^(2^k) squaring and the readout     */
                       /* stay FP64                                              */
-  QPE_C64_BF16X3 = 2, /* reserved: split-BF16 tensor-core U-application         */
+  QPE_C64_BF16X3 = 2, /* complex64 state; controlled gates on the tcgen05       */
+                      /* tensor cores as A_hi B_hi + A_hi B_lo + A_lo B_hi with  */
+                      /* bf16 hi/lo splits and FP32 accumulation (nmat >= 5,     */
+                      /* plain schedule); squaring and readout stay FP64         */
   QPE_C64_FP16X2 = 3, /* reserved: split-FP16 tensor-core U-application         */
-  QPE_C64_TF32X3 = 4  /* reserved: split-TF32 tensor-core U-application         */
+  QPE_C64_TF32X3 = 4  /* as QPE_C64_BF16X3 with tf32 hi/lo splits (~21 bits)    */
 } qpe_precision;
 
 /* Plan flags. */
@@ -113,8 +116,9 @@ typedef enum {
  * qpe_plan: validate a problem and size its workspace. Host only; touches no
  * GPU. On success *out is a new plan and *workspace_bytes the device bytes
  * qpe_bind needs. Errors: QPE_ERR_ARG for null pointers or nmat/nmeas/prec
- * out of range; QPE_ERR_UNSUPPORTED for combinations not built (reserved
- * precisions; QPE_FLAG_GATE_SWEEP with nmat > 6).
+ * out of range; QPE_ERR_UNSUPPORTED for combinations not built
+ * (QPE_C64_FP16X2; tensor-core precisions with nmat < 5 or the gate-by-gate
+ * schedule; QPE_FLAG_GATE_SWEEP with nmat > 6).
  */
 qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan_t* out);
 

@@ -32,6 +32,8 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 bool is_c64(int prec) { return prec != QPE_FP64; }
+// split-precision tensor-core plans (complex64 state, tcgen05 U-application)
+bool is_tc(int prec) { return prec == QPE_C64_TF32X3 || prec == QPE_C64_BF16X3; }
 size_t elem_size(int prec) { return is_c64(prec) ? 8 : 16; }
 
 qpe_status fail(qpe_plan_t p, qpe_status st, const std::string& msg) {
@@ -66,8 +68,10 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   in.off_tw_hi32 = take(nhi * 8);
   in.off_partials = take(sizeof(qpe::Partial) * qpe::kReduceBlocks);
   in.off_scalars = take(sizeof(qpe::Scalars));
+  in.off_err = take(sizeof(int));
+  if (is_tc(prec)) in.off_tcsplit = take(qpe::tc_split_bytes(prec, in.nmat, in.nmeas));
   in.fft = qpe::make_fft_plan(in.nmeas, d, elem_size(prec));
-  in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP));
+  in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP)) && !is_tc(prec);
   in.keep_state = (flags & QPE_FLAG_KEEP_STATE) != 0;
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a
@@ -94,7 +98,8 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
   if (desc->prec < QPE_FP64 || desc->prec > QPE_C64_TF32X3) return QPE_ERR_ARG;
   if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE))
     return QPE_ERR_ARG;
-  if (desc->prec > QPE_C64_FP32) return QPE_ERR_UNSUPPORTED;
+  if (desc->prec == QPE_C64_FP16X2) return QPE_ERR_UNSUPPORTED;
+  if (is_tc(desc->prec) && (desc->nmat < 5 || (desc->flags & QPE_FLAG_GATE_SWEEP))) return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
   return QPE_OK;
 }
@@ -191,8 +196,12 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
           break;
         case QPE_STAGE_SWEEP:
           if (!in.powers_done) return fail(p, QPE_ERR_STATE, "SWEEP before POWERS");
-          r = c64 ? qpe::launch_sweep<float2>(in, p->ws, gate, p->stream)
-                  : qpe::launch_sweep<double2>(in, p->ws, gate, p->stream);
+          if (is_tc(p->prec)) {
+            cudaError_t e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
+            if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
+          }
+          r = c64 ? qpe::launch_sweep<float2>(in, p->ws, gate, p->stream, p->prec)
+                  : qpe::launch_sweep<double2>(in, p->ws, gate, p->stream, p->prec);
           in.state_stage = QPE_STAGE_SWEEP;
           in.state_natural = true;
           in.state_valid = true;
@@ -623,6 +632,7 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
     return fail(p, QPE_ERR_ARG, "QPE_FLAG_GRAPH needs a non-default stream");
   cudaError_t e = qpe::configure_kernels();
   if (e == cudaSuccess) e = qpe::configure_batched_kernels();
+  if (e == cudaSuccess && is_tc(p->prec)) e = qpe::configure_tc_kernels();
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute");
   {
     const char* v = getenv("QPE_PDL");
@@ -657,6 +667,8 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
     in.loaded = false;
     in.powers_done = false;
     in.state_stage = 0;
+    e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
     if (qpe::launch_twiddles(in, p->ws, p->stream) < 0) return cuda_fail(p, cudaGetLastError(), "twiddle tables");
   }
   if (p->batched) {
@@ -744,8 +756,11 @@ qpe_status qpe_sync(qpe_plan_t p) {
   for (const Instance& in : p->inst) {
     if (in.state_stage != QPE_STAGE_REDUCE) continue;
     qpe::Scalars s;
+    int derr = 0;
     e = cudaMemcpy(&s, p->ws + in.off_scalars, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&derr, p->ws + in.off_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(p, e, "read error word");
+    if (derr) return fail(p, (qpe_status)derr, "a bounded device wait expired during the run");
     if (s.err) return fail(p, (qpe_status)s.err, "device flagged a non-finite histogram");
   }
   return QPE_OK;
@@ -763,9 +778,12 @@ qpe_status qpe_probs(qpe_plan_t p, int32_t instance, double* probs, int64_t* arg
   if (probs)
     e = cudaMemcpyAsync(probs, p->ws + in->off_hist, (size_t)in->N * 8, kind_from_device(ptr_is_device), p->stream);
   qpe::Scalars s;
+  int derr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&s, p->ws + in->off_scalars, sizeof(s), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, p->ws + in->off_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "qpe_probs copy");
+  if (derr) return fail(p, (qpe_status)derr, "a bounded device wait expired during the run");
   if (argmax) *argmax = s.argmax;
   if (phase_argmax) *phase_argmax = s.phase_argmax;
   if (phase_mean) *phase_mean = s.phase_mean;

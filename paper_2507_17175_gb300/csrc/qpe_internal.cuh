@@ -164,6 +164,8 @@ struct Instance {
   size_t off_tw_lo64, off_tw_hi64, off_tw_lo32, off_tw_hi32;
   size_t off_partials;  // kReduceBlocks Partials
   size_t off_scalars;   // Scalars
+  size_t off_err = 0;   // int32 device error word (bounded waits)
+  size_t off_tcsplit = 0;  // split operands of the tensor-core levels
   size_t state_bytes;
   FftPlan fft;
   // fused small-d schedule
@@ -276,7 +278,10 @@ namespace qpe {
 // -1 on a launch error (cudaGetLastError is left for the caller to read).
 int launch_twiddles(const Instance& in, char* ws, cudaStream_t s);
 int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s);
-template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s);
+template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, int prec = 1);
+int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s);
+size_t tc_split_bytes(int prec, int nmat, int nmeas);
+cudaError_t configure_tc_kernels();
 template <typename C> int launch_fft(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_reduce(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s);

@@ -558,7 +558,8 @@ static int launch_rows_times_pt(C* S, const C* P, int64_t M, int d, Rows rows, c
 }
 
 template <typename C>
-int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s) {
+int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, int prec) {
+  const bool tc = prec == QPE_C64_TF32X3 || prec == QPE_C64_BF16X3;
   C* S = at<C>(ws, in.off_state);
   const C* P = (sizeof(C) == 16) ? at<C>(ws, in.off_pow64) : at<C>(ws, in.off_pow32);
   const int64_t dd = in.d * in.d;
@@ -574,6 +575,8 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s) {
     int r;
     if (gate_mode)
       r = launch_rows_times_pt<C>(S, P + j * dd, in.N / 2, (int)in.d, GateRows{j}, s);
+    else if (tc && (int64_t(1) << j) >= 128)
+      r = launch_tc_level(in, ws, prec, j, s);  // tensor cores once a level fills 128-row tiles
     else
       r = launch_rows_times_pt<C>(S, P + j * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j}, s);
     if (r < 0) return -1;
@@ -688,8 +691,8 @@ cudaError_t configure_kernels() {
   return cudaFuncSetAttribute(fft_pass_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
 }
 
-template int launch_sweep<float2>(const Instance&, char*, bool, cudaStream_t);
-template int launch_sweep<double2>(const Instance&, char*, bool, cudaStream_t);
+template int launch_sweep<float2>(const Instance&, char*, bool, cudaStream_t, int);
+template int launch_sweep<double2>(const Instance&, char*, bool, cudaStream_t, int);
 template int launch_fft<float2>(const Instance&, char*, cudaStream_t);
 template int launch_fft<double2>(const Instance&, char*, cudaStream_t);
 template int launch_reduce<float2>(const Instance&, char*, cudaStream_t);

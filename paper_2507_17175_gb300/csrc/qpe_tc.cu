@@ -1,0 +1,473 @@
+// Tensor-core controlled-gate GEMM for large target registers (sm_103a
+// tcgen05 + TMA), used by the split-precision plans (QPE_C64_TF32X3,
+// QPE_C64_BF16X3) in the doubling schedule:
+//
+//   rows [2^j, 2^(j+1)) of the state  =  rows [0, 2^j)  x  P_j^T,
+//
+// written over reals: a complex64 row is 2d interleaved floats (re, im, ...)
+// and P_j becomes the 2d x 2d real matrix B with B[2i][2k] = Re P[i][k],
+// B[2i][2k+1] = -Im P[i][k], B[2i+1][2k] = Im P[i][k], B[2i+1][2k+1] = Re P[i][k]
+// (stored n-major: row n holds the weights of output column n), so
+// out[m][n] = sum_kk A[m][kk] B[n][kk]. Each operand x is split into
+// hi = round(x) and lo = round(x - hi) in the tensor type (tf32 or bf16); the
+// product A B^T is accumulated in FP32 in tensor memory as
+// A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the lo lo term is below the FP32
+// accumulator's resolution).
+//
+// Kernel: one CTA per 128 x BN output tile (BN <= 128), 192 threads. Warp 0
+// lane 0 issues TMA loads of A and B K-slabs (128-byte swizzled, one per
+// operand pair and K-block) into a 4-stage shared-memory ring; warp 1 lane 0
+// issues tcgen05.mma (M = 128, N = BN, K = 32 bytes per instruction) into
+// one of two 128 x BN FP32 tensor-memory buffers, a few K-blocks per buffer;
+// warps 2..5 drain each finished buffer with tcgen05.ld into FP32 registers
+// (correctly rounded adds) and store the rows at the end. Every mbarrier wait
+// is bounded; on expiry the CTA records QPE_ERR_TIMEOUT in the device error
+// word, frees its tensor memory and returns.
+#include <algorithm>
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "qpe_internal.cuh"
+
+namespace qpe {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kBM = 128;
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major, 128-byte-swizzled tile:
+// start address >> 4, leading offset 16 B (unused for swizzled K-major),
+// stride offset 1024 B between 8-row groups, descriptor version 1,
+// swizzle mode 2 (128 B).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+}  // namespace
+
+// Element kinds of the split products.
+enum TcKind { kTcTF32 = 0, kTcBF16 = 1 };
+
+template <int KIND>
+__device__ __forceinline__ void umma_k(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  if constexpr (KIND == kTcTF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+// Instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = BN;
+// operand format 2 = TF32 (kind::tf32) or 1 = BF16 (kind::f16).
+template <int KIND, int BN>
+__device__ __forceinline__ uint32_t make_idesc() {
+  const uint32_t fmt = KIND == kTcTF32 ? 2u : 1u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+// D[m][n] (FP32, leading dimension ldd floats) for rows m < M of the tile grid
+// = sum over the 3 operand pairs of A_pair[m][:] . B_pair[n][:], K = 2d.
+//
+// The tensor-core accumulator drops low-order bits on every accumulation
+// step, so the K range is cut into chunks of KP K-blocks: each chunk is
+// accumulated in one of two tensor-memory buffers, and four drain warps add
+// the finished chunk into correctly rounded FP32 registers while the next
+// chunk accumulates in the other buffer.
+//   warp 0 lane 0   TMA producer (4-stage ring)
+//   warp 1 lane 0   MMA issuer
+//   warps 2..5      drain + epilogue; warp w owns tensor-memory lanes
+//                   32 (w % 4) .. +31, i.e. tile rows 32 (w % 4) .. +31
+template <int KIND, int BN>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
+                   const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
+                   float* __restrict__ D, int64_t ldd, int64_t M, int K, int* __restrict__ err) {
+  pdl_begin();
+  constexpr int ESZ = KIND == kTcTF32 ? 4 : 2;
+  constexpr int BK = 128 / ESZ;       // K elements per 128-byte swizzle row
+  constexpr int KP = 4;               // K-blocks per tensor-memory chunk
+  constexpr int A_BYTES = kBM * 128;  // 16 KiB
+  constexpr int B_BYTES = BN * 128;
+  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  unsigned char* ring =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full_bar[kStages], empty_bar[kStages], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kBM;
+  const int n0 = blockIdx.y * BN;
+  const int kblocks = K / BK;
+  const int nchunks = (kblocks + KP - 1) / KP;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)(2 * BN))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // operand pairs (hi,hi), (hi,lo), (lo,hi) for each K-block
+      const int iters = kblocks * 3;
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % kStages;
+        if (it >= kStages && !mbar_wait(&empty_bar[s], ((it / kStages) - 1) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        if (*((volatile int*)&fail)) break;
+        const int kb = it / 3, pr = it - kb * 3;
+        unsigned char* sa = ring + s * STAGE_BYTES;
+        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+        tma_load_2d(sa, pr == 2 ? &mapAlo : &mapAhi, &full_bar[s], kb * BK, (int)m0);
+        tma_load_2d(sa + A_BYTES, pr == 1 ? &mapBlo : &mapBhi, &full_bar[s], kb * BK, n0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc<KIND, BN>();
+      int it = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_addr = tmem + (uint32_t)(b * BN);
+        const int kb_end = min(kblocks, (c + 1) * KP);
+        bool first = true;
+        for (int kb = c * KP; kb < kb_end; ++kb) {
+          for (int pr = 0; pr < 3; ++pr, ++it) {
+            const int s = it % kStages;
+            if (!mbar_wait(&full_bar[s], (it / kStages) & 1)) {
+              atomicExch(&fail, 1);
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
+            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction
+              umma_k<KIND>(acc_addr, ad + 2 * k, bd + 2 * k, idesc, first ? 0u : 1u);
+              first = false;
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty_bar[s]))
+                         : "memory");
+          }
+          if (*((volatile int*)&fail)) break;
+        }
+        // chunk finished (or abandoned): hand the buffer to the drain warps
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&acc_full[b]))
+                     : "memory");
+        if (*((volatile int*)&fail)) break;
+      }
+    }
+  } else {
+    // drain warps: add every finished chunk into FP32 registers
+    const int lg = warp & 3;  // tensor-memory lane group
+    float acc[BN];
+#pragma unroll
+    for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int b = c & 1;
+      bool got = mbar_wait(&acc_full[b], (c >> 1) & 1);
+      got = __all_sync(0xffffffffu, got && !*((volatile int*)&fail)) != 0;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!got) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int q = 0; q < BN / 32; ++q) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + q * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[q * 32 + i] += __uint_as_float(v[i]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+    }
+    const int64_t row = m0 + lg * 32 + lane;
+    if (ok && row < M) {
+      float4* dst = reinterpret_cast<float4*>(D + row * ldd + n0);
+#pragma unroll
+      for (int q = 0; q < BN / 4; ++q) dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+    if (!ok) atomicExch(&fail, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (fail && threadIdx.x == 0) atomicExch(err, (int)QPE_ERR_TIMEOUT);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                 : "memory");
+  }
+  pdl_trigger();
+}
+
+// ------------------------------------------------------- operand splits
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// A rows (complex64 = 2d interleaved floats) -> hi / lo in the tensor type
+template <int KIND>
+__global__ void split_rows_kernel(const float* __restrict__ src, void* __restrict__ hi, void* __restrict__ lo,
+                                  int64_t count) {
+  pdl_begin();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = src[i];
+    if constexpr (KIND == kTcTF32) {
+      const float h = tf32_round(x);
+      reinterpret_cast<float*>(hi)[i] = h;
+      reinterpret_cast<float*>(lo)[i] = tf32_round(x - h);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      reinterpret_cast<__nv_bfloat16*>(hi)[i] = h;
+      reinterpret_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+  }
+  pdl_trigger();
+}
+
+// P (d x d complex128) -> real embedding B (2d x 2d, n-major) split hi / lo
+template <int KIND>
+__global__ void embed_split_kernel(const double2* __restrict__ P, void* __restrict__ hi, void* __restrict__ lo,
+                                   int d) {
+  pdl_begin();
+  const int64_t n2 = 2 * (int64_t)d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2 * n2; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / n2, kk = e - n * n2;
+    const int64_t i = n >> 1, k = kk >> 1;
+    const double2 p = P[i * d + k];
+    const int c = (int)(n & 1), cp = (int)(kk & 1);
+    // [[re, -im], [im, re]]
+    const double v = c == 0 ? (cp == 0 ? p.x : -p.y) : (cp == 0 ? p.y : p.x);
+    if constexpr (KIND == kTcTF32) {
+      const float h = tf32_round((float)v);
+      reinterpret_cast<float*>(hi)[e] = h;
+      reinterpret_cast<float*>(lo)[e] = tf32_round((float)(v - (double)h));
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+      reinterpret_cast<__nv_bfloat16*>(hi)[e] = h;
+      reinterpret_cast<__nv_bfloat16*>(lo)[e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    }
+  }
+  pdl_trigger();
+}
+
+// ------------------------------------------------------------ host side
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D K-major operand [rows][K], box = (128 bytes of K) x box_rows, 128 B swizzle
+bool make_map(CUtensorMap* m, void* base, int kind, int64_t rows, int64_t K, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int esz = kind == kTcTF32 ? 4 : 2;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * esz};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r =
+      fn(m, kind == kTcTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int KIND, int BN>
+size_t tc_smem() {
+  return (size_t)kStages * (kBM * 128 + BN * 128) + 1024;
+}
+
+}  // namespace
+
+cudaError_t configure_tc_kernels() {
+  cudaError_t e;
+#define QPE_TC_ATTR(K, BN)                                                                                        \
+  e = cudaFuncSetAttribute(tc_gemm_kernel<K, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<K, BN>()); \
+  if (e != cudaSuccess) return e;
+  QPE_TC_ATTR(kTcTF32, 64)
+  QPE_TC_ATTR(kTcTF32, 128)
+  QPE_TC_ATTR(kTcBF16, 64)
+  QPE_TC_ATTR(kTcBF16, 128)
+#undef QPE_TC_ATTR
+  return cudaSuccess;
+}
+
+// Split buffers (bytes) a plan of this precision needs for the largest level.
+size_t tc_split_bytes(int prec, int nmat, int nmeas) {
+  if (prec != QPE_C64_TF32X3 && prec != QPE_C64_BF16X3) return 0;
+  const size_t esz = prec == QPE_C64_TF32X3 ? 4 : 2;
+  const size_t d2 = (size_t)2 << nmat;
+  const size_t rows = nmeas >= 1 ? ((size_t)1 << (nmeas - 1)) : 1;
+  return 2 * rows * d2 * esz + 2 * d2 * d2 * esz;
+}
+
+// One doubling level j on the tensor cores: rows [half, 2 half) = rows
+// [0, half) x P_j^T. Returns launches, or -1 (launch error / tensor map).
+int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s) {
+  const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : kTcBF16;
+  const size_t esz = kind == kTcTF32 ? 4 : 2;
+  const int64_t half = int64_t(1) << j;
+  const int64_t d2 = 2 * in.d;
+  char* Ahi = ws + in.off_tcsplit;
+  char* Alo = Ahi + (size_t)(int64_t(1) << (in.nmeas - 1)) * d2 * esz;
+  char* Bhi = Alo + (size_t)(int64_t(1) << (in.nmeas - 1)) * d2 * esz;
+  char* Blo = Bhi + (size_t)d2 * d2 * esz;
+  float* S = reinterpret_cast<float*>(ws + in.off_state);
+  const double2* Pj = reinterpret_cast<const double2*>(ws + in.off_pow64) + (int64_t)j * in.d * in.d;
+  int launches = 0;
+  cudaError_t e;
+  const int64_t cnt = half * d2;
+  const int gblocks = (int)std::min<int64_t>((cnt + 255) / 256, 152 * 16);
+  e = kind == kTcTF32 ? launch_k(split_rows_kernel<kTcTF32>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
+                                 (void*)Ahi, (void*)Alo, cnt)
+                      : launch_k(split_rows_kernel<kTcBF16>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
+                                 (void*)Ahi, (void*)Alo, cnt);
+  if (e != cudaSuccess) return -1;
+  ++launches;
+  const int eblocks = (int)std::min<int64_t>((d2 * d2 + 255) / 256, 152 * 16);
+  e = kind == kTcTF32 ? launch_k(embed_split_kernel<kTcTF32>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
+                                 (void*)Blo, (int)in.d)
+                      : launch_k(embed_split_kernel<kTcBF16>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
+                                 (void*)Blo, (int)in.d);
+  if (e != cudaSuccess) return -1;
+  ++launches;
+  const int BN = d2 >= 128 ? 128 : (int)d2;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if (!make_map(&mAh, Ahi, kind, half, d2, kBM) || !make_map(&mAl, Alo, kind, half, d2, kBM) ||
+      !make_map(&mBh, Bhi, kind, d2, d2, BN) || !make_map(&mBl, Blo, kind, d2, d2, BN))
+    return -1;
+  float* Dout = S + half * d2;
+  int* err = reinterpret_cast<int*>(ws + in.off_err);
+  const dim3 grid((unsigned)((half + kBM - 1) / kBM), (unsigned)(d2 / BN));
+#define QPE_TC_LAUNCH(K, B)                                                                                    \
+  e = launch_k(tc_gemm_kernel<K, B>, grid, dim3(192), tc_smem<K, B>(), s, mAh, mAl, mBh, mBl, Dout, (int64_t)d2, \
+               half, (int)d2, err)
+  if (kind == kTcTF32) {
+    if (BN == 128)
+      QPE_TC_LAUNCH(kTcTF32, 128);
+    else
+      QPE_TC_LAUNCH(kTcTF32, 64);
+  } else {
+    if (BN == 128)
+      QPE_TC_LAUNCH(kTcBF16, 128);
+    else
+      QPE_TC_LAUNCH(kTcBF16, 64);
+  }
+#undef QPE_TC_LAUNCH
+  if (e != cudaSuccess) return -1;
+  return launches + 1;
+}
+
+}  // namespace qpe

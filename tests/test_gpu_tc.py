@@ -1,0 +1,79 @@
+"""Split-precision tensor-core plans (tcgen05 U-application, TF32x3 and
+BF16x3) against the FP64 oracle and the closed form."""
+import numpy as np
+import pytest
+
+from oracle import fejer, gates, readout
+from paper_2507_17175_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TF32X3, BF16X3 = 4, 2
+# Row tolerance relative to the largest amplitude: tf32 splits keep ~21
+# significand bits per operand, bf16 splits ~16; FP32 accumulation over 2d
+# terms and <= 2 tensor-core levels in these shapes.
+ROW_TOL = {TF32X3: 5e-6, BF16X3: 2e-4}
+PROB_TOL = {TF32X3: 1e-5, BF16X3: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2507_17175_gb300 import qpe
+    return qpe
+
+
+@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+@pytest.mark.parametrize("nmat,nmeas", [(5, 8), (5, 10), (6, 9), (7, 9), (8, 10)])
+def test_tc_rows_after_gates(q, prec, nmat, nmeas):
+    """Rows 2^7.. of the state come from the tensor-core GEMM: compare every
+    row with the oracle's gate-by-gate state."""
+    rng = np.random.default_rng(nmat * 31 + nmeas)
+    U = W.haar_unitary(rng, 1 << nmat)
+    psi = W.random_state(rng, 1 << nmat, 1)[:, 0]
+    psi /= np.linalg.norm(psi)
+    plan = q.Plan(nmat, nmeas, prec)
+    plan.load(U, psi)
+    plan.run_stages(q.STAGE_POWERS, q.STAGE_SWEEP)
+    S = plan.state()
+    ref = gates.qpe_after_sweeps(U, psi, nmeas)
+    assert np.abs(S - ref).max() <= ROW_TOL[prec] * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+@pytest.mark.parametrize("nmat,nmeas", [(5, 10), (6, 12), (7, 9), (8, 10)])
+def test_tc_end_to_end(q, prec, nmat, nmeas):
+    rng = np.random.default_rng(nmat * 7 + nmeas)
+    inst = W.haar_instance(rng, nmat, nmeas, superposition=True)
+    plan = q.Plan(nmat, nmeas, prec)
+    plan.load(inst.U, inst.psi)
+    plan.run()
+    P, am, pa, pm = plan.probs()
+    ref = gates.qpe_probabilities(inst.U, inst.psi, nmeas)
+    assert np.abs(P - ref).max() <= PROB_TOL[prec]
+    top2 = np.sort(ref)[-2:]
+    if top2[1] - top2[0] > 10 * PROB_TOL[prec]:
+        assert am == readout.argmax_lowest(ref)
+
+
+@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+def test_c3_tensor_cores_vs_closed_form(q, prec):
+    """Nmat = 12, Nmeas = 20 (32 qubits) with the U-application on the
+    tensor cores: the whole histogram against the Fejer closed form (max-abs
+    and L1), and the argmax."""
+    inst = W.c3()
+    plan = q.Plan(inst.nmat, inst.nmeas, prec)
+    plan.load(inst.U, inst.psi)
+    plan.run()
+    P, am, pa, pm = plan.probs()
+    Q = fejer.probabilities(inst.phases, inst.weights, inst.nmeas)
+    err = np.abs(P - Q)
+    print(f"prec {prec}: max-abs {err.max():.3e} L1 {err.sum():.3e}")
+    assert err.max() <= PROB_TOL[prec]
+    order = np.argsort(Q)
+    if Q[order[-1]] - Q[order[-2]] > 10 * PROB_TOL[prec]:
+        assert am == order[-1]
