@@ -242,6 +242,40 @@ qpe_status qpe_sync(qpe_plan_t plan);
  * touch the caller's workspace. NULL is accepted. */
 qpe_status qpe_destroy(qpe_plan_t plan);
 
+/* Readout written by qpe_readout_static (device memory, caller-owned). */
+typedef struct {
+  int64_t argmax;      /* most probable outcome, lowest y on exact ties        */
+  double phase_argmax; /* argmax / N                                          */
+  double phase_mean;   /* sum_y P[y] y / N                                    */
+  double total;        /* sum_y P[y]                                          */
+} qpe_readout_t;
+
+/*
+ * qpe_readout_static: histogram and readout of a final statevector without
+ * any device allocation and without a plan. The paper has no counterpart;
+ * this serves callers that cannot allocate device memory (code where an
+ * allocation would synchronise or grow a memory pool that must stay fixed,
+ * or a host library that never owns device memory), so it needs no
+ * workspace: its only scratch, the per-block partial results, is a fixed
+ * array inside the library (256 KiB on every GPU that loads it, held until
+ * the process exits).
+ *
+ * final_state: device pointer to the N x d final statevector in natural row
+ * order (complex128 for QPE_FP64, complex64 for the other precisions), as
+ * qpe_state returns it. Outputs, device pointers owned by the caller: probs
+ * (N doubles, P[y] = sum_t |X[y][t]|^2) and *readout. Enqueued on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream); no host
+ * synchronisation. Nmeas above 21 is rejected with QPE_ERR_WORKSPACE (the
+ * fixed scratch holds 8192 partials of 256 rows each); bad pointers or
+ * shapes with QPE_ERR_ARG. The first call on each device looks up the
+ * scratch's device address (cudaGetSymbolAddress); make that first call
+ * outside any stream capture. All calls on a device share the scratch: two
+ * calls whose kernels may overlap on the GPU (different streams, no
+ * ordering between them) race on it.
+ */
+qpe_status qpe_readout_static(const void* final_state, int32_t nmat, int32_t nmeas, int32_t prec, double* probs,
+                              qpe_readout_t* readout, void* cuda_stream);
+
 const char* qpe_status_string(qpe_status s);
 /* Last error message recorded on the plan ("" if none; static text for NULL). */
 const char* qpe_last_error(qpe_plan_t plan);

@@ -64,6 +64,7 @@ _sig = {
     "qpe_stage_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "qpe_kernel_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "qpe_destroy": (ctypes.c_int, [_vp]),
+    "qpe_readout_static": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "qpe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qpe_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -93,6 +94,17 @@ def plan_workspace(nmat: int, nmeas: int, prec: int = C64_FP32, flags: int = 0):
     h = _vp()
     st = _lib.qpe_plan(ctypes.byref(desc), ctypes.byref(ws), ctypes.byref(h))
     return st, ws.value, h
+
+
+def readout_static(final_state, nmat: int, nmeas: int, prec: int, probs, readout, stream=None) -> int:
+    """Histogram + readout of a device-resident final statevector through the
+    entry point that allocates nothing (qpe_readout_static). ``probs`` is a
+    float64 CUDA tensor of N elements and ``readout`` a 32-byte CUDA tensor
+    receiving (int64 argmax, phase_argmax, phase_mean, total). Returns the
+    qpe_status."""
+    s = 0 if stream is None else stream.cuda_stream
+    return _lib.qpe_readout_static(final_state.data_ptr(), nmat, nmeas, prec, probs.data_ptr(), readout.data_ptr(),
+                                   s or None)
 
 
 def plan_batched_workspace(shapes, prec: int = C64_FP32, flags: int = 0):
