@@ -127,6 +127,25 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """MAX of a per-rank scalar across the process group (a single rank: x)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(world: int, steps_per_rank: int, local_ms: float, device) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: every rank ran
+    ``steps_per_rank`` steps; the job took the slowest rank's time.
+    Returns (runs per second over all ranks, max ms over ranks)."""
+    slowest = max_over_ranks(local_ms, device)
+    return world * steps_per_rank / (slowest / 1e3), slowest
+
+
 # ------------------------------------------------------------ CPU baseline
 def oracle_cost(n: int, d: int) -> float:
     """Amplitude-gate operations of the gate-by-gate oracle: n Hadamards
@@ -235,13 +254,8 @@ def bench_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = float(sum(times))
     launches_per_run = plan.query(qpe.INFO_LAST_LAUNCHES)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = aggregate(world, args.steps, float(sum(times)), dev)
     ms_per_step = total_ms / args.steps
 
     P, am, pa, pm = plan.probs()
@@ -278,13 +292,10 @@ def bench_ours(args, rank, world, local_rank):
             e2e_plan.run()
             e2e_plan.probs(hist_h)      # D2H of the histogram + readout (synchronises)
         t_e2e = time.perf_counter() - t0
-    e2e = {"value": world * ke / t_e2e if world == 1 else None, "unit": "runs/s",
+    e2e_value, _ = aggregate(world, ke, t_e2e * 1e3, dev)
+    e2e = {"value": e2e_value, "unit": "runs/s",
            "h2d_bytes_per_step": int(inst.U.nbytes + inst.psi.nbytes),
            "d2h_bytes_per_step": int(inst.N * 8 + 40)}
-    if world > 1:
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e["value"] = world * ke / float(t.item())
 
     # ---------------- roofline of the dominant stage
     pk = peaks()
