@@ -83,9 +83,17 @@ typedef enum {
                                  /* controlled gates and run QFT^-1 and the    */
                                  /* reduction as separate passes over it; the  */
                                  /* default for nmat <= 6 is the fused         */
-                                 /* schedule (see qpe_run)                     */
+                                 /* schedule (see qpe_run), whose workspace    */
+                                 /* has no N x d state buffer unless           */
+                                 /* QPE_FLAG_KEEP_STATE is set, so stage-by-   */
+                                 /* stage runs and qpe_load_state need PLAIN   */
 #define QPE_FLAG_KEEP_STATE 0x10u /* fused schedule: also write the final     */
                                   /* statevector (one extra state write)      */
+#define QPE_FLAG_REPEAT_U 0x20u  /* with QPE_FLAG_GATE_SWEEP: apply U itself   */
+                                 /* 2^k times for measurement qubit k instead */
+                                 /* of U^(2^k) once (the construction the     */
+                                 /* paper's cost argument assumes, Sec. 4.1); */
+                                 /* nmeas <= 14                               */
 
 typedef struct {
   int32_t nmat;   /* target-register qubits, 1..12 (d = 2^nmat)                 */
@@ -118,7 +126,8 @@ typedef enum {
  * qpe_bind needs. Errors: QPE_ERR_ARG for null pointers or nmat/nmeas/prec
  * out of range; QPE_ERR_UNSUPPORTED for combinations not built
  * (QPE_C64_FP16X2; tensor-core precisions with nmat < 5 or the gate-by-gate
- * schedule; QPE_FLAG_GATE_SWEEP with nmat > 6).
+ * schedule; QPE_FLAG_GATE_SWEEP with nmat > 6; QPE_FLAG_REPEAT_U without
+ * QPE_FLAG_GATE_SWEEP or with nmeas > 14).
  */
 qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan_t* out);
 

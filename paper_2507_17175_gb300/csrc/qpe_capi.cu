@@ -57,8 +57,12 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   in.off_pow64 = take((size_t)in.nmeas * d * d * 16);
   in.off_pow32 = is_c64(prec) ? take((size_t)in.nmeas * d * d * 8) : 0;
   in.off_psi = take((size_t)d * 16);
+  in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP)) && !is_tc(prec);
+  in.keep_state = (flags & QPE_FLAG_KEEP_STATE) != 0;
+  // the fused schedule never materialises the N x d state unless asked to keep it
   in.state_bytes = (size_t)N * d * elem_size(prec);
-  in.off_state = take(in.state_bytes);
+  in.has_state = !in.fused || in.keep_state;
+  in.off_state = in.has_state ? take(in.state_bytes) : 0;
   in.off_hist = take((size_t)N * 8);
   in.htw = (in.nmeas + 1) / 2;
   const size_t nlo = size_t(1) << in.htw, nhi = size_t(1) << (in.nmeas - in.htw);
@@ -71,8 +75,6 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   in.off_err = take(sizeof(int));
   if (is_tc(prec)) in.off_tcsplit = take(qpe::tc_split_bytes(prec, in.nmat, in.nmeas));
   in.fft = qpe::make_fft_plan(in.nmeas, d, elem_size(prec));
-  in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP)) && !is_tc(prec);
-  in.keep_state = (flags & QPE_FLAG_KEEP_STATE) != 0;
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a
     // plan's layout does not depend on its schedule flags)
@@ -96,8 +98,11 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
   if (desc->nmat < 1 || desc->nmat > kMaxNmat) return QPE_ERR_ARG;
   if (desc->nmeas < 1 || desc->nmeas > kMaxNmeas) return QPE_ERR_ARG;
   if (desc->prec < QPE_FP64 || desc->prec > QPE_C64_TF32X3) return QPE_ERR_ARG;
-  if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE))
+  if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE |
+                      QPE_FLAG_REPEAT_U))
     return QPE_ERR_ARG;
+  if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
+    return QPE_ERR_UNSUPPORTED;
   if (desc->prec == QPE_C64_FP16X2) return QPE_ERR_UNSUPPORTED;
   if (is_tc(desc->prec) && (desc->nmat < 5 || (desc->flags & QPE_FLAG_GATE_SWEEP))) return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
@@ -183,6 +188,10 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
       in.state_valid = in.keep_state;
       continue;
     }
+    if (!in.has_state && last >= QPE_STAGE_SWEEP)
+      return fail(p, QPE_ERR_STATE,
+                  "this fused plan has no state buffer for stage-by-stage runs; plan with QPE_FLAG_PLAIN or "
+                  "QPE_FLAG_KEEP_STATE");
     for (int st = first; st <= last; ++st) {
       if (timing) {
         cudaError_t e = record_event(p->ev[st - 1], p->stream);
@@ -200,8 +209,11 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
             cudaError_t e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
             if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
           }
-          r = c64 ? qpe::launch_sweep<float2>(in, p->ws, gate, p->stream, p->prec)
-                  : qpe::launch_sweep<double2>(in, p->ws, gate, p->stream, p->prec);
+          {
+            const int prec_arg = (p->flags & QPE_FLAG_REPEAT_U) ? -1 : p->prec;  // -1: repeat U 2^k times
+            r = c64 ? qpe::launch_sweep<float2>(in, p->ws, gate, p->stream, prec_arg)
+                    : qpe::launch_sweep<double2>(in, p->ws, gate, p->stream, prec_arg);
+          }
           in.state_stage = QPE_STAGE_SWEEP;
           in.state_natural = true;
           in.state_valid = true;
@@ -839,6 +851,7 @@ qpe_status qpe_load_state(qpe_plan_t p, int32_t instance, const void* src, int32
   Instance* in;
   qpe_status st = get_instance(p, instance, &in);
   if (st != QPE_OK) return st;
+  if (!in->has_state) return fail(p, QPE_ERR_STATE, "this fused plan has no state buffer; plan with QPE_FLAG_PLAIN");
   cudaError_t e =
       cudaMemcpyAsync(p->ws + in->off_state, src, in->state_bytes, kind_to_device(ptr_is_device), p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "qpe_load_state copy");

@@ -167,6 +167,7 @@ struct Instance {
   size_t off_err = 0;   // int32 device error word (bounded waits)
   size_t off_tcsplit = 0;  // split operands of the tensor-core levels
   size_t state_bytes;
+  bool has_state = true;  // the workspace holds an N x d state buffer
   FftPlan fft;
   // fused small-d schedule
   bool fused = false;

@@ -571,9 +571,16 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, i
                (const double2*)at<double2>(ws, in.off_psi), init_rows, logd, scale) != cudaSuccess)
     return -1;
   ++launches;
+  const bool repeat_u = prec < 0;  // controlled-U applied 2^j times (gate schedule only)
   for (int j = 0; j < in.nmeas; ++j) {
-    int r;
-    if (gate_mode)
+    int r = 0;
+    if (gate_mode && repeat_u) {
+      for (int64_t rep = 0; rep < (int64_t(1) << j); ++rep) {
+        const int rr = launch_rows_times_pt<C>(S, P, in.N / 2, (int)in.d, GateRows{j}, s);
+        if (rr < 0) return -1;
+        r += rr;
+      }
+    } else if (gate_mode)
       r = launch_rows_times_pt<C>(S, P + j * dd, in.N / 2, (int)in.d, GateRows{j}, s);
     else if (tc && (int64_t(1) << j) >= 128)
       r = launch_tc_level(in, ws, prec, j, s);  // tensor cores once a level fills 128-row tiles

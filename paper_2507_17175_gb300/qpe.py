@@ -35,6 +35,9 @@ FP64, C64_FP32, C64_BF16X3, C64_FP16X2, C64_TF32X3 = range(5)
 FLAG_GATE_SWEEP = 0x1
 FLAG_GRAPH = 0x2
 FLAG_TIMING = 0x4
+FLAG_PLAIN = 0x8
+FLAG_KEEP_STATE = 0x10
+FLAG_REPEAT_U = 0x20
 STAGE_POWERS, STAGE_SWEEP, STAGE_FFT, STAGE_REDUCE = 1, 2, 3, 4
 INFO_WORKSPACE_BYTES, INFO_STATE_BYTES, INFO_FFT_PASSES, INFO_LAST_LAUNCHES, INFO_INSTANCES = 1, 2, 3, 4, 5
 

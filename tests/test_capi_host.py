@@ -41,7 +41,11 @@ def test_plan_sizes_workspace(q):
     st, ws, h = q.plan_workspace(6, 16, q.C64_FP32)
     assert st == q.OK
     N, d = 1 << 16, 64
-    assert ws >= N * d * 8 + N * 8 + 16 * d * d * 16
+    # default (fused) plan: powers + histogram, no N x d state buffer
+    assert N * 8 + 16 * d * d * 16 <= ws < N * d * 8
+    st, ws_plain, h2 = q.plan_workspace(6, 16, q.C64_FP32, q.FLAG_PLAIN if hasattr(q, "FLAG_PLAIN") else 0x8)
+    assert st == q.OK and ws_plain >= ws + N * d * 8
+    q.LIB.qpe_destroy(h2)
     assert q.LIB.qpe_query(h, q.INFO_STATE_BYTES) == N * d * 8
     assert q.LIB.qpe_query(h, q.INFO_FFT_PASSES) == 2
     q.LIB.qpe_destroy(h)

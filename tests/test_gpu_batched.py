@@ -99,3 +99,24 @@ def test_c4_full_batch_vs_fejer(q):
             assert am == cand[order[-1]], k
         assert abs(P.sum() - 1.0) < 1e-4, k
     assert worst <= 1e-5
+
+
+def test_precision_study_matches_oracle_readout(q):
+    """The Sec. 4.2 study on the GPU path: for small Nmeas its per-eigenvector
+    estimates equal the oracle's readout of the same histograms."""
+    from paper_2507_17175_gb300 import precision_study as ps
+    rows, phases = ps.study_rows([4, 6, 9], q.FP64)
+    rng = np.random.default_rng(12345)
+    V = W.haar_unitary(rng, 16)
+    ph = rng.random(16)
+    U = W.unitary_from_eigen(V, ph)
+    assert np.array_equal(ph, phases)
+    for r in rows:
+        n = r["nmeas"]
+        em, ew = [], []
+        for j in range(16):
+            P = gates.qpe_probabilities(U, V[:, j], n)
+            em.append(readout.phase_max_norm(P))
+            ew.append(readout.phase_weighted_mean(P))
+        assert abs(r["err_max_norm"] - float(np.mean(np.abs(np.array(em) - ph)))) < 1e-9
+        assert abs(r["err_weighted_mean"] - float(np.mean(np.abs(np.array(ew) - ph)))) < 1e-9

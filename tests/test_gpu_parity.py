@@ -111,7 +111,7 @@ def test_powers_stage(q, nmat, nmeas):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [PLAIN, 1])
 @pytest.mark.parametrize("nmat,nmeas", [(1, 1), (2, 7), (4, 11), (6, 9)])
 def test_sweep_stage_rows(q, prec, flags, nmat, nmeas):
     """After the Hadamard layer and the controlled gates, row m of the state
@@ -137,7 +137,7 @@ def test_fft_stage_vs_numpy(q, prec, nmat, nmeas):
     norm="ortho") (covers 1..3 passes and ragged digit splits)."""
     rng = np.random.default_rng(nmat * 100 + nmeas)
     S = W.random_state(rng, 1 << nmeas, 1 << nmat)
-    plan = q.Plan(nmat, nmeas, prec)
+    plan = q.Plan(nmat, nmeas, prec, PLAIN)
     dt = np.complex128 if prec == 0 else np.complex64
     plan.load(np.eye(1 << nmat, dtype=np.complex128), np.ones(1 << nmat, dtype=np.complex128))
     plan.load_state(S.astype(dt))
@@ -157,7 +157,7 @@ def test_reduce_stage(q, prec, nmat, nmeas):
     S = W.random_state(rng, 1 << nmeas, 1 << nmat)
     S /= np.linalg.norm(S)
     dt = np.complex128 if prec == 0 else np.complex64
-    plan = q.Plan(nmat, nmeas, prec)
+    plan = q.Plan(nmat, nmeas, prec, PLAIN)
     plan.load(np.eye(1 << nmat, dtype=np.complex128), np.ones(1 << nmat, dtype=np.complex128))
     plan.load_state(S.astype(dt))
     plan.run_stages(q.STAGE_FFT, q.STAGE_REDUCE)
@@ -178,7 +178,7 @@ def test_reduce_ties_go_to_lowest_index(q):
     argmax must be 0."""
     S = np.zeros((4, 2), dtype=np.complex128)
     S[0, 0] = 1.0
-    plan = q.Plan(1, 2, q.FP64)
+    plan = q.Plan(1, 2, q.FP64, PLAIN)
     plan.load(np.eye(2, dtype=np.complex128), np.ones(2, dtype=np.complex128))
     plan.load_state(S)
     plan.run_stages(q.STAGE_FFT, q.STAGE_REDUCE)
@@ -236,6 +236,25 @@ def test_fused_levels_vs_oracle(q, prec, nmat, nmeas):
     assert e.value.status == q.ERR_STATE
 
 
+def test_fused_plan_without_state_buffer(q):
+    """A default (fused) plan reserves no N x d state: stage-by-stage runs
+    and qpe_load_state say so instead of touching memory it does not have."""
+    st_f, ws_f, h = q.plan_workspace(4, 20, q.C64_FP32)
+    q.LIB.qpe_destroy(h)
+    st_p, ws_p, h = q.plan_workspace(4, 20, q.C64_FP32, PLAIN)
+    q.LIB.qpe_destroy(h)
+    assert ws_p - ws_f >= (1 << 20) * 16 * 8
+    plan = q.Plan(2, 6, q.C64_FP32)
+    U = np.eye(4, dtype=np.complex128)
+    plan.load(U, U[0].copy())
+    with pytest.raises(q.QpeError) as e:
+        plan.run_stages(q.STAGE_POWERS, q.STAGE_SWEEP)
+    assert e.value.status == q.ERR_STATE
+    with pytest.raises(q.QpeError) as e:
+        plan.load_state(np.zeros((64, 4), dtype=np.complex64))
+    assert e.value.status == q.ERR_STATE
+
+
 def test_device_inputs(q):
     import torch
     inst = W.c2()
@@ -290,7 +309,7 @@ def test_gpu_error_paths(q):
     small = torch.empty(ws // 2, dtype=torch.uint8, device="cuda")
     assert q.LIB.qpe_bind(h, small.data_ptr(), ws // 2, None) == q.ERR_WORKSPACE
     q.LIB.qpe_destroy(h)
-    plan = q.Plan(2, 6, q.FP64)
+    plan = q.Plan(2, 6, q.FP64, PLAIN)
     U = np.eye(4, dtype=np.complex128)
     with pytest.raises(q.QpeError) as e:
         plan._check(q.LIB.qpe_load(plan.handle, 0, U.ctypes.data, U.ctypes.data, 3, 6, 0), "load")
@@ -372,3 +391,40 @@ def test_c5_vs_fejer(q, prec, nmeas):
     plan.close()
     del plan
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------ paper-faithful variants
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nmat,nmeas", [(2, 6), (3, 9), (5, 8)])
+def test_repeated_u_gates(q, prec, nmat, nmeas):
+    """Controlled-U applied 2^k times per measurement qubit (no squaring, the
+    construction Sec. 4.1's cost argument assumes) gives the same
+    distribution as the oracle."""
+    rng = np.random.default_rng(nmat + 3 * nmeas)
+    inst = W.haar_instance(rng, nmat, nmeas, superposition=True)
+    plan = q.Plan(nmat, nmeas, prec, 0x1 | 0x20)
+    plan.load(inst.U, inst.psi)
+    plan.run()
+    P, am, _, _ = plan.probs()
+    assert np.abs(P - gates.qpe_probabilities(inst.U, inst.psi, nmeas)).max() <= TOL[prec] * (10 if prec == 0 else 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("flags", [0, 0x1, 0x8])
+def test_paper_analytic_family(q, prec, flags):
+    """The analytic problem of Sec. 3 (phases j / 2^Nmat, non-unitary
+    U = P Lambda P^-1, eigenvector x_j as input): probability 1 at
+    y = j 2^(Nmeas - Nmat), as the golden cases state."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_exact_phases.txt")
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        nmat, nmeas, j, y, p = (int(v) if i < 4 else float(v) for i, v in enumerate(line.split()))
+        inst = W.analytic_instance(nmat, nmeas, j)
+        plan = q.Plan(nmat, nmeas, prec, flags)
+        plan.load(inst.U, inst.psi)
+        plan.run()
+        P, am, _, _ = plan.probs()
+        assert am == y
+        assert abs(P[y] - p) <= (1e-10 if prec == 0 else 2e-5)
