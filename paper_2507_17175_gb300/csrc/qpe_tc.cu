@@ -18,9 +18,10 @@
 // lane 0 issues TMA loads of A and B K-slabs (128-byte swizzled, one per
 // operand pair and K-block) into a 4-stage shared-memory ring; warp 1 lane 0
 // issues tcgen05.mma (M = 128, N = BN, K = 32 bytes per instruction) into
-// one of two 128 x BN FP32 tensor-memory buffers, a few K-blocks per buffer;
-// warps 2..5 drain each finished buffer with tcgen05.ld into FP32 registers
-// (correctly rounded adds) and store the rows at the end. Every mbarrier wait
+// double-buffered FP32 tensor-memory accumulators (hi.hi drained after every
+// K-block, the cross terms every 8); warps 2..5 drain each finished buffer
+// with tcgen05.ld into FP32 registers (correctly rounded adds) and store the
+// rows at the end. Every mbarrier wait
 // is bounded; on expiry the CTA records QPE_ERR_TIMEOUT in the device error
 // word, frees its tensor memory and returns.
 #include <algorithm>
@@ -128,14 +129,21 @@ __device__ __forceinline__ uint32_t make_idesc() {
 // = sum over the 3 operand pairs of A_pair[m][:] . B_pair[n][:], K = 2d.
 //
 // The tensor-core accumulator drops low-order bits on every accumulation
-// step, so the K range is cut into chunks of KP K-blocks: each chunk is
-// accumulated in one of two tensor-memory buffers, and four drain warps add
-// the finished chunk into correctly rounded FP32 registers while the next
-// chunk accumulates in the other buffer.
-//   warp 0 lane 0   TMA producer (4-stage ring)
+// step, so nothing is left to accumulate there for long: the dominant
+// hi.hi product of every K-block goes to one of two "main" tensor-memory
+// buffers and is added into correctly rounded FP32 registers right after
+// that K-block; the two cross products (about 2^-11 smaller) go to one of two
+// "cross" buffers drained every KPC K-blocks. Four drain warps do the adds
+// while the MMAs of the next K-blocks run.
+//   warp 0 lane 0   TMA producer (4-stage ring, one stage per operand pair)
 //   warp 1 lane 0   MMA issuer
 //   warps 2..5      drain + epilogue; warp w owns tensor-memory lanes
 //                   32 (w % 4) .. +31, i.e. tile rows 32 (w % 4) .. +31
+// Tiles are visited in groups of kGroupM row tiles by all column tiles so the
+// operand panels in flight stay in L2.
+constexpr int kGroupM = 8;
+constexpr int kKPC = 8;  // K-blocks per cross-term chunk
+
 template <int KIND, int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
@@ -144,22 +152,36 @@ __global__ void __launch_bounds__(192, 1)
   pdl_begin();
   constexpr int ESZ = KIND == kTcTF32 ? 4 : 2;
   constexpr int BK = 128 / ESZ;       // K elements per 128-byte swizzle row
-  constexpr int KP = 4;               // K-blocks per tensor-memory chunk
   constexpr int A_BYTES = kBM * 128;  // 16 KiB
   constexpr int B_BYTES = BN * 128;
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* ring =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full_bar[kStages], empty_bar[kStages], acc_full[2], acc_empty[2];
+  __shared__ uint64_t full_bar[kStages], empty_bar[kStages];
+  __shared__ uint64_t main_full[2], main_empty[2], cross_full[2], cross_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * kBM;
-  const int n0 = blockIdx.y * BN;
+  // grouped raster: kGroupM row tiles x all column tiles per group
+  const int64_t m_tiles = (M + kBM - 1) / kBM;
+  const int n_tiles = (int)(ldd / BN);
+  int64_t m_tile, n_tile;
+  {
+    const int64_t bid = blockIdx.x;
+    const int64_t per_group = (int64_t)kGroupM * n_tiles;
+    const int64_t g = bid / per_group;
+    const int64_t first = g * kGroupM;
+    const int64_t gm = (m_tiles - first) < kGroupM ? (m_tiles - first) : kGroupM;
+    const int64_t local = bid - g * per_group;
+    m_tile = first + local % gm;
+    n_tile = local / gm;
+  }
+  const int64_t m0 = m_tile * kBM;
+  const int n0 = (int)n_tile * BN;
   const int kblocks = K / BK;
-  const int nchunks = (kblocks + KP - 1) / KP;
+  const int nchunks_x = (kblocks + kKPC - 1) / kKPC;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -167,15 +189,17 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&empty_bar[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&main_full[b], 1);
+      mbar_init(&main_empty[b], 4);
+      mbar_init(&cross_full[b], 1);
+      mbar_init(&cross_empty[b], 4);
     }
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"((uint32_t)(2 * BN))
+                 "r"((uint32_t)(4 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -183,10 +207,10 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  // tensor-memory columns: main buffers [0, 2 BN), cross buffers [2 BN, 4 BN)
 
   if (warp == 0) {
     if (lane == 0) {
-      // operand pairs (hi,hi), (hi,lo), (lo,hi) for each K-block
       const int iters = kblocks * 3;
       for (int it = 0; it < iters; ++it) {
         const int s = it % kStages;
@@ -206,64 +230,70 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       const uint32_t idesc = make_idesc<KIND, BN>();
       int it = 0;
-      for (int c = 0; c < nchunks; ++c) {
-        const int b = c & 1;
-        if (c >= 2 && !mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1)) {
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int bm = kb & 1;                    // main buffer of this K-block
+        const int cx = kb / kKPC, bx = cx & 1;    // cross chunk and its buffer
+        const bool cx_first = (kb % kKPC) == 0;
+        const bool cx_last = (kb % kKPC) == kKPC - 1 || kb == kblocks - 1;
+        if (kb >= 2 && !mbar_wait(&main_empty[bm], ((kb >> 1) - 1) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        if (cx_first && cx >= 2 && !mbar_wait(&cross_empty[bx], ((cx >> 1) - 1) & 1)) {
           atomicExch(&fail, 1);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc_addr = tmem + (uint32_t)(b * BN);
-        const int kb_end = min(kblocks, (c + 1) * KP);
-        bool first = true;
-        for (int kb = c * KP; kb < kb_end; ++kb) {
-          for (int pr = 0; pr < 3; ++pr, ++it) {
-            const int s = it % kStages;
-            if (!mbar_wait(&full_bar[s], (it / kStages) & 1)) {
-              atomicExch(&fail, 1);
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
-            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction
-              umma_k<KIND>(acc_addr, ad + 2 * k, bd + 2 * k, idesc, first ? 0u : 1u);
-              first = false;
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&empty_bar[s]))
-                         : "memory");
+        bool ok = true;
+        for (int pr = 0; pr < 3; ++pr, ++it) {
+          const int s = it % kStages;
+          if (!mbar_wait(&full_bar[s], (it / kStages) & 1)) {
+            ok = false;
+            break;
           }
-          if (*((volatile int*)&fail)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+          const uint32_t acc_addr = pr == 0 ? tmem + (uint32_t)(bm * BN) : tmem + (uint32_t)((2 + bx) * BN);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction
+            const bool fresh = k == 0 && (pr == 0 || (pr == 1 && cx_first));
+            umma_k<KIND>(acc_addr, ad + 2 * k, bd + 2 * k, idesc, fresh ? 0u : 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty_bar[s]))
+                       : "memory");
+          if (pr == 0)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&main_full[bm]))
+                         : "memory");
         }
-        // chunk finished (or abandoned): hand the buffer to the drain warps
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&acc_full[b]))
-                     : "memory");
-        if (*((volatile int*)&fail)) break;
+        if (!ok) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        if (cx_last)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&cross_full[bx]))
+                       : "memory");
       }
     }
   } else {
-    // drain warps: add every finished chunk into FP32 registers
+    // drain warps: add finished buffers into FP32 registers
     const int lg = warp & 3;  // tensor-memory lane group
     float acc[BN];
 #pragma unroll
     for (int i = 0; i < BN; ++i) acc[i] = 0.f;
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      const int b = c & 1;
-      bool got = mbar_wait(&acc_full[b], (c >> 1) & 1);
+    auto drain = [&](uint64_t* full, uint64_t* empty, uint32_t parity, uint32_t col0) -> bool {
+      bool got = mbar_wait(full, parity);
       got = __all_sync(0xffffffffu, got && !*((volatile int*)&fail)) != 0;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (!got) {
-        ok = false;
-        break;
-      }
+      if (!got) return false;
 #pragma unroll
       for (int q = 0; q < BN / 32; ++q) {
         uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + q * 32);
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + col0 + (uint32_t)(q * 32);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
             "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -280,8 +310,17 @@ __global__ void __launch_bounds__(192, 1)
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(empty)) : "memory");
+      return true;
+    };
+    for (int kb = 0; kb < kblocks && ok; ++kb) {
+      const int bm = kb & 1;
+      ok = drain(&main_full[bm], &main_empty[bm], (kb >> 1) & 1, (uint32_t)(bm * BN));
+      const int cx = kb / kKPC, bx = cx & 1;
+      const bool cx_last = (kb % kKPC) == kKPC - 1 || kb == kblocks - 1;
+      if (ok && cx_last) ok = drain(&cross_full[bx], &cross_empty[bx], (cx >> 1) & 1, (uint32_t)((2 + bx) * BN));
     }
+    (void)nchunks_x;
     const int64_t row = m0 + lg * 32 + lane;
     if (ok && row < M) {
       float4* dst = reinterpret_cast<float4*>(D + row * ldd + n0);
@@ -294,7 +333,7 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   if (fail && threadIdx.x == 0) atomicExch(err, (int)QPE_ERR_TIMEOUT);
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(4 * BN))
                  : "memory");
   }
   pdl_trigger();
@@ -450,7 +489,7 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
     return -1;
   float* Dout = S + half * d2;
   int* err = reinterpret_cast<int*>(ws + in.off_err);
-  const dim3 grid((unsigned)((half + kBM - 1) / kBM), (unsigned)(d2 / BN));
+  const dim3 grid((unsigned)(((half + kBM - 1) / kBM) * (d2 / BN)));  // grouped raster inside the kernel
 #define QPE_TC_LAUNCH(K, B)                                                                                    \
   e = launch_k(tc_gemm_kernel<K, B>, grid, dim3(192), tc_smem<K, B>(), s, mAh, mAl, mBh, mBl, Dout, (int64_t)d2, \
                half, (int)d2, err)
