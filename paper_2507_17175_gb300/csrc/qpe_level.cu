@@ -46,6 +46,33 @@ __device__ __forceinline__ float2 w32<float2>(int k) { return c_w32_32[k]; }
 template <typename C>
 __device__ __forceinline__ C ldg(const C* p) { return __ldg(p); }
 
+// Global -> shared copies that do not stall the issuing thread: every thread
+// issues all of its copies, then waits once (cp.async groups).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// one complex element; valid == false stores zeros (no bytes are read)
+__device__ __forceinline__ void cp_async_elem(float2* smem, const float2* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* smem, const double2* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// count contiguous complex elements (16-byte aligned, count * sizeof(C) a multiple of 16)
+template <typename C>
+__device__ __forceinline__ void cp_async_block(C* smem, const C* gmem, int count, int tid, int nthreads) {
+  constexpr int V = 16 / (int)sizeof(C);
+  for (int e = tid * V; e < count; e += nthreads * V) cp_async16(smem + e, gmem + e);
+}
+
 template <typename C>
 __device__ __forceinline__ C tw_lookup(const C* lo, const C* hi, int h, int64_t e) {
   const int64_t mask = (int64_t(1) << h) - 1;
@@ -331,11 +358,21 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   const int i_base = cg * DI;
   const int tab_col0 = S::TAB_SMEM ? 0 : i_base;
   if (S::TAB_SMEM) {
-    // slice: tabS[k][m_b DI + ii] = tab[k][m_b D + i_base + ii]
-    for (int e = tid; e < D * ROWS; e += blockDim.x) {
-      const int k = e / ROWS, rr = e - k * ROWS;
-      const int mb = rr / DI, ii = rr - mb * DI;
-      tabS[e] = ldg(a.tab + (int64_t)k * (L * D) + mb * D + i_base + ii);
+    // slice: tabS[k][m_b DI + ii] = tab[k][m_b D + i_base + ii], asynchronous,
+    // completed by the first iteration's wait
+    constexpr int V = 16 / (int)sizeof(C);  // elements per 16-byte copy
+    if constexpr (DI % V == 0) {
+      for (int e = tid * V; e < D * ROWS; e += blockDim.x * V) {
+        const int k = e / ROWS, rr = e - k * ROWS;
+        const int mb = rr / DI, ii = rr - mb * DI;
+        cp_async16(tabS + e, a.tab + (int64_t)k * (L * D) + mb * D + i_base + ii);
+      }
+    } else {
+      for (int e = tid; e < D * ROWS; e += blockDim.x) {
+        const int k = e / ROWS, rr = e - k * ROWS;
+        const int mb = rr / DI, ii = rr - mb * DI;
+        cp_async_elem(tabS + e, a.tab + (int64_t)k * (L * D) + mb * D + i_base + ii, true);
+      }
     }
   }
 
@@ -353,8 +390,10 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
     __syncthreads();  // previous iteration's buffers consumed (and the table slice loaded)
     for (int e = tid; e < G * D; e += blockDim.x) {
       const int g = e / D, k = e - g * D;
-      ZsT[k * G + g] = (g < gvalid) ? ldg(a.seeds + ((ya0 + g) << LOGD) + k) : czero<C>();
+      const bool valid = g < gvalid;
+      cp_async_elem(ZsT + k * G + g, a.seeds + (valid ? ((ya0 + g) << LOGD) + k : 0), valid);
     }
+    cp_async_commit();
     for (int e = tid; e < G * L; e += blockDim.x) {
       const int g = e >> r, mb = e & (L - 1);
       const int64_t ya = ya0 + g;
@@ -362,6 +401,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
       if (mb && ya) w = tw_lookup(a.tw_lo, a.tw_hi, a.htw, (((int64_t)mb * ya) & lvl_mask) << lvl_shift);
       twS[e] = w;
     }
+    cp_async_wait<0>();
     __syncthreads();
     // T[g][m_b][ii] = w^(m_b y_a) sum_k M[m_b][i_base + ii][k] Z[g][k]
     {
@@ -486,6 +526,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
       }
     }
   }
+  cp_async_wait<0>();  // a share with no iterations still issued its slice copies
   if (MODE != 0) {
     if (sizeof(C) == 8) {
       wsum = (double)wsum_f;
@@ -558,8 +599,8 @@ __global__ void __launch_bounds__(256) level_table_kernel(const C* __restrict__ 
   const int D = 1 << logd;
   const int TB = D < 16 ? D : 16;  // rows per CTA
   const int nrb = D / TB;
-  C* Pb = reinterpret_cast<C*>(smem_raw);  // D x D factor
-  C* V = Pb + D * D;                        // TB x D running rows
+  C* Pb0 = reinterpret_cast<C*>(smem_raw);  // two D x D factors (double buffer)
+  C* V = Pb0 + 2 * D * D;                    // TB x D running rows
   C* Vn = V + TB * D;
   // locate (level, m_b, row block)
   int64_t b = blockIdx.x;
@@ -577,43 +618,55 @@ __global__ void __launch_bounds__(256) level_table_kernel(const C* __restrict__ 
   const int i0 = rb * TB;
   const int64_t DD = (int64_t)D * D;
   const int tid = threadIdx.x;
-  bool started = false;
-  for (int j = 0; j < jobs.r[li]; ++j) {
-    if (!((mb >> j) & 1)) continue;
-    const C* Pj = P + (int64_t)(jobs.off[li] + j) * DD;
-    if (!started) {
-      for (int e = tid; e < TB * D; e += blockDim.x) V[e] = ldg(Pj + (int64_t)i0 * D + e);
-      started = true;
-      continue;
-    }
-    __syncthreads();
-    for (int e = tid; e < D * D; e += blockDim.x) Pb[e] = ldg(Pj + e);
-    __syncthreads();
-    // each thread: 4 outputs (row rr, columns k0..k0+3 spaced by D/4), 4 independent chains
-    const int q4 = D >= 4 ? D / 4 : 1;
-    for (int e = tid; e < TB * q4; e += blockDim.x) {
-      const int rr = e / q4, k0 = e - rr * q4;
-      const int nk = D >= 4 ? 4 : D;
-      C acc[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
-#pragma unroll 4
-      for (int l = 0; l < D; ++l) {
-        const C v = V[rr * D + l];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t < nk) cfma(acc[t], v, Pb[l * D + k0 + t * q4]);
-      }
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (t < nk) Vn[rr * D + k0 + t * q4] = acc[t];
-    }
-    __syncthreads();
-    for (int e = tid; e < TB * D; e += blockDim.x) V[e] = Vn[e];
-  }
-  if (!started) {  // m_b = 0: identity rows
+  // the factors P_(off+j), j in bits(m_b), in increasing j
+  int js[8];
+  int nf = 0;
+  for (int j = 0; j < jobs.r[li]; ++j)
+    if ((mb >> j) & 1) js[nf++] = j;
+  const C* Pbase = P + (int64_t)jobs.off[li] * DD;
+  if (nf == 0) {  // m_b = 0: identity rows
     for (int e = tid; e < TB * D; e += blockDim.x) {
       const int rr = e / D, k = e - rr * D;
       V[e] = (k == i0 + rr) ? mk((typename real_of<C>::type)1, (typename real_of<C>::type)0) : czero<C>();
     }
+  } else {
+    // rows i0.. of the first factor, and the second factor, in flight together
+    cp_async_block(V, Pbase + js[0] * DD + (int64_t)i0 * D, TB * D, tid, blockDim.x);
+    if (nf > 1) cp_async_block(Pb0, Pbase + js[1] * DD, D * D, tid, blockDim.x);
+    cp_async_commit();
+    for (int f = 1; f < nf; ++f) {
+      const C* Pb = Pb0 + (f & 1 ? 0 : D * D);
+      if (f + 1 < nf) {  // next factor into the other buffer while this one is used
+        cp_async_block(Pb0 + (f & 1 ? D * D : 0), Pbase + js[f + 1] * DD, D * D, tid, blockDim.x);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      // each thread: 4 outputs (row rr, columns k0..k0+3 spaced by D/4), 4 independent chains
+      const int q4 = D >= 4 ? D / 4 : 1;
+      for (int e = tid; e < TB * q4; e += blockDim.x) {
+        const int rr = e / q4, k0 = e - rr * q4;
+        const int nk = D >= 4 ? 4 : D;
+        C acc[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
+#pragma unroll 4
+        for (int l = 0; l < D; ++l) {
+          const C v = V[rr * D + l];
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (t < nk) cfma(acc[t], v, Pb[l * D + k0 + t * q4]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < nk) Vn[rr * D + k0 + t * q4] = acc[t];
+      }
+      __syncthreads();
+      C* tmp = V;
+      V = Vn;
+      Vn = tmp;
+    }
+    cp_async_wait<0>();
   }
   __syncthreads();
   const int L = 1 << jobs.r[li];
@@ -699,7 +752,10 @@ static cudaError_t set_level_attrs() {
 cudaError_t configure_level_kernels() {
   {
     cudaError_t e0 = cudaFuncSetAttribute(level_table_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (64 * 64 + 2 * 16 * 64) * 16);
+                                          (2 * 64 * 64 + 2 * 16 * 64) * 16);
+    if (e0 != cudaSuccess) return e0;
+    e0 = cudaFuncSetAttribute(level_table_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (2 * 64 * 64 + 2 * 16 * 64) * 8);
     if (e0 != cudaSuccess) return e0;
   }
   double2 w64[32];
@@ -730,32 +786,37 @@ static void launch_level2(int logd, unsigned grid, size_t smem, cudaStream_t s, 
 }
 
 template <typename C>
-int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s, cudaEvent_t* top_ev) {
+static int launch_level_tables(const Instance& in, char* ws, int first, int count, cudaStream_t s) {
   const size_t esize = sizeof(C);
   const C* P = reinterpret_cast<const C*>(ws + (esize == 16 ? in.off_pow64 : in.off_pow32));
+  TableJobs jobs{};
+  jobs.count = count;
+  const int D = (int)in.d;
+  const int TB = D < 16 ? D : 16;
+  int64_t blocks = 0;
+  for (int j = 0; j < count; ++j) {
+    const Level& L = in.levels[first + j];
+    jobs.off[j] = L.off;
+    jobs.r[j] = L.r;
+    jobs.tab_off[j] = L.tab_off;
+    blocks += (int64_t(1) << L.r) * (D / TB);
+  }
+  const size_t smem = (2 * (size_t)D * D + 2 * (size_t)TB * D) * esize;
+  return launch_k(level_table_kernel<C>, dim3((unsigned)blocks), dim3(256), smem, s, P, ws, jobs, in.nmat) ==
+                 cudaSuccess
+             ? 1
+             : -1;
+}
+
+template <typename C>
+int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s, cudaEvent_t* top_ev) {
+  const size_t esize = sizeof(C);
   const C* tlo = reinterpret_cast<const C*>(ws + (esize == 16 ? in.off_tw_lo64 : in.off_tw_lo32));
   const C* thi = reinterpret_cast<const C*>(ws + (esize == 16 ? in.off_tw_hi64 : in.off_tw_hi32));
   int launches = 0;
   const int nl = (int)in.levels.size();
-  // tables of every level
-  {
-    TableJobs jobs{};
-    jobs.count = nl;
-    const int D = (int)in.d;
-    const int TB = D < 16 ? D : 16;
-    int64_t blocks = 0;
-    for (int li = 0; li < nl; ++li) {
-      jobs.off[li] = in.levels[li].off;
-      jobs.r[li] = in.levels[li].r;
-      jobs.tab_off[li] = in.levels[li].tab_off;
-      blocks += (int64_t(1) << in.levels[li].r) * (D / TB);
-    }
-    const size_t smem = ((size_t)D * D + 2 * (size_t)TB * D) * esize;
-    if (launch_k(level_table_kernel<C>, dim3((unsigned)blocks), dim3(256), smem, s, P, ws, jobs, in.nmat) !=
-        cudaSuccess)
-      return -1;
-    ++launches;
-  }
+  if (launch_level_tables<C>(in, ws, 0, nl, s) < 0) return -1;
+  ++launches;
   C* seed = reinterpret_cast<C*>(ws + in.zbuf_seed_off);
   if (launch_k(seed_psi_kernel<C>, dim3(1), dim3(64), 0, s, reinterpret_cast<const double2*>(ws + in.off_psi), seed,
                (int)in.d) != cudaSuccess)
