@@ -229,7 +229,7 @@ __host__ __device__ constexpr LvCfg lv_cfg(int logd, bool dbl) {
                 : logd == 3 ? LvCfg{5, 16, 4, 4, true, 8, 16}
                 : logd == 4 ? LvCfg{4, 16, 4, 4, true, 8, 32}
                 : logd == 5 ? LvCfg{3, 16, 4, 4, false, 8, 64}
-                            : LvCfg{4, 8, 4, 4, false, 8, 32});
+                            : LvCfg{4, 8, 2, 8, false, 8, 32});
 }
 
 // Per-MODE view of the configuration: the final level (MODE 1/2) takes whole
@@ -428,6 +428,11 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
               load4(tp, av);
             else
               ldg4(tp, av);
+          } else if constexpr (TR == 2 && sizeof(C) == 8) {
+            const float4 v2 = S::TAB_SMEM ? *reinterpret_cast<const float4*>(tp)
+                                          : __ldg(reinterpret_cast<const float4*>(tp));
+            av[0] = mk((R_t)v2.x, (R_t)v2.y);
+            av[1] = mk((R_t)v2.z, (R_t)v2.w);
           } else {
 #pragma unroll
             for (int t = 0; t < TR; ++t) av[t] = S::TAB_SMEM ? tp[t] : ldg(tp + t);
@@ -435,6 +440,9 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
           const C* zp = ZsT + k * G + gg * TG;
           if constexpr (TG == 4) {
             load4(zp, zv);
+          } else if constexpr (TG == 8) {
+            load4(zp, *reinterpret_cast<C(*)[4]>(&zv[0]));
+            load4(zp + 4, *reinterpret_cast<C(*)[4]>(&zv[4]));
           } else {
 #pragma unroll
             for (int g = 0; g < TG; ++g) zv[g] = zp[g];
