@@ -94,6 +94,13 @@ typedef enum {
                                  /* of U^(2^k) once (the construction the     */
                                  /* paper's cost argument assumes, Sec. 4.1); */
                                  /* nmeas <= 14                               */
+#define QPE_FLAG_CHECK_UNITARY 0x40u /* the POWERS stage first forms U^dagger */
+                                     /* U in FP64; if any entry of            */
+                                     /* U^dagger U - I exceeds 1e-8 in        */
+                                     /* modulus (or is not finite) the run's  */
+                                     /* device error word is set and          */
+                                     /* qpe_sync / qpe_probs return           */
+                                     /* QPE_ERR_NUMERIC. 8 d^3 FP64 flop.     */
 
 typedef struct {
   int32_t nmat;   /* target-register qubits, 1..12 (d = 2^nmat)                 */

@@ -99,7 +99,7 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
   if (desc->nmeas < 1 || desc->nmeas > kMaxNmeas) return QPE_ERR_ARG;
   if (desc->prec < QPE_FP64 || desc->prec > QPE_C64_TF32X3) return QPE_ERR_ARG;
   if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE |
-                      QPE_FLAG_REPEAT_U))
+                      QPE_FLAG_REPEAT_U | QPE_FLAG_CHECK_UNITARY))
     return QPE_ERR_ARG;
   if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
     return QPE_ERR_UNSUPPORTED;
@@ -107,6 +107,12 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
   if (is_tc(desc->prec) && (desc->nmat < 5 || (desc->flags & QPE_FLAG_GATE_SWEEP))) return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
   return QPE_OK;
+}
+
+// What a non-zero device error word means.
+const char* err_word_message(int derr) {
+  return derr == QPE_ERR_NUMERIC ? "U is not unitary to 1e-8 (QPE_FLAG_CHECK_UNITARY)"
+                                 : "a bounded device wait expired during the run";
 }
 
 qpe_status get_instance(qpe_plan_t p, int32_t i, Instance** out) {
@@ -156,8 +162,18 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
   const bool timing = (p->flags & QPE_FLAG_TIMING) && p->inst.size() == 1 && p->ev[0];
   p->timed_run = timing && first == QPE_STAGE_POWERS && last == QPE_STAGE_REDUCE;
   p->timed_kernel = false;
+  const bool check_u = (p->flags & QPE_FLAG_CHECK_UNITARY) != 0;
   for (Instance& in : p->inst) {
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
+    // the error word covers one run: cleared where the run's first checked stage begins
+    if ((first == QPE_STAGE_POWERS && (check_u || is_tc(p->prec))) || (first == QPE_STAGE_SWEEP && is_tc(p->prec))) {
+      cudaError_t e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
+    }
+    if (check_u && first == QPE_STAGE_POWERS) {
+      if (qpe::launch_check_unitary(in, p->ws, p->stream) < 0) return cuda_fail(p, cudaGetLastError(), "unitarity check");
+      ++n;
+    }
     if (in.fused && first <= QPE_STAGE_SWEEP && last == QPE_STAGE_REDUCE) {
       // fused schedule: POWERS, then the levels (gates + QFT^-1 + histogram)
       for (int st = first; st <= QPE_STAGE_REDUCE; ++st) {
@@ -205,10 +221,6 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
           break;
         case QPE_STAGE_SWEEP:
           if (!in.powers_done) return fail(p, QPE_ERR_STATE, "SWEEP before POWERS");
-          if (is_tc(p->prec)) {
-            cudaError_t e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
-            if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
-          }
           {
             const int prec_arg = (p->flags & QPE_FLAG_REPEAT_U) ? -1 : p->prec;  // -1: repeat U 2^k times
             r = c64 ? qpe::launch_sweep<float2>(in, p->ws, gate, p->stream, prec_arg)
@@ -497,6 +509,13 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
   };
   for (Instance& in : p->inst)
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
+  if (p->flags & QPE_FLAG_CHECK_UNITARY) {
+    for (Instance& in : p->inst) {
+      cudaError_t e = cudaMemsetAsync(ws + in.off_err, 0, sizeof(int), p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
+      if (!chk(qpe::launch_check_unitary(in, ws, p->stream))) return cuda_fail(p, cudaGetLastError(), "unitarity check");
+    }
+  }
   for (int k = 1; k < bm.maxn; ++k)
     if (!chk(qpe::launch_square_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_sq) + bm.sq_begin[k],
                                         bm.sq_count[k], bm.sq_tiles[k], p->stream)))
@@ -766,13 +785,15 @@ qpe_status qpe_sync(qpe_plan_t p) {
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaStreamSynchronize");
   for (const Instance& in : p->inst) {
+    if (!in.loaded) continue;
+    int derr = 0;
+    e = cudaMemcpy(&derr, p->ws + in.off_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p, e, "read error word");
+    if (derr) return fail(p, (qpe_status)derr, err_word_message(derr));
     if (in.state_stage != QPE_STAGE_REDUCE) continue;
     qpe::Scalars s;
-    int derr = 0;
     e = cudaMemcpy(&s, p->ws + in.off_scalars, sizeof(s), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&derr, p->ws + in.off_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(p, e, "read error word");
-    if (derr) return fail(p, (qpe_status)derr, "a bounded device wait expired during the run");
+    if (e != cudaSuccess) return cuda_fail(p, e, "read readout scalars");
     if (s.err) return fail(p, (qpe_status)s.err, "device flagged a non-finite histogram");
   }
   return QPE_OK;
@@ -795,7 +816,7 @@ qpe_status qpe_probs(qpe_plan_t p, int32_t instance, double* probs, int64_t* arg
   if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, p->ws + in->off_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "qpe_probs copy");
-  if (derr) return fail(p, (qpe_status)derr, "a bounded device wait expired during the run");
+  if (derr) return fail(p, (qpe_status)derr, err_word_message(derr));
   if (argmax) *argmax = s.argmax;
   if (phase_argmax) *phase_argmax = s.phase_argmax;
   if (phase_mean) *phase_mean = s.phase_mean;

@@ -279,6 +279,8 @@ namespace qpe {
 // -1 on a launch error (cudaGetLastError is left for the caller to read).
 int launch_twiddles(const Instance& in, char* ws, cudaStream_t s);
 int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s);
+// U^dagger U = I to 1e-8 per entry, else the instance's error word = QPE_ERR_NUMERIC
+int launch_check_unitary(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, int prec = 1);
 int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s);
 size_t tc_split_bytes(int prec, int nmat, int nmeas);

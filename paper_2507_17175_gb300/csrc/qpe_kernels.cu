@@ -96,6 +96,40 @@ __global__ void __launch_bounds__(TS * TS * KS) square_small_kernel(const double
   pdl_trigger();
 }
 
+// Unitarity check of U (the FP64 P_0): G = U^dagger U in 16 x 16 output
+// tiles, 16-row slabs of U staged in shared memory; any |G_ij - delta_ij| above
+// tol (or not finite) sets *err to QPE_ERR_NUMERIC, keeping an earlier error.
+__global__ void __launch_bounds__(256) unitarity_kernel(const double2* __restrict__ U, int d, double tol,
+                                                        int* __restrict__ err) {
+  pdl_begin();
+  __shared__ double2 Ui[16][17];  // U[k0 + r][i0 + c]
+  __shared__ double2 Uj[16][17];  // U[k0 + r][j0 + c]
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  const double2 zero = make_double2(0.0, 0.0);
+  double2 acc = zero;
+  for (int k0 = 0; k0 < d; k0 += 16) {
+    const int k = k0 + ty;
+    Ui[ty][tx] = (k < d && i0 + tx < d) ? U[(int64_t)k * d + i0 + tx] : zero;
+    Uj[ty][tx] = (k < d && j0 + tx < d) ? U[(int64_t)k * d + j0 + tx] : zero;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const double2 a = Ui[kk][ty];  // U[k][i]
+      const double2 b = Uj[kk][tx];  // U[k][j]
+      acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));   // Re(conj(a) b)
+      acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));  // Im(conj(a) b)
+    }
+    __syncthreads();
+  }
+  const int i = i0 + ty, j = j0 + tx;
+  if (i < d && j < d) {
+    const double re = acc.x - (i == j ? 1.0 : 0.0);
+    if (!(re * re + acc.y * acc.y <= tol * tol)) atomicCAS(err, 0, (int)QPE_ERR_NUMERIC);
+  }
+  pdl_trigger();
+}
+
 // C = A * A for d >= 512: 32 x 32 output tiles, 16-wide k slabs in shared
 // memory, 2 x 2 outputs per thread.
 __global__ void __launch_bounds__(256) square_tiled_kernel(const double2* __restrict__ A,
@@ -512,6 +546,14 @@ static int launch_square(const double2* A, double2* C, int d, float2* C32, float
     default: e = launch_k(square_tiled_kernel, dim3(d / 32, d / 32), dim3(256), 0, s, A, C, d, C32, A32); break;
   }
   return e == cudaSuccess ? 1 : -1;
+}
+
+int launch_check_unitary(const Instance& in, char* ws, cudaStream_t s) {
+  const unsigned t = (unsigned)((in.d + 15) / 16);
+  return launch_k(unitarity_kernel, dim3(t, t), dim3(256), 0, s, (const double2*)at<double2>(ws, in.off_pow64),
+                  (int)in.d, 1e-8, at<int>(ws, in.off_err)) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s) {

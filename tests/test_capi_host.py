@@ -66,6 +66,8 @@ def test_plan_sizes_workspace(q):
     (7, 4, 1, 1, "ERR_UNSUPPORTED"),
     (12, 30, 1, 0, "OK"),
     (1, 1, 0, 0, "OK"),
+    (6, 16, 1, 0x40, "OK"),   # QPE_FLAG_CHECK_UNITARY
+    (6, 16, 0, 0x42, "OK"),
 ])
 def test_plan_validation(q, nmat, nmeas, prec, flags, want):
     st, ws, h = q.plan_workspace(nmat, nmeas, prec, flags)
