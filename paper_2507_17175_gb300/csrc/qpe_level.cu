@@ -244,7 +244,7 @@ struct LvShape {
   static constexpr bool TAB_SMEM = MODE == 0 ? true : c.tab_smem;
   static constexpr size_t smem(size_t esize) {
     const size_t acc = esize == 8 ? 4 : 8;
-    size_t b = (size_t)G * LMAX * DI * esize + (size_t)G * D * esize + (size_t)G * LMAX * esize;
+    size_t b = (size_t)G * LMAX * DI * esize + (size_t)G * D * esize + 2 * (size_t)G * LMAX * esize;
     if (TAB_SMEM) b += (size_t)D * LMAX * DI * esize;
     if (MODE != 0) b += (size_t)LMAX * D * (G + 1) * acc;
     return b;
@@ -328,6 +328,36 @@ __device__ __forceinline__ void dft_r(C (&x)[N], int r) {
   }
 }
 
+// Butterfly reduce-scatter of NV values over the lanes whose index bits below
+// 2 O differ: each step keeps half of the values (the upper half on lanes with
+// bit O set) and adds the partner's copy of that half. With NV >= lanes, lane
+// li ends holding the sums for indices yb0 .. yb0 + NV / lanes - 1; with fewer
+// values than lanes the remaining steps are plain all-reduce steps.
+template <int O, int NV, typename A, int N>
+__device__ __forceinline__ void reduce_scatter_step(A (&v)[N], int li, int& yb0) {
+  if constexpr (O >= 1) {
+    if constexpr (NV > 1) {
+      constexpr int H = NV / 2;
+      const bool up = (li & O) != 0;
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const A send = up ? v[j] : v[j + H];
+        const A keep = up ? v[j + H] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if (up) yb0 += H;
+      reduce_scatter_step<O / 2, H>(v, li, yb0);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+      reduce_scatter_step<O / 2, 1>(v, li, yb0);
+    }
+  }
+}
+template <int O, int NV, typename A, int N>
+__device__ __forceinline__ void reduce_scatter(A (&v)[N], int li, int& yb0) {
+  reduce_scatter_step<O, NV>(v, li, yb0);
+}
+
 // ------------------------------------------------------------------ kernel
 // One CTA's share of a level: column group cg, pencil-group iterations
 // it_begin, it_begin + it_step, ... < it_end. MODE != 0 writes this share's
@@ -347,8 +377,9 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   const int ROWS = L * DI;  // GEMM rows of this CTA: (m_b, column in group)
   C* T = reinterpret_cast<C*>(smem_raw);  // [G][L][DI]
   C* ZsT = T + G * LMAX * DI;             // [D][G]  (k-major: seeds of the G pencils)
-  C* twS = ZsT + G * D;                   // [G][L]
-  C* tabS = twS + G * LMAX;               // [D][L DI] (TAB_SMEM)
+  C* twLo = ZsT + G * D;                  // [G][L] low factor of w^(m_b y_a)
+  C* twHi = twLo + G * LMAX;              // [G][L] high factor
+  C* tabS = twHi + G * LMAX;              // [D][L DI] (TAB_SMEM)
   A_t* sq = reinterpret_cast<A_t*>(tabS + (S::TAB_SMEM ? D * LMAX * DI : 0));  // [L][D][G+1] (MODE != 0)
   const C* tab = S::TAB_SMEM ? tabS : a.tab;
   const int tab_ld = S::TAB_SMEM ? ROWS : L * D;  // row stride (per k) of the table in use
@@ -384,25 +415,62 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   int64_t besty = INT64_MAX;
   float wsum_f = 0.f, wcomp_f = 0.f, psum_f = 0.f, pcomp_f = 0.f;
 
+  // histogram bin y <- s / N^2, with the readout partials (argmax, Kahan sums)
+  auto account = [&](A_t s, int64_t y) {
+    if (sizeof(C) == 8) {
+      const float v = (float)s * (float)a.pscale;  // pscale = 1/N^2, a power of two
+      a.hist[y] = widen_nonneg(v);
+      if ((double)v > best || ((double)v == best && y < besty)) {
+        best = v;
+        besty = y;
+      }
+      const float yv = v * (float)y;  // P y (finalize divides by N), Kahan-compensated
+      float t1 = yv - wcomp_f;
+      float t2 = wsum_f + t1;
+      wcomp_f = (t2 - wsum_f) - t1;
+      wsum_f = t2;
+      t1 = v - pcomp_f;
+      t2 = psum_f + t1;
+      pcomp_f = (t2 - psum_f) - t1;
+      psum_f = t2;
+    } else {
+      const double v = (double)s * a.pscale;
+      a.hist[y] = v;
+      if (v > best || (v == best && y < besty)) {
+        best = v;
+        besty = y;
+      }
+      wsum += v * (double)y;
+      psum += v;
+    }
+  };
+
+  // seeds Z[y_a] (k-major) and the two table factors of w^(m_b y_a) of the
+  // pencil group `itg`, as asynchronous copies (w^0 = lo[0] hi[0] = 1 exactly)
+  const int64_t tw_mask = (int64_t(1) << a.htw) - 1;
+  auto issue_group = [&](int64_t itg) {
+    const int64_t yg = itg * G;
+    const int gv = (int)(Na - yg < G ? Na - yg : G);
+    for (int e = tid; e < G * D; e += blockDim.x) {
+      const int g = e / D, k = e - g * D;
+      const bool valid = g < gv;
+      cp_async_elem(ZsT + k * G + g, a.seeds + (valid ? ((yg + g) << LOGD) + k : 0), valid);
+    }
+    for (int e = tid; e < G * L; e += blockDim.x) {
+      const int g = e >> r, mb = e & (L - 1);
+      const int64_t ex = (((int64_t)mb * (yg + g)) & lvl_mask) << lvl_shift;
+      cp_async_elem(twLo + e, a.tw_lo + (ex & tw_mask), true);
+      cp_async_elem(twHi + e, a.tw_hi + (ex >> a.htw), true);
+    }
+    cp_async_commit();
+  };
+  if (it_begin < it_end) issue_group(it_begin);
+
   for (int64_t it = it_begin; it < it_end; it += it_step) {
     const int64_t ya0 = it * G;
     const int gvalid = (int)(Na - ya0 < G ? Na - ya0 : G);
-    __syncthreads();  // previous iteration's buffers consumed (and the table slice loaded)
-    for (int e = tid; e < G * D; e += blockDim.x) {
-      const int g = e / D, k = e - g * D;
-      const bool valid = g < gvalid;
-      cp_async_elem(ZsT + k * G + g, a.seeds + (valid ? ((ya0 + g) << LOGD) + k : 0), valid);
-    }
-    cp_async_commit();
-    for (int e = tid; e < G * L; e += blockDim.x) {
-      const int g = e >> r, mb = e & (L - 1);
-      const int64_t ya = ya0 + g;
-      C w = mk((R_t)1, (R_t)0);
-      if (mb && ya) w = tw_lookup(a.tw_lo, a.tw_hi, a.htw, (((int64_t)mb * ya) & lvl_mask) << lvl_shift);
-      twS[e] = w;
-    }
     cp_async_wait<0>();
-    __syncthreads();
+    __syncthreads();  // this group's copies (and the table slice) landed; the previous iteration is consumed
     // T[g][m_b][ii] = w^(m_b y_a) sum_k M[m_b][i_base + ii][k] Z[g][k]
     {
       const int nrg = ROWS / TR;
@@ -455,7 +523,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
 #pragma unroll
         for (int g = 0; g < TG; ++g) {
           const int gi = gg * TG + g;
-          const C w = twS[gi * L + mb];
+          const C w = cmul(twLo[gi * L + mb], twHi[gi * L + mb]);
           C* out = T + (gi * L + mb) * DI + ii0;
           if constexpr (TR == 4) {
             C ov[4];
@@ -470,7 +538,41 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
       }
     }
     __syncthreads();
+    // the GEMM was the only reader of ZsT / twLo / twHi: fetch the next group now
+    if (it + it_step < it_end) issue_group(it + it_step);
     // length-L DFT over m_b for every (g, column)
+    // Final level with d <= 32 columns and a full-width level: the d lanes of a
+    // pencil hold its columns, so the sums over columns are a butterfly
+    // reduce-scatter over shuffles (no shared-memory pass, no extra barrier).
+    constexpr bool kShuffleHist = MODE != 0 && D <= 32;
+    if constexpr (kShuffleHist) if (r == cfg.logl) {
+      for (int pb = 0; pb < G * D; pb += blockDim.x) {  // same trip count on every lane
+        const int p = pb + tid;
+        const bool act = p < G * D;  // G D is a multiple of 32: whole warps
+        const int g = p / D, ii = p - g * D;
+        const bool valid = act && g < gvalid;
+        C x[LMAX];
+        A_t v[LMAX];
+#pragma unroll
+        for (int m = 0; m < LMAX; ++m) x[m] = act ? T[(g * LMAX + m) * D + ii] : czero<C>();
+        dft_k<C, cfg.logl, LMAX>(x);
+#pragma unroll
+        for (int m = 0; m < LMAX; ++m) v[m] = (A_t)x[m].x * (A_t)x[m].x + (A_t)x[m].y * (A_t)x[m].y;
+        if (MODE == 2 && valid) {
+#pragma unroll
+          for (int yb = 0; yb < LMAX; ++yb)
+            a.xout[((ya0 + g + ((int64_t)yb << a.logna)) << LOGD) + ii] = cscale(x[yb], (R_t)a.xscale);
+        }
+        int yb0 = 0;
+        reduce_scatter<D / 2, LMAX>(v, ii, yb0);
+        constexpr int NV = LMAX >= D ? LMAX / D : 1;  // column sums left on each lane
+        if (valid && (LMAX >= D || ii % (D / LMAX) == 0)) {
+#pragma unroll
+          for (int j = 0; j < NV; ++j) account(v[j], ya0 + g + ((int64_t)(yb0 + j) << a.logna));
+        }
+      }
+      continue;
+    }
     for (int p = tid; p < gvalid * DI; p += blockDim.x) {
       const int g = p / DI, ii = p - g * DI;
       C x[LMAX];
@@ -500,37 +602,10 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
       for (int q = tid; q < G * L; q += blockDim.x) {
         const int g = q % G, yb = q / G;
         if (g >= gvalid) continue;
-        const int64_t ya = ya0 + g;
         A_t s = 0;
 #pragma unroll 8
         for (int i = 0; i < D; ++i) s += sq[(yb * D + i) * (G + 1) + g];
-        const int64_t y = ya + ((int64_t)yb << a.logna);
-        if (sizeof(C) == 8) {
-          const float v = (float)s * (float)a.pscale;  // pscale = 1/N^2, a power of two
-          a.hist[y] = widen_nonneg(v);
-          if ((double)v > best || ((double)v == best && y < besty)) {
-            best = v;
-            besty = y;
-          }
-          const float yv = v * (float)y;  // P y (finalize divides by N), Kahan-compensated
-          float t1 = yv - wcomp_f;
-          float t2 = wsum_f + t1;
-          wcomp_f = (t2 - wsum_f) - t1;
-          wsum_f = t2;
-          t1 = v - pcomp_f;
-          t2 = psum_f + t1;
-          pcomp_f = (t2 - psum_f) - t1;
-          psum_f = t2;
-        } else {
-          const double v = (double)s * a.pscale;
-          a.hist[y] = v;
-          if (v > best || (v == best && y < besty)) {
-            best = v;
-            besty = y;
-          }
-          wsum += v * (double)y;
-          psum += v;
-        }
+        account(s, ya0 + g + ((int64_t)yb << a.logna));
       }
     }
   }
