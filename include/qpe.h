@@ -66,7 +66,10 @@ typedef enum {
                       /* tensor cores as A_hi B_hi + A_hi B_lo + A_lo B_hi with  */
                       /* bf16 hi/lo splits and FP32 accumulation (nmat >= 5,     */
                       /* plain schedule); squaring and readout stay FP64         */
-  QPE_C64_FP16X2 = 3, /* reserved: split-FP16 tensor-core U-application         */
+  QPE_C64_FP16X2 = 3, /* as QPE_C64_BF16X3 with fp16 hi/lo splits (~22 bits)    */
+                      /* in two passes (hi.hi, then both cross products over a   */
+                      /* doubled K); rows of the state are scaled by powers of   */
+                      /* two into fp16's range and U's embedding by 2^14         */
   QPE_C64_TF32X3 = 4  /* as QPE_C64_BF16X3 with tf32 hi/lo splits (~21 bits)    */
 } qpe_precision;
 
@@ -132,8 +135,8 @@ typedef enum {
  * GPU. On success *out is a new plan and *workspace_bytes the device bytes
  * qpe_bind needs. Errors: QPE_ERR_ARG for null pointers or nmat/nmeas/prec
  * out of range; QPE_ERR_UNSUPPORTED for combinations not built
- * (QPE_C64_FP16X2; tensor-core precisions with nmat < 5 or the gate-by-gate
- * schedule; QPE_FLAG_GATE_SWEEP with nmat > 6; QPE_FLAG_REPEAT_U without
+ * (tensor-core precisions with nmat < 5 or the gate-by-gate schedule;
+ * QPE_FLAG_GATE_SWEEP with nmat > 6; QPE_FLAG_REPEAT_U without
  * QPE_FLAG_GATE_SWEEP or with nmeas > 14).
  */
 qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan_t* out);

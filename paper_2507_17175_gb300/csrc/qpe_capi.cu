@@ -33,7 +33,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 bool is_c64(int prec) { return prec != QPE_FP64; }
 // split-precision tensor-core plans (complex64 state, tcgen05 U-application)
-bool is_tc(int prec) { return prec == QPE_C64_TF32X3 || prec == QPE_C64_BF16X3; }
+bool is_tc(int prec) { return prec == QPE_C64_TF32X3 || prec == QPE_C64_BF16X3 || prec == QPE_C64_FP16X2; }
 size_t elem_size(int prec) { return is_c64(prec) ? 8 : 16; }
 
 qpe_status fail(qpe_plan_t p, qpe_status st, const std::string& msg) {
@@ -103,7 +103,6 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
     return QPE_ERR_ARG;
   if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
     return QPE_ERR_UNSUPPORTED;
-  if (desc->prec == QPE_C64_FP16X2) return QPE_ERR_UNSUPPORTED;
   if (is_tc(desc->prec) && (desc->nmat < 5 || (desc->flags & QPE_FLAG_GATE_SWEEP))) return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
   return QPE_OK;

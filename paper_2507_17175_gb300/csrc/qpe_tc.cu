@@ -1,6 +1,6 @@
 // Tensor-core controlled-gate GEMM for large target registers (sm_103a
 // tcgen05 + TMA), used by the split-precision plans (QPE_C64_TF32X3,
-// QPE_C64_BF16X3) in the doubling schedule:
+// QPE_C64_BF16X3, QPE_C64_FP16X2) in the doubling schedule:
 //
 //   rows [2^j, 2^(j+1)) of the state  =  rows [0, 2^j)  x  P_j^T,
 //
@@ -9,10 +9,15 @@
 // B[2i][2k+1] = -Im P[i][k], B[2i+1][2k] = Im P[i][k], B[2i+1][2k+1] = Re P[i][k]
 // (stored n-major: row n holds the weights of output column n), so
 // out[m][n] = sum_kk A[m][kk] B[n][kk]. Each operand x is split into
-// hi = round(x) and lo = round(x - hi) in the tensor type (tf32 or bf16); the
-// product A B^T is accumulated in FP32 in tensor memory as
+// hi = round(x) and lo = round(x - hi) in the tensor type (tf32, bf16 or
+// fp16); the product A B^T is accumulated in FP32 in tensor memory as
 // A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the lo lo term is below the FP32
-// accumulator's resolution).
+// accumulator's resolution). The hi.hi pass and the cross pass (the two cross
+// products into one accumulator, i.e. [A_hi | A_lo] [B_lo ; B_hi]^T over a
+// doubled K) are the two passes of the FP16x2 scheme. fp16 has 5 exponent
+// bits, so its operands are scaled by powers of two first: each A row so that
+// its largest |entry| lies in [2^14, 2^15), B (entries of a unitary, |.| <= 1)
+// by 2^14; the drain multiplies each output row by the exact inverse.
 //
 // Kernel: one CTA per 128 x BN output tile (BN <= 128), 192 threads. Warp 0
 // lane 0 issues TMA loads of A and B K-slabs (128-byte swizzled, one per
@@ -28,6 +33,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -96,7 +102,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 }  // namespace
 
 // Element kinds of the split products.
-enum TcKind { kTcTF32 = 0, kTcBF16 = 1 };
+enum TcKind { kTcTF32 = 0, kTcBF16 = 1, kTcFP16 = 2 };
 
 template <int KIND>
 __device__ __forceinline__ void umma_k(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -118,10 +124,10 @@ __device__ __forceinline__ void umma_k(uint32_t tmem_d, uint64_t adesc, uint64_t
 }
 
 // Instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = BN;
-// operand format 2 = TF32 (kind::tf32) or 1 = BF16 (kind::f16).
+// operand format 2 = TF32 (kind::tf32), 1 = BF16 or 0 = FP16 (kind::f16).
 template <int KIND, int BN>
 __device__ __forceinline__ uint32_t make_idesc() {
-  const uint32_t fmt = KIND == kTcTF32 ? 2u : 1u;
+  const uint32_t fmt = KIND == kTcTF32 ? 2u : (KIND == kTcBF16 ? 1u : 0u);
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
@@ -148,7 +154,8 @@ template <int KIND, int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
                    const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
-                   float* __restrict__ D, int64_t ldd, int64_t M, int K, int* __restrict__ err) {
+                   float* __restrict__ D, int64_t ldd, int64_t M, int K, int* __restrict__ err,
+                   const float* __restrict__ row_scale) {
   pdl_begin();
   constexpr int ESZ = KIND == kTcTF32 ? 4 : 2;
   constexpr int BK = 128 / ESZ;       // K elements per 128-byte swizzle row
@@ -323,6 +330,11 @@ __global__ void __launch_bounds__(192, 1)
     (void)nchunks_x;
     const int64_t row = m0 + lg * 32 + lane;
     if (ok && row < M) {
+      if constexpr (KIND == kTcFP16) {  // undo the power-of-two operand scales (exact)
+        const float sc = row_scale[row];
+#pragma unroll
+        for (int i = 0; i < BN; ++i) acc[i] *= sc;
+      }
       float4* dst = reinterpret_cast<float4*>(D + row * ldd + n0);
 #pragma unroll
       for (int q = 0; q < BN / 4; ++q) dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
@@ -366,6 +378,42 @@ __global__ void split_rows_kernel(const float* __restrict__ src, void* __restric
   pdl_trigger();
 }
 
+// A rows -> fp16 hi / lo after scaling each row by 2^e so that its largest
+// |entry| lies in [2^14, 2^15); inv_scale[row] = 2^-(e + 14) undoes both
+// operand scales. One warp per row (width floats, a multiple of 4).
+__global__ void split_rows_fp16_kernel(const float* __restrict__ src, __half* __restrict__ hi,
+                                       __half* __restrict__ lo, float* __restrict__ inv_scale, int64_t rows,
+                                       int width) {
+  pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const float* row = src + r * width;
+    float mx = 0.f;
+    for (int c = lane * 4; c < width; c += 128) {
+      const float4 v = *reinterpret_cast<const float4*>(row + c);
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // floor(log2(mx)) from the exponent field; zero / tiny rows keep scale 1
+    const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
+    const int e = (ex < -100 || ex > 100) ? 0 : 14 - ex;
+    const float sc = __uint_as_float((uint32_t)(127 + e) << 23);
+    if (lane == 0) inv_scale[r] = __uint_as_float((uint32_t)(127 - e - 14) << 23);
+    for (int c = lane * 4; c < width; c += 128) {
+      const float4 v = *reinterpret_cast<const float4*>(row + c);
+      const float x[4] = {v.x * sc, v.y * sc, v.z * sc, v.w * sc};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const __half h = __float2half_rn(x[t]);
+        hi[r * width + c + t] = h;
+        lo[r * width + c + t] = __float2half_rn(x[t] - __half2float(h));
+      }
+    }
+  }
+  pdl_trigger();
+}
+
 // P (d x d complex128) -> real embedding B (2d x 2d, n-major) split hi / lo
 template <int KIND>
 __global__ void embed_split_kernel(const double2* __restrict__ P, void* __restrict__ hi, void* __restrict__ lo,
@@ -383,6 +431,11 @@ __global__ void embed_split_kernel(const double2* __restrict__ P, void* __restri
       const float h = tf32_round((float)v);
       reinterpret_cast<float*>(hi)[e] = h;
       reinterpret_cast<float*>(lo)[e] = tf32_round((float)(v - (double)h));
+    } else if constexpr (KIND == kTcFP16) {
+      const double vs = v * 16384.0;  // 2^14, exact
+      const __half h = __float2half_rn((float)vs);
+      reinterpret_cast<__half*>(hi)[e] = h;
+      reinterpret_cast<__half*>(lo)[e] = __float2half_rn((float)(vs - (double)__half2float(h)));
     } else {
       const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
       reinterpret_cast<__nv_bfloat16*>(hi)[e] = h;
@@ -417,7 +470,11 @@ bool make_map(CUtensorMap* m, void* base, int kind, int64_t rows, int64_t K, int
   const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r =
-      fn(m, kind == kTcTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+      fn(m,
+         kind == kTcTF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+         : kind == kTcBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+         2, base, dims,
          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -439,23 +496,26 @@ cudaError_t configure_tc_kernels() {
   QPE_TC_ATTR(kTcTF32, 128)
   QPE_TC_ATTR(kTcBF16, 64)
   QPE_TC_ATTR(kTcBF16, 128)
+  QPE_TC_ATTR(kTcFP16, 64)
+  QPE_TC_ATTR(kTcFP16, 128)
 #undef QPE_TC_ATTR
   return cudaSuccess;
 }
 
 // Split buffers (bytes) a plan of this precision needs for the largest level.
 size_t tc_split_bytes(int prec, int nmat, int nmeas) {
-  if (prec != QPE_C64_TF32X3 && prec != QPE_C64_BF16X3) return 0;
+  if (prec != QPE_C64_TF32X3 && prec != QPE_C64_BF16X3 && prec != QPE_C64_FP16X2) return 0;
   const size_t esz = prec == QPE_C64_TF32X3 ? 4 : 2;
   const size_t d2 = (size_t)2 << nmat;
   const size_t rows = nmeas >= 1 ? ((size_t)1 << (nmeas - 1)) : 1;
-  return 2 * rows * d2 * esz + 2 * d2 * d2 * esz;
+  const size_t scales = prec == QPE_C64_FP16X2 ? rows * sizeof(float) : 0;  // per-row inverse scales
+  return 2 * rows * d2 * esz + 2 * d2 * d2 * esz + scales;
 }
 
 // One doubling level j on the tensor cores: rows [half, 2 half) = rows
 // [0, half) x P_j^T. Returns launches, or -1 (launch error / tensor map).
 int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s) {
-  const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : kTcBF16;
+  const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : (prec == QPE_C64_BF16X3 ? kTcBF16 : kTcFP16);
   const size_t esz = kind == kTcTF32 ? 4 : 2;
   const int64_t half = int64_t(1) << j;
   const int64_t d2 = 2 * in.d;
@@ -463,23 +523,32 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
   char* Alo = Ahi + (size_t)(int64_t(1) << (in.nmeas - 1)) * d2 * esz;
   char* Bhi = Alo + (size_t)(int64_t(1) << (in.nmeas - 1)) * d2 * esz;
   char* Blo = Bhi + (size_t)d2 * d2 * esz;
+  float* inv_scale = reinterpret_cast<float*>(Blo + (size_t)d2 * d2 * esz);  // FP16x2 only
   float* S = reinterpret_cast<float*>(ws + in.off_state);
   const double2* Pj = reinterpret_cast<const double2*>(ws + in.off_pow64) + (int64_t)j * in.d * in.d;
   int launches = 0;
   cudaError_t e;
   const int64_t cnt = half * d2;
   const int gblocks = (int)std::min<int64_t>((cnt + 255) / 256, 152 * 16);
-  e = kind == kTcTF32 ? launch_k(split_rows_kernel<kTcTF32>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
-                                 (void*)Ahi, (void*)Alo, cnt)
-                      : launch_k(split_rows_kernel<kTcBF16>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
-                                 (void*)Ahi, (void*)Alo, cnt);
+  if (kind == kTcFP16) {
+    const int rblocks = (int)std::min<int64_t>((half + 7) / 8, 152 * 16);  // 8 warps (rows) per block
+    e = launch_k(split_rows_fp16_kernel, dim3(rblocks), dim3(256), 0, s, (const float*)S,
+                 reinterpret_cast<__half*>(Ahi), reinterpret_cast<__half*>(Alo), inv_scale, half, (int)d2);
+  } else {
+    e = kind == kTcTF32 ? launch_k(split_rows_kernel<kTcTF32>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
+                                   (void*)Ahi, (void*)Alo, cnt)
+                        : launch_k(split_rows_kernel<kTcBF16>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
+                                   (void*)Ahi, (void*)Alo, cnt);
+  }
   if (e != cudaSuccess) return -1;
   ++launches;
   const int eblocks = (int)std::min<int64_t>((d2 * d2 + 255) / 256, 152 * 16);
-  e = kind == kTcTF32 ? launch_k(embed_split_kernel<kTcTF32>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
-                                 (void*)Blo, (int)in.d)
-                      : launch_k(embed_split_kernel<kTcBF16>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
-                                 (void*)Blo, (int)in.d);
+  e = kind == kTcTF32   ? launch_k(embed_split_kernel<kTcTF32>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
+                                   (void*)Blo, (int)in.d)
+      : kind == kTcBF16 ? launch_k(embed_split_kernel<kTcBF16>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
+                                   (void*)Blo, (int)in.d)
+                        : launch_k(embed_split_kernel<kTcFP16>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
+                                   (void*)Blo, (int)in.d);
   if (e != cudaSuccess) return -1;
   ++launches;
   const int BN = d2 >= 128 ? 128 : (int)d2;
@@ -492,17 +561,22 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
   const dim3 grid((unsigned)(((half + kBM - 1) / kBM) * (d2 / BN)));  // grouped raster inside the kernel
 #define QPE_TC_LAUNCH(K, B)                                                                                    \
   e = launch_k(tc_gemm_kernel<K, B>, grid, dim3(192), tc_smem<K, B>(), s, mAh, mAl, mBh, mBl, Dout, (int64_t)d2, \
-               half, (int)d2, err)
+               half, (int)d2, err, (const float*)inv_scale)
   if (kind == kTcTF32) {
     if (BN == 128)
       QPE_TC_LAUNCH(kTcTF32, 128);
     else
       QPE_TC_LAUNCH(kTcTF32, 64);
-  } else {
+  } else if (kind == kTcBF16) {
     if (BN == 128)
       QPE_TC_LAUNCH(kTcBF16, 128);
     else
       QPE_TC_LAUNCH(kTcBF16, 64);
+  } else {
+    if (BN == 128)
+      QPE_TC_LAUNCH(kTcFP16, 128);
+    else
+      QPE_TC_LAUNCH(kTcFP16, 64);
   }
 #undef QPE_TC_LAUNCH
   if (e != cudaSuccess) return -1;

@@ -18,7 +18,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--nmat", type=int, required=True)
     ap.add_argument("--nmeas", type=int, required=True)
-    ap.add_argument("--prec", choices=["fp64", "c64", "tf32x3", "bf16x3"], default="c64")
+    ap.add_argument("--prec", choices=["fp64", "c64", "tf32x3", "bf16x3", "fp16x2"], default="c64")
     ap.add_argument("--flags", type=lambda s: int(s, 0), default=0)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--seed", type=int, default=12345)
@@ -26,7 +26,8 @@ def main(argv=None):
 
     from . import qpe, workloads
     inst = workloads.haar_instance(np.random.default_rng(args.seed), args.nmat, args.nmeas, superposition=True)
-    prec = {"fp64": qpe.FP64, "c64": qpe.C64_FP32, "tf32x3": qpe.C64_TF32X3, "bf16x3": qpe.C64_BF16X3}[args.prec]
+    prec = {"fp64": qpe.FP64, "c64": qpe.C64_FP32, "tf32x3": qpe.C64_TF32X3, "bf16x3": qpe.C64_BF16X3,
+            "fp16x2": qpe.C64_FP16X2}[args.prec]
     plan = qpe.Plan(args.nmat, args.nmeas, prec, args.flags | qpe.FLAG_TIMING)
     plan.load(inst.U, inst.psi)
     for i in range(args.repeat):

@@ -67,6 +67,8 @@ def test_plan_sizes_workspace(q):
     (12, 30, 1, 0, "OK"),
     (1, 1, 0, 0, "OK"),
     (6, 16, 1, 0x40, "OK"),   # QPE_FLAG_CHECK_UNITARY
+    (7, 10, 3, 0, "OK"),      # QPE_C64_FP16X2
+    (4, 10, 3, 0, "ERR_UNSUPPORTED"),  # tensor-core precisions need nmat >= 5
     (6, 16, 0, 0x42, "OK"),
 ])
 def test_plan_validation(q, nmat, nmeas, prec, flags, want):

@@ -1,5 +1,5 @@
-"""Split-precision tensor-core plans (tcgen05 U-application, TF32x3 and
-BF16x3) against the FP64 oracle and the closed form."""
+"""Split-precision tensor-core plans (tcgen05 U-application, TF32x3, BF16x3
+and FP16x2) against the FP64 oracle and the closed form."""
 import numpy as np
 import pytest
 
@@ -8,12 +8,14 @@ from paper_2507_17175_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TF32X3, BF16X3 = 4, 2
-# Row tolerance relative to the largest amplitude: tf32 splits keep ~21
-# significand bits per operand, bf16 splits ~16; FP32 accumulation over 2d
-# terms and <= 2 tensor-core levels in these shapes.
-ROW_TOL = {TF32X3: 5e-6, BF16X3: 2e-4}
-PROB_TOL = {TF32X3: 1e-5, BF16X3: 1e-4}
+TF32X3, BF16X3, FP16X2 = 4, 2, 3
+# Row tolerance relative to the largest amplitude: tf32 and fp16 splits keep
+# ~21-22 significand bits per operand (fp16 after the power-of-two scaling),
+# bf16 splits ~16; FP32 accumulation over 2d terms and <= 2 tensor-core
+# levels in these shapes.
+ROW_TOL = {TF32X3: 5e-6, BF16X3: 2e-4, FP16X2: 5e-6}
+PROB_TOL = {TF32X3: 1e-5, BF16X3: 1e-4, FP16X2: 1e-5}
+ALL = [TF32X3, BF16X3, FP16X2]
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +29,7 @@ def q():
     return qpe
 
 
-@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+@pytest.mark.parametrize("prec", ALL)
 @pytest.mark.parametrize("nmat,nmeas", [(5, 8), (5, 10), (6, 9), (7, 9), (8, 10)])
 def test_tc_rows_after_gates(q, prec, nmat, nmeas):
     """Rows 2^7.. of the state come from the tensor-core GEMM: compare every
@@ -44,7 +46,7 @@ def test_tc_rows_after_gates(q, prec, nmat, nmeas):
     assert np.abs(S - ref).max() <= ROW_TOL[prec] * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+@pytest.mark.parametrize("prec", ALL)
 @pytest.mark.parametrize("nmat,nmeas", [(5, 10), (6, 12), (7, 9), (8, 10)])
 def test_tc_end_to_end(q, prec, nmat, nmeas):
     rng = np.random.default_rng(nmat * 7 + nmeas)
@@ -60,7 +62,7 @@ def test_tc_end_to_end(q, prec, nmat, nmeas):
         assert am == readout.argmax_lowest(ref)
 
 
-@pytest.mark.parametrize("prec", [TF32X3, BF16X3])
+@pytest.mark.parametrize("prec", ALL)
 def test_c3_tensor_cores_vs_closed_form(q, prec):
     """Nmat = 12, Nmeas = 20 (32 qubits) with the U-application on the
     tensor cores: the whole histogram against the Fejer closed form (max-abs
