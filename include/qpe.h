@@ -97,6 +97,12 @@ typedef enum {
                                  /* of U^(2^k) once (the construction the     */
                                  /* paper's cost argument assumes, Sec. 4.1); */
                                  /* nmeas <= 14                               */
+#define QPE_FLAG_AUTOTUNE 0x80u /* batched plans: qpe_bind times the grouped */
+                                /* FP64 squaring with 8 x 8, 16 x 16 and 32 x  */
+                                /* 32 output tiles on the plan's own first     */
+                                /* squaring step and keeps the fastest (the    */
+                                /* environment variable QPE_SQUARE_TILE = 8,   */
+                                /* 16 or 32 forces one instead)                */
 #define QPE_FLAG_CHECK_UNITARY 0x40u /* the POWERS stage first forms U^dagger */
                                      /* U in FP64; if any entry of            */
                                      /* U^dagger U - I exceeds 1e-8 in        */
@@ -127,7 +133,9 @@ typedef enum {
   QPE_INFO_STATE_BYTES = 2,     /* bytes of one instance's state                */
   QPE_INFO_FFT_PASSES = 3,      /* passes over the state the QFT^-1 takes      */
   QPE_INFO_LAST_LAUNCHES = 4,   /* kernels enqueued by the last qpe_run*       */
-  QPE_INFO_INSTANCES = 5
+  QPE_INFO_INSTANCES = 5,
+  QPE_INFO_SQUARE_TILE = 6      /* batched plans: output tile edge (8, 16, 32)  */
+                                /* of the grouped FP64 squaring in use         */
 } qpe_info;
 
 /*

@@ -67,6 +67,79 @@ __global__ void __launch_bounds__(256) square_grouped_kernel(const SqItem* __res
   pdl_trigger();
 }
 
+__device__ __forceinline__ int64_t sq_first(const SqItem& it, int v) {
+  return v == 0 ? it.tile0 : (v == 1 ? it.tile16 : it.tile32);
+}
+
+// P_k = P_(k-1)^2 for every listed instance: T x T output tile per CTA (256
+// threads, TM x TM outputs each), 16-wide k slabs of the row and column
+// panels staged in shared memory. V selects the item's CTA numbering.
+template <int T, int TM, int V>
+__global__ void __launch_bounds__(256) square_grouped_smem_kernel(const SqItem* __restrict__ items, int nitems) {
+  pdl_begin();
+  constexpr int BK = 16;
+  constexpr int TPD = T / TM;  // threads per tile dimension (16)
+  __shared__ double2 As[BK][T + 1];  // As[kk][r] = A[r0 + r][k0 + kk]
+  __shared__ double2 Bs[BK][T + 1];  // Bs[kk][c] = A[k0 + kk][c0 + c]
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sq_first(items[mid], V) <= (int64_t)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const SqItem it = items[lo];
+  const int64_t t = blockIdx.x - sq_first(it, V);
+  const int d = it.d;
+  const int nt = (d + T - 1) / T;
+  const int r0 = (int)(t / nt) * T, c0 = (int)(t % nt) * T;
+  const int tc = threadIdx.x % TPD, tr = threadIdx.x / TPD;
+  const double2 zero = make_double2(0.0, 0.0);
+  double2 acc[TM][TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) acc[i][j] = zero;
+  for (int k0 = 0; k0 < d; k0 += BK) {
+    for (int idx = threadIdx.x; idx < T * BK; idx += 256) {
+      const int r = idx / BK, kk = idx % BK;
+      As[kk][r] = (r0 + r < d && k0 + kk < d) ? ldgc(it.A + (int64_t)(r0 + r) * d + k0 + kk) : zero;
+      const int kb = idx / T, cb = idx % T;
+      Bs[kb][cb] = (k0 + kb < d && c0 + cb < d) ? ldgc(it.A + (int64_t)(k0 + kb) * d + c0 + cb) : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double2 a[TM], b[TM];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tr + i * TPD];
+#pragma unroll
+      for (int j = 0; j < TM; ++j) b[j] = Bs[kk][tc + j * TPD];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) {
+      const int row = r0 + tr + i * TPD, col = c0 + tc + j * TPD;
+      if (row >= d || col >= d) continue;
+      const int64_t o = (int64_t)row * d + col;
+      it.C[o] = acc[i][j];
+      if (it.C32) it.C32[o] = make_float2((float)acc[i][j].x, (float)acc[i][j].y);
+      if (it.A32) {
+        const double2 v = it.A[o];
+        it.A32[o] = make_float2((float)v.x, (float)v.y);
+      }
+    }
+  pdl_trigger();
+}
+
 // complex64 copy of P_0 for instances with Nmeas = 1 (no squaring writes it)
 __global__ void convert_grouped_kernel(const SqItem* __restrict__ items, int nitems) {
   pdl_begin();
@@ -202,10 +275,15 @@ __global__ void __launch_bounds__(256) finalize_grouped_kernel(const FinItem* __
 }
 
 // ------------------------------------------------------------- launchers
-int launch_square_grouped(const SqItem* items, int nitems, int64_t tiles, cudaStream_t s) {
+int launch_square_grouped(const SqItem* items, int nitems, int64_t tiles, int variant, cudaStream_t s) {
   if (nitems <= 0) return 0;
-  return launch_k(square_grouped_kernel, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems) == cudaSuccess ? 1
-                                                                                                               : -1;
+  cudaError_t e;
+  switch (variant) {
+    case 1: e = launch_k(square_grouped_smem_kernel<16, 1, 1>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+    case 2: e = launch_k(square_grouped_smem_kernel<32, 2, 2>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+    default: e = launch_k(square_grouped_kernel, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+  }
+  return e == cudaSuccess ? 1 : -1;
 }
 
 int launch_convert_grouped(const SqItem* items, int nitems, int64_t tiles, cudaStream_t s) {

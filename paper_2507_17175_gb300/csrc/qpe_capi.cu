@@ -99,7 +99,7 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
   if (desc->nmeas < 1 || desc->nmeas > kMaxNmeas) return QPE_ERR_ARG;
   if (desc->prec < QPE_FP64 || desc->prec > QPE_C64_TF32X3) return QPE_ERR_ARG;
   if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE |
-                      QPE_FLAG_REPEAT_U | QPE_FLAG_CHECK_UNITARY))
+                      QPE_FLAG_REPEAT_U | QPE_FLAG_CHECK_UNITARY | QPE_FLAG_AUTOTUNE))
     return QPE_ERR_ARG;
   if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
     return QPE_ERR_UNSUPPORTED;
@@ -281,9 +281,11 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
   bm.sq_begin.assign(bm.maxn + 1, 0);
   bm.sq_count.assign(bm.maxn + 1, 0);
   bm.sq_tiles.assign(bm.maxn + 1, 0);
+  bm.sq_tiles16.assign(bm.maxn + 1, 0);
+  bm.sq_tiles32.assign(bm.maxn + 1, 0);
   for (int k = 1; k < bm.maxn; ++k) {
     bm.sq_begin[k] = (int)bm.sq.size();
-    int64_t tiles = 0;
+    int64_t tiles = 0, tiles16 = 0, tiles32 = 0;
     for (Instance& in : p->inst) {
       if (in.nmeas <= k) continue;
       const int64_t dd = in.d * in.d;
@@ -296,11 +298,17 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
       it.A32 = (P32 && k == 1) ? P32 : nullptr;
       it.d = (int)in.d;
       it.tile0 = tiles;
+      it.tile16 = tiles16;
+      it.tile32 = tiles32;
       tiles += ((in.d + 7) / 8) * ((in.d + 7) / 8);
+      tiles16 += ((in.d + 15) / 16) * ((in.d + 15) / 16);
+      tiles32 += ((in.d + 31) / 32) * ((in.d + 31) / 32);
       bm.sq.push_back(it);
     }
     bm.sq_count[k] = (int)bm.sq.size() - bm.sq_begin[k];
     bm.sq_tiles[k] = tiles;
+    bm.sq_tiles16[k] = tiles16;
+    bm.sq_tiles32[k] = tiles32;
   }
   bm.conv_tiles = 0;
   if (c64)
@@ -496,6 +504,47 @@ qpe_status upload_batch_meta(qpe_plan_t p) {
 
 // One whole batched run: grouped squaring steps, grouped fused levels, then
 // the plain schedule instance by instance.
+// CTAs of the grouped squaring launch of step k with the given tile variant
+int64_t square_tiles(const qpe::BatchMeta& bm, int k, int variant) {
+  return variant == 1 ? bm.sq_tiles16[k] : (variant == 2 ? bm.sq_tiles32[k] : bm.sq_tiles[k]);
+}
+
+// The squaring tile autotuner of batched plans: every variant runs the plan's
+// own first squaring step (all instances with Nmeas > 1, at their own d) once
+// to warm up and twice under CUDA events; the fastest is kept. It runs at bind
+// time, before any input is loaded: the arithmetic does not depend on the
+// values, and the outputs it writes are recomputed by every qpe_run.
+qpe_status autotune_square(qpe_plan_t p) {
+  const qpe::BatchMeta& bm = p->bm;
+  if (bm.maxn < 2 || bm.sq_count[1] == 0) return QPE_OK;
+  const qpe::SqItem* items = reinterpret_cast<const qpe::SqItem*>(p->ws + bm.off_sq) + bm.sq_begin[1];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best = 0;
+  for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+    if (qpe::launch_square_grouped(items, bm.sq_count[1], square_tiles(bm, 1, v), v, p->stream) < 0) {
+      e = cudaGetLastError();
+      break;
+    }
+    e = cudaEventRecord(e0, p->stream);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+      if (qpe::launch_square_grouped(items, bm.sq_count[1], square_tiles(bm, 1, v), v, p->stream) < 0)
+        e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    p->tune_ms[v] = ms / 2;
+    if (e == cudaSuccess && p->tune_ms[v] < p->tune_ms[best]) best = v;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(p, e, "squaring autotune");
+  p->sq_variant = best;
+  return QPE_OK;
+}
+
 qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
   qpe::BatchMeta& bm = p->bm;
   const bool c64 = is_c64(p->prec);
@@ -517,7 +566,8 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
   }
   for (int k = 1; k < bm.maxn; ++k)
     if (!chk(qpe::launch_square_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_sq) + bm.sq_begin[k],
-                                        bm.sq_count[k], bm.sq_tiles[k], p->stream)))
+                                        bm.sq_count[k], square_tiles(bm, k, p->sq_variant), p->sq_variant,
+                                        p->stream)))
       return cuda_fail(p, cudaGetLastError(), "grouped squaring");
   if (!chk(qpe::launch_convert_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_conv), (int)bm.conv.size(),
                                        bm.conv_tiles, p->stream)))
@@ -703,8 +753,16 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
   }
   if (p->batched) {
     build_batch_meta(p, p->ws, nsm);
-    const qpe_status st = upload_batch_meta(p);
+    qpe_status st = upload_batch_meta(p);
     if (st != QPE_OK) return st;
+    const char* forced = getenv("QPE_SQUARE_TILE");  // 8, 16 or 32: skip the autotuner
+    if (forced && forced[0]) {
+      const int t = atoi(forced);
+      p->sq_variant = t == 16 ? 1 : (t == 32 ? 2 : 0);
+    } else if (p->flags & QPE_FLAG_AUTOTUNE) {
+      st = autotune_square(p);
+      if (st != QPE_OK) return st;
+    }
   }
   p->bound = true;
   return QPE_OK;
@@ -906,6 +964,7 @@ int64_t qpe_query(qpe_plan_t p, int32_t key) {
     case QPE_INFO_FFT_PASSES: return p->inst[0].fft.passes;
     case QPE_INFO_LAST_LAUNCHES: return p->last_launches;
     case QPE_INFO_INSTANCES: return (int64_t)p->inst.size();
+    case QPE_INFO_SQUARE_TILE: return p->sq_variant == 1 ? 16 : (p->sq_variant == 2 ? 32 : 8);
   }
   return -1;
 }

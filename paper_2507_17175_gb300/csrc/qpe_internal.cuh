@@ -190,7 +190,8 @@ struct SqItem {  // one instance's squaring step: C = A^2 (FP64), complex64 copi
   float2* C32;
   float2* A32;
   int d, pad;
-  int64_t tile0;  // first CTA of this item in the grouped launch
+  int64_t tile0;  // first CTA of this item in the grouped launch (8 x 8 tiles)
+  int64_t tile16, tile32;  // the same with 16 x 16 and 32 x 32 tiles
 };
 template <typename C>
 struct TabItem {  // one (instance, level) table
@@ -222,7 +223,7 @@ struct BatchMeta {
   // squaring: items of step k at [sq_begin[k], sq_begin[k] + sq_count[k])
   std::vector<SqItem> sq;
   std::vector<int> sq_begin, sq_count;
-  std::vector<int64_t> sq_tiles;
+  std::vector<int64_t> sq_tiles, sq_tiles16, sq_tiles32;  // CTAs per step, per tile variant
   std::vector<SqItem> conv;
   int64_t conv_tiles = 0;
   // fused instances
@@ -238,7 +239,9 @@ struct BatchMeta {
   size_t bytes = 0;
 };
 
-int launch_square_grouped(const SqItem* items, int nitems, int64_t tiles, cudaStream_t s);
+// variant 0: 8 x 8 output tiles, inner index split 4 ways; 1: 16 x 16 tiles and
+// 2: 32 x 32 tiles, both with 16-wide k slabs staged in shared memory
+int launch_square_grouped(const SqItem* items, int nitems, int64_t tiles, int variant, cudaStream_t s);
 int launch_convert_grouped(const SqItem* items, int nitems, int64_t tiles, cudaStream_t s);
 template <typename C>
 int launch_table_grouped(const TabItem<C>* items, int nitems, int64_t blocks, int max_logd, cudaStream_t s);
@@ -267,6 +270,8 @@ struct qpe_plan_s {
   cudaGraphExec_t graph_exec = nullptr;
   cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // QPE_FLAG_TIMING
   bool timed_kernel = false;  // ev[5], ev[6] bracket the top-level fused kernel of the last run
+  int sq_variant = 0;            // batched squaring tile variant (autotuned or forced)
+  float tune_ms[3] = {0, 0, 0};  // the autotuner's timing of each variant (ms)
   bool batched = false;
   qpe::BatchMeta bm;
   bool timed_run = false;  // the last enqueue recorded all five events

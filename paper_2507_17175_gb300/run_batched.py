@@ -20,6 +20,7 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--single", action="store_true", help="also time one plan per instance")
+    ap.add_argument("--autotune", action="store_true", help="let qpe_bind pick the squaring tiles")
     args = ap.parse_args(argv)
 
     import torch
@@ -28,7 +29,7 @@ def main(argv=None):
     prec = qpe.FP64 if args.prec == "fp64" else qpe.C64_FP32
     shapes = [(i.nmat, i.nmeas) for i in insts]
     stream = torch.cuda.Stream()
-    bp = qpe.BatchedPlan(shapes, prec, qpe.FLAG_GRAPH, stream=stream)
+    bp = qpe.BatchedPlan(shapes, prec, qpe.FLAG_GRAPH | (qpe.FLAG_AUTOTUNE if args.autotune else 0), stream=stream)
     dev_inputs = [(torch.from_numpy(i.U).cuda(), torch.from_numpy(i.psi).cuda()) for i in insts]
     for k, (U, psi) in enumerate(dev_inputs):
         bp.load(k, U, psi)
@@ -47,6 +48,7 @@ def main(argv=None):
     res = {"workload": f"{args.count} instances, Nmat 3..10, Nmeas 8..18", "prec": args.prec,
            "batched_ms": min(times), "batched_runs_per_s": 1e3 / min(times),
            "launches_per_run": bp.query(qpe.INFO_LAST_LAUNCHES),
+           "square_tile": bp.query(qpe.INFO_SQUARE_TILE),
            "workspace_gib": bp.ws_bytes / 2 ** 30}
     del bp
     torch.cuda.empty_cache()

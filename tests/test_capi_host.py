@@ -61,7 +61,8 @@ def test_plan_sizes_workspace(q):
     (2, 31, 0, 0, "ERR_ARG"),
     (2, 4, 7, 0, "ERR_ARG"),
     (2, 4, -1, 0, "ERR_ARG"),
-    (2, 4, 0, 0x80, "ERR_ARG"),
+    (2, 4, 0, 0x100, "ERR_ARG"),
+    (2, 4, 0, 0x80, "OK"),    # QPE_FLAG_AUTOTUNE
     (2, 4, 2, 0, "ERR_UNSUPPORTED"),
     (7, 4, 1, 1, "ERR_UNSUPPORTED"),
     (12, 30, 1, 0, "OK"),

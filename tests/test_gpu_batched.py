@@ -120,3 +120,42 @@ def test_precision_study_matches_oracle_readout(q):
             ew.append(readout.phase_weighted_mean(P))
         assert abs(r["err_max_norm"] - float(np.mean(np.abs(np.array(em) - ph)))) < 1e-9
         assert abs(r["err_weighted_mean"] - float(np.mean(np.abs(np.array(ew) - ph)))) < 1e-9
+
+
+# ------------------------------------------------- squaring tile variants
+BIG = [(8, 6), (3, 9), (9, 4), (6, 7), (10, 3), (5, 8)]
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forced_square_tiles_match_oracle(q, tile, prec, monkeypatch):
+    """Every tile variant of the grouped FP64 squaring gives the same
+    histograms (FP64 summation order differs only)."""
+    monkeypatch.setenv("QPE_SQUARE_TILE", str(tile))
+    rng = np.random.default_rng(tile + prec)
+    insts = [W.haar_instance(rng, a, b, superposition=True) for a, b in BIG]
+    bp = q.BatchedPlan(BIG, prec, 0x8 if prec else 0)
+    assert bp.query(q.INFO_SQUARE_TILE) == tile
+    for i, inst in enumerate(insts):
+        bp.load(i, inst.U, inst.psi)
+    bp.run()
+    for i, inst in enumerate(insts):
+        P, *_ = bp.probs(i)
+        ref = gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas)
+        assert np.abs(P - ref).max() <= TOL[prec], (tile, BIG[i])
+
+
+def test_autotuned_plan(q, monkeypatch):
+    monkeypatch.delenv("QPE_SQUARE_TILE", raising=False)
+    rng = np.random.default_rng(5)
+    insts = [W.haar_instance(rng, a, b, superposition=True) for a, b in BIG]
+    bp = q.BatchedPlan(BIG, q.C64_FP32, q.FLAG_AUTOTUNE | q.FLAG_GRAPH)
+    assert bp.query(q.INFO_SQUARE_TILE) in (8, 16, 32)
+    for i, inst in enumerate(insts):
+        bp.load(i, inst.U, inst.psi)
+    for _ in range(2):
+        bp.run()
+        for i, inst in enumerate(insts):
+            P, *_ = bp.probs(i)
+            ref = gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas)
+            assert np.abs(P - ref).max() <= TOL[1]
