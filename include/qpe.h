@@ -103,6 +103,13 @@ typedef enum {
                                 /* squaring step and keeps the fastest (the    */
                                 /* environment variable QPE_SQUARE_TILE = 8,   */
                                 /* 16 or 32 forces one instead)                */
+#define QPE_FLAG_SQUARE_TC 0x100u /* U^(2^k) squarings of d >= 256 on the  */
+                                  /* tcgen05 tensor cores with FP64-grade     */
+                                  /* accuracy: 7 balanced 8-bit digits per     */
+                                  /* entry (row / column power-of-two scales), */
+                                  /* 28 exact bf16 digit products accumulated  */
+                                  /* in integers (the Ozaki scheme); single-   */
+                                  /* instance plans                            */
 #define QPE_FLAG_CHECK_UNITARY 0x40u /* the POWERS stage first forms U^dagger */
                                      /* U in FP64; if any entry of            */
                                      /* U^dagger U - I exceeds 1e-8 in        */

@@ -74,6 +74,8 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   in.off_scalars = take(sizeof(qpe::Scalars));
   in.off_err = take(sizeof(int));
   if (is_tc(prec)) in.off_tcsplit = take(qpe::tc_split_bytes(prec, in.nmat, in.nmeas));
+  in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
+  if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
   in.fft = qpe::make_fft_plan(in.nmeas, d, elem_size(prec));
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a
@@ -99,7 +101,7 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
   if (desc->nmeas < 1 || desc->nmeas > kMaxNmeas) return QPE_ERR_ARG;
   if (desc->prec < QPE_FP64 || desc->prec > QPE_C64_TF32X3) return QPE_ERR_ARG;
   if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE |
-                      QPE_FLAG_REPEAT_U | QPE_FLAG_CHECK_UNITARY | QPE_FLAG_AUTOTUNE))
+                      QPE_FLAG_REPEAT_U | QPE_FLAG_CHECK_UNITARY | QPE_FLAG_AUTOTUNE | QPE_FLAG_SQUARE_TC))
     return QPE_ERR_ARG;
   if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
     return QPE_ERR_UNSUPPORTED;
@@ -165,7 +167,8 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
   for (Instance& in : p->inst) {
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
     // the error word covers one run: cleared where the run's first checked stage begins
-    if ((first == QPE_STAGE_POWERS && (check_u || is_tc(p->prec))) || (first == QPE_STAGE_SWEEP && is_tc(p->prec))) {
+    if ((first == QPE_STAGE_POWERS && (check_u || is_tc(p->prec) || in.oz_square)) ||
+        (first == QPE_STAGE_SWEEP && is_tc(p->prec))) {
       cudaError_t e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
     }
@@ -676,7 +679,7 @@ qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* w
     if (st != QPE_OK) return st;
     if (descs[i].prec != descs[0].prec || descs[i].flags != descs[0].flags) return QPE_ERR_ARG;
   }
-  if (descs[0].flags & (QPE_FLAG_GATE_SWEEP | QPE_FLAG_TIMING)) return QPE_ERR_UNSUPPORTED;
+  if (descs[0].flags & (QPE_FLAG_GATE_SWEEP | QPE_FLAG_TIMING | QPE_FLAG_SQUARE_TC)) return QPE_ERR_UNSUPPORTED;
   qpe_plan_s* p = new (std::nothrow) qpe_plan_s();
   if (!p) return QPE_ERR_ARG;
   p->prec = descs[0].prec;
@@ -712,7 +715,7 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
     return fail(p, QPE_ERR_ARG, "QPE_FLAG_GRAPH needs a non-default stream");
   cudaError_t e = qpe::configure_kernels();
   if (e == cudaSuccess) e = qpe::configure_batched_kernels();
-  if (e == cudaSuccess && is_tc(p->prec)) e = qpe::configure_tc_kernels();
+  if (e == cudaSuccess && (is_tc(p->prec) || (p->flags & QPE_FLAG_SQUARE_TC))) e = qpe::configure_tc_kernels();
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute");
   {
     const char* v = getenv("QPE_PDL");

@@ -166,6 +166,8 @@ struct Instance {
   size_t off_scalars;   // Scalars
   size_t off_err = 0;   // int32 device error word (bounded waits)
   size_t off_tcsplit = 0;  // split operands of the tensor-core levels
+  size_t off_ozsq = 0;     // scales + digit slices of the tensor-core squaring
+  bool oz_square = false;  // U^(2^k) squared on the tensor cores (QPE_FLAG_SQUARE_TC, d >= 256)
   size_t state_bytes;
   bool has_state = true;  // the workspace holds an N x d state buffer
   FftPlan fft;
@@ -288,6 +290,8 @@ int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s);
 int launch_check_unitary(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, int prec = 1);
 int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s);
+size_t oz_square_bytes(int nmat);
+int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStream_t s);
 size_t tc_split_bytes(int prec, int nmat, int nmeas);
 cudaError_t configure_tc_kernels();
 template <typename C> int launch_fft(const Instance& in, char* ws, cudaStream_t s);

@@ -563,6 +563,12 @@ int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s) {
   int launches = 0;
   for (int k = 1; k < in.nmeas; ++k) {
     // complex64 copies ride along: P_k from the squaring that makes it, P_0 from the first one
+    if (in.oz_square) {
+      const int r = launch_square_oz(in, ws, k, want_c64, s);
+      if (r < 0) return -1;
+      launches += r;
+      continue;
+    }
     if (launch_square(P + (k - 1) * dd, P + k * dd, (int)in.d, P32 ? P32 + k * dd : nullptr,
                       (P32 && k == 1) ? P32 : nullptr, s) < 0)
       return -1;

@@ -445,6 +445,321 @@ __global__ void embed_split_kernel(const double2* __restrict__ P, void* __restri
   pdl_trigger();
 }
 
+// ------------------------------------- FP64-accurate squaring (Ozaki scheme)
+// P_(k+1) = P_k^2 on the tensor cores with the accuracy of an FP64 product.
+// Over reals, with E = [[Re P, -Im P], [Im P, Re P]] (2d x 2d), the first d
+// columns of E^2 are [Re P^2 ; Im P^2]; so out = E (2d x 2d) times
+// B^T, B[n][kk] = E[kk][n] (n < d, K-major). Every entry of row m of E is
+// written as x = 2^(tau_m - 55) sum_{s=1..7} a_s 2^(8 (7 - s)) with balanced
+// integer digits |a_s| <= 128 (round to nearest at 2^(tau_m - 55), |x| <
+// 2^tau_m), and every entry of column n of B likewise with sigma_n. Digits are
+// exact in bf16 and the product of two is an exact integer below 2^14, so
+// tcgen05 MMAs with FP32 accumulation sum them exactly as long as a partial
+// sum stays below 2^24: the digit pairs (s, t) of one weight u = s + t (at
+// most 7 pairs) go into one tensor-memory accumulator per 64-element K-block
+// (at most 7 * 64 * 2^14 < 2^23), which the drain warps convert to integers
+// and add into int32 registers (at most 128 K-blocks: < 2^30). The pairs with
+// u <= 8 are formed (28 bf16 products); the rest lie below 2^-53 of
+// 2^(tau + sigma) K. At the end of each weight the integer sums are folded in
+// FP64, val += acc_u 2^(-8 u), and out = val 2^(tau_m + sigma_n + 2).
+constexpr int kOzS = 7;       // digits per operand entry
+constexpr int kOzBeta = 8;    // bits per digit
+constexpr int kOzBN = 64;     // output columns per CTA
+constexpr int kOzStages = 6;  // TMA ring stages (A 16 KiB + B 8 KiB each)
+
+__device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// exponent t with 0 < |x| < 2^t for the largest |x| of a row or column; tiny
+// or zero lines get a floor (their digits are all zero)
+__device__ __forceinline__ int oz_exponent(double mx) {
+  if (!(mx > 0x1p-900)) return -900;
+  const int eb = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+  return eb + 1;
+}
+
+// tau[i]: scale of rows i and i + d of E (from row i of P); sig[j]: of column
+// j of [Re P ; Im P]. A non-finite entry sets the error word.
+__global__ void __launch_bounds__(256) oz_scale_kernel(const double2* __restrict__ P, int d, int* __restrict__ tau,
+                                                       int* __restrict__ sig, int* __restrict__ err) {
+  pdl_begin();
+  const int b = blockIdx.x;
+  double mx = 0.0;
+  bool finite = true;
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    const double2 p = b < d ? P[(int64_t)b * d + k] : P[(int64_t)k * d + (b - d)];
+    finite = finite && isfinite(p.x) && isfinite(p.y);
+    mx = fmax(mx, fmax(fabs(p.x), fabs(p.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ double wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  if (__syncthreads_or(!finite) && threadIdx.x == 0) atomicCAS(err, 0, (int)QPE_ERR_NUMERIC);
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wm[w]);
+    mx = fmax(mx, wm[0]);
+    const int e = oz_exponent(mx);
+    if (b < d)
+      tau[b] = e;
+    else
+      sig[b - d] = e;
+  }
+  pdl_trigger();
+}
+
+// balanced base-2^8 digits of x at scale 2^t, most significant first:
+// out[s * stride], s = 0 .. kOzS - 1
+__device__ __forceinline__ void oz_digits(double x, int t, __nv_bfloat16* out, int64_t stride) {
+  long long F = __double2ll_rn(x * pow2d(kOzS * kOzBeta - 1 - t));  // |F| < 2^55
+#pragma unroll
+  for (int s = kOzS - 1; s >= 1; --s) {
+    long long r = F & 255;
+    if (r >= 128) r -= 256;
+    out[(int64_t)s * stride] = __float2bfloat16_rn((float)r);
+    F = (F - r) / 256;
+  }
+  out[0] = __float2bfloat16_rn((float)F);
+}
+
+// digits of E (rows 2d, K = 2d) per slice: A[(s 2d + m) 2d + kk]; also the
+// complex64 copy of P when A32 is given
+__global__ void __launch_bounds__(256) oz_slice_a_kernel(const double2* __restrict__ P, int d,
+                                                         const int* __restrict__ tau, __nv_bfloat16* __restrict__ A,
+                                                         float2* __restrict__ A32) {
+  pdl_begin();
+  const int64_t dd = (int64_t)d * d, d2 = 2 * (int64_t)d, stride = d2 * d2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dd; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d, j = e - i * d;
+    const double2 p = P[e];
+    if (A32) A32[e] = make_float2((float)p.x, (float)p.y);
+    const int t = tau[i];
+    oz_digits(p.x, t, A + i * d2 + j, stride);             // E[i][j]     = Re
+    oz_digits(p.x, t, A + (i + d) * d2 + j + d, stride);   // E[i+d][j+d] = Re
+    oz_digits(-p.y, t, A + i * d2 + j + d, stride);        // E[i][j+d]   = -Im
+    oz_digits(p.y, t, A + (i + d) * d2 + j, stride);       // E[i+d][j]   = Im
+  }
+  pdl_trigger();
+}
+
+// digits of B (rows d, K = 2d): B[(s d + n) 2d + kk] = digits of E[kk][n]
+__global__ void __launch_bounds__(256) oz_slice_b_kernel(const double2* __restrict__ P, int d,
+                                                         const int* __restrict__ sig, __nv_bfloat16* __restrict__ B) {
+  pdl_begin();
+  const int64_t dd = (int64_t)d * d, d2 = 2 * (int64_t)d, stride = (int64_t)d * d2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dd; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / d, kk = e - n * d;  // consecutive threads: consecutive kk (contiguous writes)
+    const double2 p = P[kk * d + n];
+    const int t = sig[n];
+    oz_digits(p.x, t, B + n * d2 + kk, stride);      // E[kk][n]   = Re P[kk][n]
+    oz_digits(p.y, t, B + n * d2 + kk + d, stride);  // E[kk+d][n] = Im P[kk][n]
+  }
+  pdl_trigger();
+}
+
+struct OzArgs {
+  const int* tau;
+  const int* sig;
+  double2* C;    // P_(k+1), complex128 d x d
+  float2* C32;   // its complex64 copy, or null
+  int d;
+  int* err;
+};
+
+// One CTA per 128 x 64 tile of out (rows of E, columns n < d); roles as in
+// tc_gemm_kernel: warp 0 lane 0 TMA producer, warp 1 lane 0 MMA issuer, warps
+// 2..5 drain (one tile row per thread). Stages run weight by weight
+// (u = 2 .. 8), K-block by K-block, digit pair by digit pair.
+__global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB, OzArgs a) {
+  pdl_begin();
+  constexpr int A_BYTES = kBM * 128;
+  constexpr int B_BYTES = kOzBN * 128;
+  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int VLD = kOzBN + 1;  // padded row of the FP64 fold buffer
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  unsigned char* ring =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  double* val = reinterpret_cast<double*>(ring + kOzStages * STAGE_BYTES);  // [128][VLD]
+  __shared__ uint64_t full_bar[kOzStages], empty_bar[kOzStages], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int d = a.d, d2 = 2 * d;
+  const int m_tiles = d2 / kBM, n_tiles = d / kOzBN;
+  int m_tile, n_tile;
+  {
+    const int bid = blockIdx.x;
+    const int per_group = kGroupM * n_tiles;
+    const int g = bid / per_group;
+    const int first = g * kGroupM;
+    const int gm = (m_tiles - first) < kGroupM ? (m_tiles - first) : kGroupM;
+    const int local = bid - g * per_group;
+    m_tile = first + local % gm;
+    n_tile = local / gm;
+  }
+  const int m0 = m_tile * kBM, n0 = n_tile * kOzBN;
+  const int kblocks = d2 / 64;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kOzStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)(2 * kOzBN))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool go = true;
+      for (int u = 2; u <= kOzS + 1 && go; ++u)
+        for (int kb = 0; kb < kblocks && go; ++kb)
+          for (int s = 1; s < u; ++s, ++it) {
+            const int st = it % kOzStages;
+            if (it >= kOzStages && !mbar_wait(&empty_bar[st], ((it / kOzStages) - 1) & 1)) {
+              atomicExch(&fail, 1);
+              go = false;
+              break;
+            }
+            if (*((volatile int*)&fail)) {
+              go = false;
+              break;
+            }
+            unsigned char* sa = ring + st * STAGE_BYTES;
+            mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+            tma_load_2d(sa, &mapA, &full_bar[st], kb * 64, (s - 1) * d2 + m0);
+            tma_load_2d(sa + A_BYTES, &mapB, &full_bar[st], kb * 64, (u - s - 1) * d + n0);
+          }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc<kTcBF16, kOzBN>();
+      int it = 0, g = 0;
+      bool go = true;
+      for (int u = 2; u <= kOzS + 1 && go; ++u)
+        for (int kb = 0; kb < kblocks && go; ++kb, ++g) {
+          const int b = g & 1;
+          if (g >= 2 && !mbar_wait(&acc_empty[b], ((g >> 1) - 1) & 1)) {
+            atomicExch(&fail, 1);
+            go = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int s = 1; s < u; ++s, ++it) {
+            const int st = it % kOzStages;
+            if (!mbar_wait(&full_bar[st], (it / kOzStages) & 1)) {
+              atomicExch(&fail, 1);
+              go = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(ring + st * STAGE_BYTES);
+            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              umma_k<kTcBF16>(tmem + (uint32_t)(b * kOzBN), ad + 2 * k, bd + 2 * k, idesc,
+                              (s == 1 && k == 0) ? 0u : 1u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty_bar[st]))
+                         : "memory");
+          }
+          if (!go) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&acc_full[b]))
+                       : "memory");
+        }
+    }
+  } else {
+    const int lg = warp & 3;
+    const int row = lg * 32 + lane;  // tile row of this thread
+    int acc[kOzBN];
+    bool ok = true;
+    int g = 0;
+    for (int u = 2; u <= kOzS + 1 && ok; ++u) {
+      for (int kb = 0; kb < kblocks && ok; ++kb, ++g) {
+        const int b = g & 1;
+        bool got = mbar_wait(&acc_full[b], (g >> 1) & 1);
+        got = __all_sync(0xffffffffu, got && !*((volatile int*)&fail)) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!got) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int q = 0; q < kOzBN / 32; ++q) {
+          uint32_t v[32];
+          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * kOzBN + q * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+              "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+              "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int x = __float2int_rn(__uint_as_float(v[i]));  // an exact integer below 2^23
+            acc[q * 32 + i] = kb == 0 ? x : acc[q * 32 + i] + x;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+      }
+      if (!ok) break;
+      const double w = pow2d(-kOzBeta * u);
+      double* vr = val + row * VLD;
+#pragma unroll
+      for (int n = 0; n < kOzBN; ++n) vr[n] = (u == 2 ? 0.0 : vr[n]) + (double)acc[n] * w;
+    }
+    if (ok) {
+      const int gm = m0 + row;  // row of E
+      const int i = gm < d ? gm : gm - d;
+      const int t = a.tau[i];
+      double* vr = val + row * VLD;
+      for (int n = 0; n < kOzBN; ++n) {
+        const int col = n0 + n;
+        const int e = t + a.sig[col] + 2;
+        const double c = vr[n] == 0.0 ? 0.0 : vr[n] * pow2d(e < -1022 ? -1022 : e);
+        double* dst = reinterpret_cast<double*>(a.C + (int64_t)i * d + col) + (gm < d ? 0 : 1);
+        *dst = c;
+        if (a.C32) reinterpret_cast<float*>(a.C32 + (int64_t)i * d + col)[gm < d ? 0 : 1] = (float)c;
+      }
+    } else {
+      atomicExch(&fail, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (fail && threadIdx.x == 0) atomicExch(a.err, (int)QPE_ERR_TIMEOUT);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * kOzBN))
+                 : "memory");
+  }
+  pdl_trigger();
+}
+
 // ------------------------------------------------------------ host side
 namespace {
 
@@ -485,6 +800,8 @@ size_t tc_smem() {
   return (size_t)kStages * (kBM * 128 + BN * 128) + 1024;
 }
 
+size_t oz_smem() { return (size_t)kOzStages * (kBM * 128 + kOzBN * 128) + (size_t)kBM * (kOzBN + 1) * 8 + 1024; }
+
 }  // namespace
 
 cudaError_t configure_tc_kernels() {
@@ -499,7 +816,45 @@ cudaError_t configure_tc_kernels() {
   QPE_TC_ATTR(kTcFP16, 64)
   QPE_TC_ATTR(kTcFP16, 128)
 #undef QPE_TC_ATTR
-  return cudaSuccess;
+  return cudaFuncSetAttribute(oz_square_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
+}
+
+// Workspace of the tensor-core squaring: row / column scales and the digit
+// slices of E (kOzS x 2d x 2d) and of B (kOzS x d x 2d), bf16.
+size_t oz_square_bytes(int nmat) {
+  const size_t d = (size_t)1 << nmat;
+  return 256 + 2 * d * sizeof(int) + 256 + (size_t)kOzS * (4 * d * d + 2 * d * d) * 2;
+}
+
+// P_k = P_(k-1)^2 on the tensor cores (d >= 256): scales, digit slices, GEMM.
+// want_c64 also writes the complex64 copies (P_k, and P_0 when k = 1).
+int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStream_t s) {
+  const int d = (int)in.d;
+  const int64_t dd = in.d * in.d;
+  const double2* P = reinterpret_cast<const double2*>(ws + in.off_pow64) + (k - 1) * dd;
+  double2* C = reinterpret_cast<double2*>(ws + in.off_pow64) + k * dd;
+  float2* P32 = want_c64 ? reinterpret_cast<float2*>(ws + in.off_pow32) : nullptr;
+  char* base = ws + in.off_ozsq;
+  int* tau = reinterpret_cast<int*>(base);
+  int* sig = tau + d;
+  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(base + ((2 * (size_t)d * sizeof(int) + 255) & ~size_t(255)));
+  __nv_bfloat16* B = A + (size_t)kOzS * 4 * dd;
+  int* err = reinterpret_cast<int*>(ws + in.off_err);
+  cudaError_t e = launch_k(oz_scale_kernel, dim3(2 * d), dim3(256), 0, s, P, d, tau, sig, err);
+  const unsigned eb = (unsigned)std::min<int64_t>((dd + 255) / 256, 152 * 16);
+  if (e == cudaSuccess)
+    e = launch_k(oz_slice_a_kernel, dim3(eb), dim3(256), 0, s, P, d, (const int*)tau, A,
+                 (P32 && k == 1) ? P32 : (float2*)nullptr);
+  if (e == cudaSuccess) e = launch_k(oz_slice_b_kernel, dim3(eb), dim3(256), 0, s, P, d, (const int*)sig, B);
+  if (e != cudaSuccess) return -1;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, A, kTcBF16, (int64_t)kOzS * 2 * d, 2 * (int64_t)d, kBM) ||
+      !make_map(&mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, kOzBN))
+    return -1;
+  OzArgs a{tau, sig, C, P32 ? P32 + k * dd : nullptr, d, err};
+  const unsigned grid = (unsigned)((2 * d / kBM) * (d / kOzBN));
+  e = launch_k(oz_square_kernel, dim3(grid), dim3(192), oz_smem(), s, mA, mB, a);
+  return e == cudaSuccess ? 4 : -1;
 }
 
 // Split buffers (bytes) a plan of this precision needs for the largest level.

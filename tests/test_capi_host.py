@@ -61,7 +61,8 @@ def test_plan_sizes_workspace(q):
     (2, 31, 0, 0, "ERR_ARG"),
     (2, 4, 7, 0, "ERR_ARG"),
     (2, 4, -1, 0, "ERR_ARG"),
-    (2, 4, 0, 0x100, "ERR_ARG"),
+    (2, 4, 0, 0x200, "ERR_ARG"),
+    (9, 8, 1, 0x100, "OK"),   # QPE_FLAG_SQUARE_TC
     (2, 4, 0, 0x80, "OK"),    # QPE_FLAG_AUTOTUNE
     (2, 4, 2, 0, "ERR_UNSUPPORTED"),
     (7, 4, 1, 1, "ERR_UNSUPPORTED"),
