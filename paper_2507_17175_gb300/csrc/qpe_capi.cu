@@ -290,7 +290,7 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
     bm.sq_begin[k] = (int)bm.sq.size();
     int64_t tiles = 0, tiles16 = 0, tiles32 = 0;
     for (Instance& in : p->inst) {
-      if (in.nmeas <= k) continue;
+      if (in.nmeas <= k || in.oz_square) continue;  // tensor-core squarings are launched per instance
       const int64_t dd = in.d * in.d;
       double2* P = reinterpret_cast<double2*>(ws + in.off_pow64);
       float2* P32 = c64 ? reinterpret_cast<float2*>(ws + in.off_pow32) : nullptr;
@@ -567,11 +567,20 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
       if (!chk(qpe::launch_check_unitary(in, ws, p->stream))) return cuda_fail(p, cudaGetLastError(), "unitarity check");
     }
   }
-  for (int k = 1; k < bm.maxn; ++k)
+  for (Instance& in : p->inst)
+    if (in.oz_square && !(p->flags & QPE_FLAG_CHECK_UNITARY)) {  // (the unitarity check cleared it already)
+      cudaError_t e = cudaMemsetAsync(ws + in.off_err, 0, sizeof(int), p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
+    }
+  for (int k = 1; k < bm.maxn; ++k) {
     if (!chk(qpe::launch_square_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_sq) + bm.sq_begin[k],
                                         bm.sq_count[k], square_tiles(bm, k, p->sq_variant), p->sq_variant,
                                         p->stream)))
       return cuda_fail(p, cudaGetLastError(), "grouped squaring");
+    for (Instance& in : p->inst)
+      if (in.oz_square && in.nmeas > k && !chk(qpe::launch_square_oz(in, ws, k, c64, p->stream)))
+        return cuda_fail(p, cudaGetLastError(), "tensor-core squaring");
+  }
   if (!chk(qpe::launch_convert_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_conv), (int)bm.conv.size(),
                                        bm.conv_tiles, p->stream)))
     return cuda_fail(p, cudaGetLastError(), "grouped conversion");
@@ -679,7 +688,7 @@ qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* w
     if (st != QPE_OK) return st;
     if (descs[i].prec != descs[0].prec || descs[i].flags != descs[0].flags) return QPE_ERR_ARG;
   }
-  if (descs[0].flags & (QPE_FLAG_GATE_SWEEP | QPE_FLAG_TIMING | QPE_FLAG_SQUARE_TC)) return QPE_ERR_UNSUPPORTED;
+  if (descs[0].flags & (QPE_FLAG_GATE_SWEEP | QPE_FLAG_TIMING)) return QPE_ERR_UNSUPPORTED;
   qpe_plan_s* p = new (std::nothrow) qpe_plan_s();
   if (!p) return QPE_ERR_ARG;
   p->prec = descs[0].prec;

@@ -21,6 +21,7 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--single", action="store_true", help="also time one plan per instance")
     ap.add_argument("--autotune", action="store_true", help="let qpe_bind pick the squaring tiles")
+    ap.add_argument("--square-tc", action="store_true", help="square U^(2^k) of d >= 256 on the tensor cores")
     args = ap.parse_args(argv)
 
     import torch
@@ -29,7 +30,8 @@ def main(argv=None):
     prec = qpe.FP64 if args.prec == "fp64" else qpe.C64_FP32
     shapes = [(i.nmat, i.nmeas) for i in insts]
     stream = torch.cuda.Stream()
-    bp = qpe.BatchedPlan(shapes, prec, qpe.FLAG_GRAPH | (qpe.FLAG_AUTOTUNE if args.autotune else 0), stream=stream)
+    flags = qpe.FLAG_GRAPH | (qpe.FLAG_AUTOTUNE if args.autotune else 0) | (qpe.FLAG_SQUARE_TC if args.square_tc else 0)
+    bp = qpe.BatchedPlan(shapes, prec, flags, stream=stream)
     dev_inputs = [(torch.from_numpy(i.U).cuda(), torch.from_numpy(i.psi).cuda()) for i in insts]
     for k, (U, psi) in enumerate(dev_inputs):
         bp.load(k, U, psi)
@@ -46,6 +48,7 @@ def main(argv=None):
             stream.synchronize()
             times.append(e0.elapsed_time(e1))
     res = {"workload": f"{args.count} instances, Nmat 3..10, Nmeas 8..18", "prec": args.prec,
+           "square_tc": bool(args.square_tc),
            "batched_ms": min(times), "batched_runs_per_s": 1e3 / min(times),
            "launches_per_run": bp.query(qpe.INFO_LAST_LAUNCHES),
            "square_tile": bp.query(qpe.INFO_SQUARE_TILE),
@@ -57,7 +60,7 @@ def main(argv=None):
         total_launches = 0
         t_single = 0.0
         for inst, (U, psi) in zip(insts, dev_inputs):
-            p = qpe.Plan(inst.nmat, inst.nmeas, prec, 0, stream=stream)
+            p = qpe.Plan(inst.nmat, inst.nmeas, prec, qpe.FLAG_SQUARE_TC if args.square_tc else 0, stream=stream)
             p.load(U, psi)
             with torch.cuda.stream(stream):
                 p.run()

@@ -107,3 +107,21 @@ def test_nan_is_reported(q):
     with pytest.raises(q.QpeError) as e:
         plan.probs()
     assert e.value.status == q.ERR_NUMERIC
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_mix_with_tensor_core_squaring(q, prec):
+    """Instances with d >= 256 square on the tensor cores, the others in the
+    grouped FP64 launches, in one plan."""
+    shapes = [(8, 7), (3, 9), (9, 5), (6, 8), (10, 4), (2, 6)]
+    rng = np.random.default_rng(21 + prec)
+    insts = [W.haar_instance(rng, a, b, superposition=True) for a, b in shapes]
+    bp = q.BatchedPlan(shapes, prec, q.FLAG_SQUARE_TC | q.FLAG_GRAPH)
+    for i, inst in enumerate(insts):
+        bp.load(i, inst.U, inst.psi)
+    for _ in range(2):
+        bp.run()
+        for i, inst in enumerate(insts):
+            P, *_ = bp.probs(i)
+            ref = gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas)
+            assert np.abs(P - ref).max() <= (1e-10 if prec == 0 else 1e-5), shapes[i]
