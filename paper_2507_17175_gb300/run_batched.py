@@ -13,6 +13,8 @@ import argparse
 import json
 import time
 
+import numpy as np
+
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
@@ -22,6 +24,8 @@ def main(argv=None):
     ap.add_argument("--single", action="store_true", help="also time one plan per instance")
     ap.add_argument("--autotune", action="store_true", help="let qpe_bind pick the squaring tiles")
     ap.add_argument("--square-tc", action="store_true", help="square U^(2^k) of d >= 256 on the tensor cores")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also run the plain FP64 batched plan and report the histograms' L1 difference")
     args = ap.parse_args(argv)
 
     import torch
@@ -47,6 +51,7 @@ def main(argv=None):
             e1.record(stream)
             stream.synchronize()
             times.append(e0.elapsed_time(e1))
+    hists = [bp.probs(k)[0] for k in range(len(insts))] if args.compare_fp64 else None
     res = {"workload": f"{args.count} instances, Nmat 3..10, Nmeas 8..18", "prec": args.prec,
            "square_tc": bool(args.square_tc),
            "batched_ms": min(times), "batched_runs_per_s": 1e3 / min(times),
@@ -55,6 +60,27 @@ def main(argv=None):
            "workspace_gib": bp.ws_bytes / 2 ** 30}
     del bp
     torch.cuda.empty_cache()
+    if hists is not None:
+        ref = qpe.BatchedPlan(shapes, qpe.FP64, qpe.FLAG_GRAPH, stream=stream)
+        for k, (U, psi) in enumerate(dev_inputs):
+            ref.load(k, U, psi)
+        with torch.cuda.stream(stream):
+            ref.run()
+            e0.record(stream)
+            ref.run()
+            e1.record(stream)
+            stream.synchronize()
+        l1, mx, same = [], [], 0
+        for k in range(len(insts)):
+            Pr, amr, *_ = ref.probs(k)
+            l1.append(float(np.abs(hists[k] - Pr).sum()))
+            mx.append(float(np.abs(hists[k] - Pr).max()))
+            same += int(np.argmax(hists[k]) == amr)
+        res.update({"fp64_batched_ms": e0.elapsed_time(e1), "l1_vs_fp64_max": max(l1),
+                    "l1_vs_fp64_median": float(np.median(l1)), "maxabs_vs_fp64": max(mx),
+                    "argmax_equal": f"{same}/{len(insts)}"})
+        del ref
+        torch.cuda.empty_cache()
     if args.single:
         plans = []
         total_launches = 0
