@@ -298,6 +298,33 @@ struct FftArgs {
 
 __device__ __forceinline__ int bitrev(int x, int bits) { return bits ? (__brev(x) >> (32 - bits)) : 0; }
 
+// K consecutive radix-2 DIF stages on the rows row0 + j 2^logs (j < 2^K) of
+// column w, in registers (see fft_pass_kernel).
+template <typename C, int K>
+__device__ __forceinline__ void fft_group(C* tile, const C* twp, int W, int w, int row0, int logm, int logs,
+                                          int logr) {
+  constexpr int RK = 1 << K;
+  C x[RK];
+#pragma unroll
+  for (int j = 0; j < RK; ++j) x[j] = tile[(row0 + (j << logs)) * W + w];
+#pragma unroll
+  for (int lt = 0; lt < K; ++lt) {
+    const int logh = logm - lt - 1;  // global half size h = 2^logh
+#pragma unroll
+    for (int j = 0; j < RK; ++j) {
+      const int hh = RK >> (lt + 1);
+      if (j & hh) continue;
+      const C x0 = x[j], x1 = x[j + hh];
+      x[j] = cadd(x0, x1);
+      const C dlt = csub(x0, x1);
+      const int pos = (row0 + (j << logs)) & ((1 << logh) - 1);
+      x[j + hh] = pos ? cmul(dlt, twp[pos << (logr - logh - 1)]) : dlt;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < RK; ++j) tile[(row0 + (j << logs)) * W + w] = x[j];
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const C* __restrict__ tw_lo,
                                                        const C* __restrict__ tw_hi, FftArgs a) {
@@ -313,24 +340,47 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const 
   const int64_t qs = bid & ((int64_t(1) << slices_log) - 1);
   C* base = X + (blk << (a.logr + a.logq)) + (qs << a.logw);
   const int RW = R * W;
-  for (int idx = threadIdx.x; idx < RW; idx += blockDim.x) {
-    const int r = idx >> a.logw, w = idx & (W - 1);
-    tile[idx] = base[((int64_t)r << a.logq) + w];
+  C* twp = tile + RW;  // w_R^e = omega_N^(e << (n - logr)), e < R / 2: the pass's twiddles
+  // the tile arrives by asynchronous 16-byte copies (every thread's copies in
+  // flight at once) while the twiddles are computed
+  constexpr int V = 16 / (int)sizeof(C);  // elements per copy
+  if (W >= V) {
+    for (int idx = threadIdx.x * V; idx < RW; idx += blockDim.x * V) {
+      const int r = idx >> a.logw, w = idx & (W - 1);
+      cp_async16(tile + idx, base + ((int64_t)r << a.logq) + w);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < RW; idx += blockDim.x) {
+      const int r = idx >> a.logw, w = idx & (W - 1);
+      cp_async_elem(tile + idx, base + ((int64_t)r << a.logq) + w, true);
+    }
   }
+  cp_async_commit();
+  for (int e = threadIdx.x; e < (R >> 1); e += blockDim.x)
+    twp[e] = twiddle(tw_lo, tw_hi, a.htw, (int64_t)e << (a.n - a.logr));
+  cp_async_wait<0>();
   __syncthreads();
-  for (int s = 0; s < a.logr; ++s) {
-    const int logh = a.logr - s - 1;
-    const int h = 1 << logh;
-    const int tshift = a.n - logh - 1;  // omega_(2h)^pos = omega_N^(pos << (n - log2(2h)))
-    for (int idx = threadIdx.x; idx < (RW >> 1); idx += blockDim.x) {
-      const int p = idx >> a.logw, w = idx & (W - 1);
-      const int grp = p >> logh, pos = p & (h - 1);
-      const int i0 = ((grp << (logh + 1)) + pos) * W + w;
-      const int i1 = i0 + h * W;
-      const C x0 = tile[i0], x1 = tile[i1];
-      tile[i0] = cadd(x0, x1);
-      const C dlt = csub(x0, x1);
-      tile[i1] = pos ? cmul(dlt, twiddle(tw_lo, tw_hi, a.htw, (int64_t)pos << tshift)) : dlt;
+  // Radix-2 DIF stages s = 0 .. logr - 1 (stage s pairs rows p and p + h,
+  // h = 2^(logr - s - 1), twiddle omega_(2h)^(p mod h) on the difference),
+  // three at a time in registers: rows base + j S, j < 2^K, meet only each
+  // other within those K stages. The butterflies and twiddles are those of
+  // the stage-by-stage order, so the result is the same bit for bit.
+  for (int s0 = 0; s0 < a.logr; s0 += 3) {
+    const int K = a.logr - s0 < 3 ? a.logr - s0 : 3;
+    const int logm = a.logr - s0;  // sub-blocks of 2^logm rows
+    const int logs = logm - K;     // stride S = 2^logs between a task's rows
+    const int tasks = (R >> K) << a.logw;
+    for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
+      const int w = t & (W - 1);
+      const int rest = t >> a.logw;
+      const int q = rest & ((1 << logs) - 1);
+      const int b0 = rest >> logs;
+      const int row0 = (b0 << logm) + q;
+      switch (K) {
+        case 1: fft_group<C, 1>(tile, twp, W, w, row0, logm, logs, a.logr); break;
+        case 2: fft_group<C, 2>(tile, twp, W, w, row0, logm, logs, a.logr); break;
+        default: fft_group<C, 3>(tile, twp, W, w, row0, logm, logs, a.logr); break;
+      }
     }
     __syncthreads();
   }
@@ -410,9 +460,31 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
     double acc = 0.0;
     if (p < N) {
       const C* row = X + (p << logd);
-      for (int k = 0; k < per; ++k) {
-        const C v = row[sub + k * lpr];
-        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      if constexpr (sizeof(C) == 8) {
+        // complex64: squares and the lane's partial sum (d / 32 <= 128 terms) in
+        // FP32, two elements per 16-byte load when a lane owns >= 2; the sum
+        // across lanes and rows is FP64
+        float f = 0.f;
+        if (per >= 2) {
+          float comp = 0.f;  // Kahan compensation of the running FP32 sum
+          for (int k = 0; k < per; k += 2) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(row + 2 * sub + k * lpr));
+            const float term = fmaf(v.x, v.x, v.y * v.y) + fmaf(v.z, v.z, v.w * v.w);
+            const float y = term - comp;
+            const float t = f + y;
+            comp = (t - f) - y;
+            f = t;
+          }
+        } else {
+          const C v = row[sub];
+          f = fmaf(v.x, v.x, v.y * v.y);
+        }
+        acc = (double)f;
+      } else {
+        for (int k = 0; k < per; ++k) {
+          const C v = row[sub + k * lpr];
+          acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        }
       }
     }
     for (int off = lpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -697,7 +769,7 @@ int launch_fft(const Instance& in, char* ws, cudaStream_t s) {
     a.last = (i == in.fft.passes - 1);
     a.scale = a.last ? final_scale : 1.0;
     const int64_t blocks = p.B * (p.Q / p.W);
-    const size_t smem = (size_t)(int64_t(1) << p.logr) * p.W * sizeof(C);
+    const size_t smem = ((size_t)(int64_t(1) << p.logr) * p.W + ((size_t)1 << p.logr) / 2) * sizeof(C);
     if (launch_k(fft_pass_kernel<C>, dim3((unsigned)blocks), dim3(256), smem, s, X, lo, hi, a) != cudaSuccess)
       return -1;
     ++launches;
@@ -740,10 +812,11 @@ int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t
 cudaError_t configure_kernels() {
   cudaError_t e = configure_level_kernels();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(fft_pass_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       64 * 1024);
+  // tile (<= 64 KiB) + the pass's twiddles (<= 256 entries)
+  e = cudaFuncSetAttribute(fft_pass_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 4096);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fft_pass_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  return cudaFuncSetAttribute(fft_pass_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              64 * 1024 + 4096);
 }
 
 template int launch_sweep<float2>(const Instance&, char*, bool, cudaStream_t, int);
