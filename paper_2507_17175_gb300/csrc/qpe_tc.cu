@@ -20,8 +20,8 @@
 // by 2^14; the drain multiplies each output row by the exact inverse.
 //
 // Kernel: one CTA per 128 x BN output tile (BN <= 128), 192 threads. Warp 0
-// lane 0 issues TMA loads of A and B K-slabs (128-byte swizzled, one per
-// operand pair and K-block) into a 4-stage shared-memory ring; warp 1 lane 0
+// lane 0 issues TMA loads of the K-slabs A_hi, A_lo, B_hi, B_lo (128-byte
+// swizzled, one ring stage per K-block, 3 or 4 stages); warp 1 lane 0
 // issues tcgen05.mma (M = 128, N = BN, K = 32 bytes per instruction) into
 // double-buffered FP32 tensor-memory accumulators (hi.hi drained after every
 // K-block, the cross terms every 8); warps 2..5 drain each finished buffer
@@ -43,7 +43,12 @@ namespace qpe {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 4;  // most stages of any ring below
+
+// Stages of the controlled-gate GEMM's ring: one stage holds the four operand
+// tiles of a K-block (A_hi, A_lo, B_hi, B_lo), 64 KiB for BN = 128.
+template <int BN>
+__host__ __device__ constexpr int tc_stages() { return BN == 128 ? 3 : 4; }
 constexpr int kBM = 128;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -141,7 +146,7 @@ __device__ __forceinline__ uint32_t make_idesc() {
 // that K-block; the two cross products (about 2^-11 smaller) go to one of two
 // "cross" buffers drained every KPC K-blocks. Four drain warps do the adds
 // while the MMAs of the next K-blocks run.
-//   warp 0 lane 0   TMA producer (4-stage ring, one stage per operand pair)
+//   warp 0 lane 0   TMA producer (one stage = the four operand tiles of a K-block)
 //   warp 1 lane 0   MMA issuer
 //   warps 2..5      drain + epilogue; warp w owns tensor-memory lanes
 //                   32 (w % 4) .. +31, i.e. tile rows 32 (w % 4) .. +31
@@ -161,7 +166,8 @@ __global__ void __launch_bounds__(192, 1)
   constexpr int BK = 128 / ESZ;       // K elements per 128-byte swizzle row
   constexpr int A_BYTES = kBM * 128;  // 16 KiB
   constexpr int B_BYTES = BN * 128;
-  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);  // A_hi, A_lo, B_hi, B_lo of one K-block
+  constexpr int QS = tc_stages<BN>();
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* ring =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -191,7 +197,7 @@ __global__ void __launch_bounds__(192, 1)
   const int nchunks_x = (kblocks + kKPC - 1) / kKPC;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < QS; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -218,25 +224,24 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      const int iters = kblocks * 3;
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % kStages;
-        if (it >= kStages && !mbar_wait(&empty_bar[s], ((it / kStages) - 1) & 1)) {
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int st = kb % QS;
+        if (kb >= QS && !mbar_wait(&empty_bar[st], ((kb / QS) - 1) & 1)) {
           atomicExch(&fail, 1);
           break;
         }
         if (*((volatile int*)&fail)) break;
-        const int kb = it / 3, pr = it - kb * 3;
-        unsigned char* sa = ring + s * STAGE_BYTES;
-        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-        tma_load_2d(sa, pr == 2 ? &mapAlo : &mapAhi, &full_bar[s], kb * BK, (int)m0);
-        tma_load_2d(sa + A_BYTES, pr == 1 ? &mapBlo : &mapBhi, &full_bar[s], kb * BK, n0);
+        unsigned char* sa = ring + st * STAGE_BYTES;
+        mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+        tma_load_2d(sa, &mapAhi, &full_bar[st], kb * BK, (int)m0);
+        tma_load_2d(sa + A_BYTES, &mapAlo, &full_bar[st], kb * BK, (int)m0);
+        tma_load_2d(sa + 2 * A_BYTES, &mapBhi, &full_bar[st], kb * BK, n0);
+        tma_load_2d(sa + 2 * A_BYTES + B_BYTES, &mapBlo, &full_bar[st], kb * BK, n0);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = make_idesc<KIND, BN>();
-      int it = 0;
       for (int kb = 0; kb < kblocks; ++kb) {
         const int bm = kb & 1;                    // main buffer of this K-block
         const int cx = kb / kKPC, bx = cx & 1;    // cross chunk and its buffer
@@ -251,34 +256,30 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        bool ok = true;
-        for (int pr = 0; pr < 3; ++pr, ++it) {
-          const int s = it % kStages;
-          if (!mbar_wait(&full_bar[s], (it / kStages) & 1)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
-          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+        const int st = kb % QS;
+        if (!mbar_wait(&full_bar[st], (kb / QS) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(ring + st * STAGE_BYTES);
+        for (int pr = 0; pr < 3; ++pr) {  // (hi, hi), (hi, lo), (lo, hi)
+          const uint64_t ad = sw128_desc(pr == 2 ? sa + A_BYTES : sa);
+          const uint64_t bd = sw128_desc(sa + 2 * A_BYTES + (pr == 1 ? B_BYTES : 0));
           const uint32_t acc_addr = pr == 0 ? tmem + (uint32_t)(bm * BN) : tmem + (uint32_t)((2 + bx) * BN);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction
             const bool fresh = k == 0 && (pr == 0 || (pr == 1 && cx_first));
             umma_k<KIND>(acc_addr, ad + 2 * k, bd + 2 * k, idesc, fresh ? 0u : 1u);
           }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&empty_bar[s]))
-                       : "memory");
           if (pr == 0)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&main_full[bm]))
                          : "memory");
         }
-        if (!ok) {
-          atomicExch(&fail, 1);
-          break;
-        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&empty_bar[st]))
+                     : "memory");
         if (cx_last)
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&cross_full[bx]))
@@ -797,7 +798,7 @@ bool make_map(CUtensorMap* m, void* base, int kind, int64_t rows, int64_t K, int
 
 template <int KIND, int BN>
 size_t tc_smem() {
-  return (size_t)kStages * (kBM * 128 + BN * 128) + 1024;
+  return (size_t)tc_stages<BN>() * 2 * (kBM * 128 + BN * 128) + 1024;
 }
 
 size_t oz_smem() { return (size_t)kOzStages * (kBM * 128 + kOzBN * 128) + (size_t)kBM * (kOzBN + 1) * 8 + 1024; }
