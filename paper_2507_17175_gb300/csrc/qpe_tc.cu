@@ -465,8 +465,7 @@ __global__ void embed_split_kernel(const double2* __restrict__ P, void* __restri
 // FP64, val += acc_u 2^(-8 u), and out = val 2^(tau_m + sigma_n + 2).
 constexpr int kOzS = 7;       // digits per operand entry
 constexpr int kOzBeta = 8;    // bits per digit
-constexpr int kOzBN = 64;     // output columns per CTA
-constexpr int kOzStages = 6;  // TMA ring stages (A 16 KiB + B 8 KiB each)
+constexpr int kOzStages = 6;  // TMA ring stages (A 16 KiB + B BN x 128 B each)
 
 __device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023
   return __longlong_as_double((long long)(1023 + e) << 52);
@@ -567,21 +566,23 @@ struct OzArgs {
   int* err;
 };
 
-// One CTA per 128 x 64 tile of out (rows of E, columns n < d); roles as in
+// One CTA per 128 x BN tile of out (rows of E, columns n < d); roles as in
 // tc_gemm_kernel: warp 0 lane 0 TMA producer, warp 1 lane 0 MMA issuer, warps
 // 2..5 drain (one tile row per thread). Stages run weight by weight
-// (u = 2 .. 8), K-block by K-block, digit pair by digit pair.
+// (u = 2 .. 8), K-block by K-block, digit pair by digit pair. At the end of
+// each weight a drain thread folds its row's int32 sums into FP64 values kept
+// in its own row of the output (read back only by the same thread).
+template <int BN>
 __global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB, OzArgs a) {
   pdl_begin();
+  constexpr int kOzBN = BN;
   constexpr int A_BYTES = kBM * 128;
   constexpr int B_BYTES = kOzBN * 128;
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr int VLD = kOzBN + 1;  // padded row of the FP64 fold buffer
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* ring =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  double* val = reinterpret_cast<double*>(ring + kOzStages * STAGE_BYTES);  // [128][VLD]
   __shared__ uint64_t full_bar[kOzStages], empty_bar[kOzStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
@@ -730,21 +731,21 @@ __global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant
       }
       if (!ok) break;
       const double w = pow2d(-kOzBeta * u);
-      double* vr = val + row * VLD;
+      const int gm = m0 + row;  // row of E: real part of P row gm, or imaginary part of row gm - d
+      double* vr = reinterpret_cast<double*>(a.C + (int64_t)(gm < d ? gm : gm - d) * d + n0) + (gm < d ? 0 : 1);
 #pragma unroll
-      for (int n = 0; n < kOzBN; ++n) vr[n] = (u == 2 ? 0.0 : vr[n]) + (double)acc[n] * w;
+      for (int n = 0; n < kOzBN; ++n) vr[2 * n] = (u == 2 ? 0.0 : vr[2 * n]) + (double)acc[n] * w;
     }
     if (ok) {
-      const int gm = m0 + row;  // row of E
+      const int gm = m0 + row;
       const int i = gm < d ? gm : gm - d;
       const int t = a.tau[i];
-      double* vr = val + row * VLD;
+      double* vr = reinterpret_cast<double*>(a.C + (int64_t)i * d + n0) + (gm < d ? 0 : 1);
       for (int n = 0; n < kOzBN; ++n) {
         const int col = n0 + n;
         const int e = t + a.sig[col] + 2;
-        const double c = vr[n] == 0.0 ? 0.0 : vr[n] * pow2d(e < -1022 ? -1022 : e);
-        double* dst = reinterpret_cast<double*>(a.C + (int64_t)i * d + col) + (gm < d ? 0 : 1);
-        *dst = c;
+        const double c = vr[2 * n] == 0.0 ? 0.0 : vr[2 * n] * pow2d(e < -1022 ? -1022 : e);
+        vr[2 * n] = c;
         if (a.C32) reinterpret_cast<float*>(a.C32 + (int64_t)i * d + col)[gm < d ? 0 : 1] = (float)c;
       }
     } else {
@@ -801,7 +802,8 @@ size_t tc_smem() {
   return (size_t)tc_stages<BN>() * 2 * (kBM * 128 + BN * 128) + 1024;
 }
 
-size_t oz_smem() { return (size_t)kOzStages * (kBM * 128 + kOzBN * 128) + (size_t)kBM * (kOzBN + 1) * 8 + 1024; }
+template <int BN>
+size_t oz_smem() { return (size_t)kOzStages * (kBM * 128 + BN * 128) + 1024; }
 
 }  // namespace
 
@@ -817,7 +819,10 @@ cudaError_t configure_tc_kernels() {
   QPE_TC_ATTR(kTcFP16, 64)
   QPE_TC_ATTR(kTcFP16, 128)
 #undef QPE_TC_ATTR
-  return cudaFuncSetAttribute(oz_square_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
+  e = cudaFuncSetAttribute(oz_square_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem<64>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(oz_square_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)oz_smem<128>());
 }
 
 // Workspace of the tensor-core squaring: row / column scales and the digit
@@ -848,13 +853,17 @@ int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStr
                  (P32 && k == 1) ? P32 : (float2*)nullptr);
   if (e == cudaSuccess) e = launch_k(oz_slice_b_kernel, dim3(eb), dim3(256), 0, s, P, d, (const int*)sig, B);
   if (e != cudaSuccess) return -1;
+  // 128-column tiles halve the operand bytes per MMA; below d = 2048 they
+  // would leave SMs idle (fewer than 256 tiles), so 64 there
+  const int BN = d >= 2048 ? 128 : 64;
   CUtensorMap mA, mB;
   if (!make_map(&mA, A, kTcBF16, (int64_t)kOzS * 2 * d, 2 * (int64_t)d, kBM) ||
-      !make_map(&mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, kOzBN))
+      !make_map(&mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, BN))
     return -1;
   OzArgs a{tau, sig, C, P32 ? P32 + k * dd : nullptr, d, err};
-  const unsigned grid = (unsigned)((2 * d / kBM) * (d / kOzBN));
-  e = launch_k(oz_square_kernel, dim3(grid), dim3(192), oz_smem(), s, mA, mB, a);
+  const unsigned grid = (unsigned)((2 * d / kBM) * (d / BN));
+  e = BN == 128 ? launch_k(oz_square_kernel<128>, dim3(grid), dim3(192), oz_smem<128>(), s, mA, mB, a)
+                : launch_k(oz_square_kernel<64>, dim3(grid), dim3(192), oz_smem<64>(), s, mA, mB, a);
   return e == cudaSuccess ? 4 : -1;
 }
 
