@@ -46,7 +46,9 @@ qpe_status cuda_fail(qpe_plan_t p, cudaError_t e, const char* where) {
 }
 
 // Lays out one instance starting at byte offset `base`; returns the end.
-size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
+// Batched plans keep instances with Nmat <= 6 on the fused complex64 schedule
+// under the split precisions; those apply to the plain instances' gate GEMMs.
+size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool batched = false) {
   const int64_t d = in.d, N = in.N;
   size_t off = align_up(base);
   auto take = [&](size_t bytes) {
@@ -57,7 +59,8 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   in.off_pow64 = take((size_t)in.nmeas * d * d * 16);
   in.off_pow32 = is_c64(prec) ? take((size_t)in.nmeas * d * d * 8) : 0;
   in.off_psi = take((size_t)d * 16);
-  in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP)) && !is_tc(prec);
+  in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP)) &&
+             (!is_tc(prec) || batched);
   in.keep_state = (flags & QPE_FLAG_KEEP_STATE) != 0;
   // the fused schedule never materialises the N x d state unless asked to keep it
   in.state_bytes = (size_t)N * d * elem_size(prec);
@@ -73,7 +76,7 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   in.off_partials = take(sizeof(qpe::Partial) * qpe::kReduceBlocks);
   in.off_scalars = take(sizeof(qpe::Scalars));
   in.off_err = take(sizeof(int));
-  if (is_tc(prec)) in.off_tcsplit = take(qpe::tc_split_bytes(prec, in.nmat, in.nmeas));
+  if (is_tc(prec) && !in.fused) in.off_tcsplit = take(qpe::tc_split_bytes(prec, in.nmat, in.nmeas));
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
   if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
   in.fft = qpe::make_fft_plan(in.nmeas, d, elem_size(prec));
@@ -95,7 +98,7 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base) {
   return off;
 }
 
-qpe_status check_desc(const qpe_plan_desc* desc) {
+qpe_status check_desc(const qpe_plan_desc* desc, bool batched = false) {
   if (!desc) return QPE_ERR_ARG;
   if (desc->nmat < 1 || desc->nmat > kMaxNmat) return QPE_ERR_ARG;
   if (desc->nmeas < 1 || desc->nmeas > kMaxNmeas) return QPE_ERR_ARG;
@@ -105,7 +108,8 @@ qpe_status check_desc(const qpe_plan_desc* desc) {
     return QPE_ERR_ARG;
   if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
     return QPE_ERR_UNSUPPORTED;
-  if (is_tc(desc->prec) && (desc->nmat < 5 || (desc->flags & QPE_FLAG_GATE_SWEEP))) return QPE_ERR_UNSUPPORTED;
+  if (is_tc(desc->prec) && ((desc->nmat < 5 && !batched) || (desc->flags & QPE_FLAG_GATE_SWEEP)))
+    return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
   return QPE_OK;
 }
@@ -560,6 +564,12 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
   };
   for (Instance& in : p->inst)
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
+  // error words of the instances whose kernels can set them, cleared per run
+  for (Instance& in : p->inst)
+    if (in.oz_square || (is_tc(p->prec) && !in.fused)) {
+      cudaError_t e = cudaMemsetAsync(ws + in.off_err, 0, sizeof(int), p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
+    }
   if (p->flags & QPE_FLAG_CHECK_UNITARY) {
     for (Instance& in : p->inst) {
       cudaError_t e = cudaMemsetAsync(ws + in.off_err, 0, sizeof(int), p->stream);
@@ -567,11 +577,6 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
       if (!chk(qpe::launch_check_unitary(in, ws, p->stream))) return cuda_fail(p, cudaGetLastError(), "unitarity check");
     }
   }
-  for (Instance& in : p->inst)
-    if (in.oz_square && !(p->flags & QPE_FLAG_CHECK_UNITARY)) {  // (the unitarity check cleared it already)
-      cudaError_t e = cudaMemsetAsync(ws + in.off_err, 0, sizeof(int), p->stream);
-      if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
-    }
   for (int k = 1; k < bm.maxn; ++k) {
     if (!chk(qpe::launch_square_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_sq) + bm.sq_begin[k],
                                         bm.sq_count[k], square_tiles(bm, k, p->sq_variant), p->sq_variant,
@@ -624,7 +629,8 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
   for (int i : bm.plain) {
     Instance& in = p->inst[i];
     in.powers_done = true;
-    int r = c64 ? qpe::launch_sweep<float2>(in, ws, false, p->stream) : qpe::launch_sweep<double2>(in, ws, false, p->stream);
+    int r = c64 ? qpe::launch_sweep<float2>(in, ws, false, p->stream, p->prec)
+                : qpe::launch_sweep<double2>(in, ws, false, p->stream, p->prec);
     if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain sweep");
     r = c64 ? qpe::launch_fft<float2>(in, ws, p->stream) : qpe::launch_fft<double2>(in, ws, p->stream);
     if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain fft");
@@ -684,7 +690,7 @@ qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* w
   if (!descs || !workspace_bytes || !out || count < 1) return QPE_ERR_ARG;
   *out = nullptr;
   for (int32_t i = 0; i < count; ++i) {
-    const qpe_status st = check_desc(&descs[i]);
+    const qpe_status st = check_desc(&descs[i], true);
     if (st != QPE_OK) return st;
     if (descs[i].prec != descs[0].prec || descs[i].flags != descs[0].flags) return QPE_ERR_ARG;
   }
@@ -702,7 +708,7 @@ qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* w
       in.nmeas = descs[i].nmeas;
       in.d = int64_t(1) << in.nmat;
       in.N = int64_t(1) << in.nmeas;
-      off = layout_instance(in, p->prec, p->flags, off);
+      off = layout_instance(in, p->prec, p->flags, off, true);
       p->inst.push_back(in);
     }
     build_batch_meta(p, nullptr, 0);

@@ -79,3 +79,22 @@ def test_c3_tensor_cores_vs_closed_form(q, prec):
     order = np.argsort(Q)
     if Q[order[-1]] - Q[order[-2]] > 10 * PROB_TOL[prec]:
         assert am == order[-1]
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_batched_split_precision(q, prec):
+    """A batched plan under a split precision: instances with Nmat <= 6 run the
+    fused complex64 schedule, the others the doubling schedule with the gate
+    GEMMs on the tensor cores; every histogram against the oracle."""
+    shapes = [(3, 8), (7, 9), (6, 10), (8, 8), (5, 7), (2, 5)]
+    rng = np.random.default_rng(prec)
+    insts = [W.haar_instance(rng, a, b, superposition=True) for a, b in shapes]
+    bp = q.BatchedPlan(shapes, prec, q.FLAG_GRAPH | q.FLAG_SQUARE_TC)
+    for i, inst in enumerate(insts):
+        bp.load(i, inst.U, inst.psi)
+    for _ in range(2):
+        bp.run()
+        for i, inst in enumerate(insts):
+            P, *_ = bp.probs(i)
+            ref = gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas)
+            assert np.abs(P - ref).max() <= PROB_TOL[prec], shapes[i]
