@@ -19,14 +19,14 @@
 // its largest |entry| lies in [2^14, 2^15), B (entries of a unitary, |.| <= 1)
 // by 2^14; the drain multiplies each output row by the exact inverse.
 //
-// Kernel: one CTA per 128 x BN output tile (BN <= 128), 192 threads. Warp 0
+// Kernel: one CTA per 128 x BN output tile (BN <= 128), 320 threads. Warp 0
 // lane 0 issues TMA loads of the K-slabs A_hi, A_lo, B_hi, B_lo (128-byte
 // swizzled, one ring stage per K-block, 3 or 4 stages); warp 1 lane 0
 // issues tcgen05.mma (M = 128, N = BN, K = 32 bytes per instruction) into
 // double-buffered FP32 tensor-memory accumulators (hi.hi drained after every
-// K-block, the cross terms every 8); warps 2..5 drain each finished buffer
-// with tcgen05.ld into FP32 registers (correctly rounded adds) and store the
-// rows at the end. Every mbarrier wait
+// two instructions, the cross terms every 8 K-blocks); warps 2..9 drain each
+// finished buffer with tcgen05.ld into FP32 registers (correctly rounded adds)
+// and store the rows at the end. Every mbarrier wait
 // is bounded; on expiry the CTA records QPE_ERR_TIMEOUT in the device error
 // word, frees its tensor memory and returns.
 #include <algorithm>
@@ -141,22 +141,27 @@ __device__ __forceinline__ uint32_t make_idesc() {
 //
 // The tensor-core accumulator drops low-order bits on every accumulation
 // step, so nothing is left to accumulate there for long: the dominant
-// hi.hi product of every K-block goes to one of two "main" tensor-memory
-// buffers and is added into correctly rounded FP32 registers right after
-// that K-block; the two cross products (about 2^-11 smaller) go to one of two
-// "cross" buffers drained every KPC K-blocks. Four drain warps do the adds
-// while the MMAs of the next K-blocks run.
+// hi.hi product goes, two MMA instructions (32 elements of K for 16-bit
+// types) at a time, to one of two "main" tensor-memory buffers and is added
+// into correctly rounded FP32 registers right after; the two cross products
+// (about 2^-11 smaller) go to one of two "cross" buffers drained every KPC
+// K-blocks. Eight drain warps do the adds while the next MMAs run. (Draining
+// after every instruction instead halves the histogram error again but makes
+// the kernel drain-bound, about twice slower.)
 //   warp 0 lane 0   TMA producer (one stage = the four operand tiles of a K-block)
 //   warp 1 lane 0   MMA issuer
-//   warps 2..5      drain + epilogue; warp w owns tensor-memory lanes
-//                   32 (w % 4) .. +31, i.e. tile rows 32 (w % 4) .. +31
+//   warps 2..9      drain + epilogue; warp w owns tensor-memory lanes
+//                   32 (w % 4) .. +31, i.e. tile rows 32 (w % 4) .. +31, and
+//                   the column half (w - 2) / 4 of the tile
 // Tiles are visited in groups of kGroupM row tiles by all column tiles so the
 // operand panels in flight stay in L2.
 constexpr int kGroupM = 8;
 constexpr int kKPC = 8;  // K-blocks per cross-term chunk
+constexpr int kMS = 2;   // hi.hi drains per K-block (every 2 MMA instructions)
+constexpr int kTcDrainWarps = 8;  // 4 lane quarters x 2 column halves
 
 template <int KIND, int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(64 + 32 * kTcDrainWarps, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
                    const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
                    float* __restrict__ D, int64_t ldd, int64_t M, int K, int* __restrict__ err,
@@ -203,9 +208,9 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&main_full[b], 1);
-      mbar_init(&main_empty[b], 4);
+      mbar_init(&main_empty[b], kTcDrainWarps);
       mbar_init(&cross_full[b], 1);
-      mbar_init(&cross_empty[b], 4);
+      mbar_init(&cross_empty[b], kTcDrainWarps);
     }
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -243,19 +248,13 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       const uint32_t idesc = make_idesc<KIND, BN>();
       for (int kb = 0; kb < kblocks; ++kb) {
-        const int bm = kb & 1;                    // main buffer of this K-block
         const int cx = kb / kKPC, bx = cx & 1;    // cross chunk and its buffer
         const bool cx_first = (kb % kKPC) == 0;
         const bool cx_last = (kb % kKPC) == kKPC - 1 || kb == kblocks - 1;
-        if (kb >= 2 && !mbar_wait(&main_empty[bm], ((kb >> 1) - 1) & 1)) {
-          atomicExch(&fail, 1);
-          break;
-        }
         if (cx_first && cx >= 2 && !mbar_wait(&cross_empty[bx], ((cx >> 1) - 1) & 1)) {
           atomicExch(&fail, 1);
           break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int st = kb % QS;
         if (!mbar_wait(&full_bar[st], (kb / QS) & 1)) {
           atomicExch(&fail, 1);
@@ -263,19 +262,39 @@ __global__ void __launch_bounds__(192, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sa = smem_u32(ring + st * STAGE_BYTES);
-        for (int pr = 0; pr < 3; ++pr) {  // (hi, hi), (hi, lo), (lo, hi)
-          const uint64_t ad = sw128_desc(pr == 2 ? sa + A_BYTES : sa);
-          const uint64_t bd = sw128_desc(sa + 2 * A_BYTES + (pr == 1 ? B_BYTES : 0));
-          const uint32_t acc_addr = pr == 0 ? tmem + (uint32_t)(bm * BN) : tmem + (uint32_t)((2 + bx) * BN);
+        bool ok = true;
+        {  // hi.hi: kMS groups of 4 / kMS instructions, each group into its own main buffer
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + 2 * A_BYTES);
+          for (int gs = 0; gs < kMS; ++gs) {
+            const int j = kb * kMS + gs, bm = j & 1;
+            if (j >= 2 && !mbar_wait(&main_empty[bm], ((j >> 1) - 1) & 1)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction
-            const bool fresh = k == 0 && (pr == 0 || (pr == 1 && cx_first));
-            umma_k<KIND>(acc_addr, ad + 2 * k, bd + 2 * k, idesc, fresh ? 0u : 1u);
-          }
-          if (pr == 0)
+            for (int kk = 0; kk < 4 / kMS; ++kk) {
+              const int k = gs * (4 / kMS) + kk;
+              umma_k<KIND>(tmem + (uint32_t)(bm * BN), ad + 2 * k, bd + 2 * k, idesc, kk == 0 ? 0u : 1u);
+            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&main_full[bm]))
                          : "memory");
+          }
+        }
+        if (!ok) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        for (int pr = 1; pr < 3; ++pr) {  // (hi, lo), (lo, hi) into the cross buffer
+          const uint64_t ad = sw128_desc(pr == 2 ? sa + A_BYTES : sa);
+          const uint64_t bd = sw128_desc(sa + 2 * A_BYTES + (pr == 1 ? B_BYTES : 0));
+          const uint32_t acc_addr = tmem + (uint32_t)((2 + bx) * BN);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction
+            const bool fresh = k == 0 && pr == 1 && cx_first;
+            umma_k<KIND>(acc_addr, ad + 2 * k, bd + 2 * k, idesc, fresh ? 0u : 1u);
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&empty_bar[st]))
@@ -288,10 +307,12 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else {
     // drain warps: add finished buffers into FP32 registers
-    const int lg = warp & 3;  // tensor-memory lane group
-    float acc[BN];
+    const int lg = warp & 3;  // tensor-memory lane group (fixed by the warp's rank)
+    constexpr int CW = BN / 2;  // columns of this drain warp
+    const int ch = (warp - 2) >> 2;  // column half
+    float acc[CW];
 #pragma unroll
-    for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+    for (int i = 0; i < CW; ++i) acc[i] = 0.f;
     bool ok = true;
     auto drain = [&](uint64_t* full, uint64_t* empty, uint32_t parity, uint32_t col0) -> bool {
       bool got = mbar_wait(full, parity);
@@ -299,9 +320,9 @@ __global__ void __launch_bounds__(192, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!got) return false;
 #pragma unroll
-      for (int q = 0; q < BN / 32; ++q) {
+      for (int q = 0; q < CW / 32; ++q) {
         uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + col0 + (uint32_t)(q * 32);
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + col0 + (uint32_t)(ch * CW + q * 32);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
             "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -322,8 +343,10 @@ __global__ void __launch_bounds__(192, 1)
       return true;
     };
     for (int kb = 0; kb < kblocks && ok; ++kb) {
-      const int bm = kb & 1;
-      ok = drain(&main_full[bm], &main_empty[bm], (kb >> 1) & 1, (uint32_t)(bm * BN));
+      for (int gs = 0; gs < kMS && ok; ++gs) {
+        const int j = kb * kMS + gs, bm = j & 1;
+        ok = drain(&main_full[bm], &main_empty[bm], (j >> 1) & 1, (uint32_t)(bm * BN));
+      }
       const int cx = kb / kKPC, bx = cx & 1;
       const bool cx_last = (kb % kKPC) == kKPC - 1 || kb == kblocks - 1;
       if (ok && cx_last) ok = drain(&cross_full[bx], &cross_empty[bx], (cx >> 1) & 1, (uint32_t)((2 + bx) * BN));
@@ -334,11 +357,11 @@ __global__ void __launch_bounds__(192, 1)
       if constexpr (KIND == kTcFP16) {  // undo the power-of-two operand scales (exact)
         const float sc = row_scale[row];
 #pragma unroll
-        for (int i = 0; i < BN; ++i) acc[i] *= sc;
+        for (int i = 0; i < CW; ++i) acc[i] *= sc;
       }
-      float4* dst = reinterpret_cast<float4*>(D + row * ldd + n0);
+      float4* dst = reinterpret_cast<float4*>(D + row * ldd + n0 + ch * CW);
 #pragma unroll
-      for (int q = 0; q < BN / 4; ++q) dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+      for (int q = 0; q < CW / 4; ++q) dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
     }
     if (!ok) atomicExch(&fail, 1);
   }
@@ -925,7 +948,8 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
   int* err = reinterpret_cast<int*>(ws + in.off_err);
   const dim3 grid((unsigned)(((half + kBM - 1) / kBM) * (d2 / BN)));  // grouped raster inside the kernel
 #define QPE_TC_LAUNCH(K, B)                                                                                    \
-  e = launch_k(tc_gemm_kernel<K, B>, grid, dim3(192), tc_smem<K, B>(), s, mAh, mAl, mBh, mBl, Dout, (int64_t)d2, \
+  e = launch_k(tc_gemm_kernel<K, B>, grid, dim3(64 + 32 * kTcDrainWarps), tc_smem<K, B>(), s, mAh, mAl, mBh, mBl, \
+               Dout, (int64_t)d2, \
                half, (int)d2, err, (const float*)inv_scale)
   if (kind == kTcTF32) {
     if (BN == 128)
