@@ -54,111 +54,8 @@ __device__ __forceinline__ void cp_async_block(C* smem, const C* gmem, int count
 }
 
 template <typename C>
-__device__ __forceinline__ C tw_lookup(const C* lo, const C* hi, int h, int64_t e) {
-  const int64_t mask = (int64_t(1) << h) - 1;
-  return cmul(ldg(lo + (e & mask)), ldg(hi + (e >> h)));
-}
-
-template <typename C>
 __device__ __forceinline__ C czero() {
   return mk((typename real_of<C>::type)0, (typename real_of<C>::type)0);
-}
-
-// In-register length-R DFT (R = 2^K <= 32), forward kernel w_R^(j j'),
-// output in natural order.
-template <typename C, int K>
-__device__ __forceinline__ void dft_reg(C (&x)[1 << K]) {
-  constexpr int R = 1 << K;
-  // radix-2 decimation in frequency; output lands in bit-reversed order
-#pragma unroll
-  for (int s = 0; s < K; ++s) {
-    const int h = R >> (s + 1);
-#pragma unroll
-    for (int g = 0; g < R; g += 2 * h) {
-#pragma unroll
-      for (int p = 0; p < h; ++p) {
-        const C a = x[g + p], b = x[g + p + h];
-        x[g + p] = cadd(a, b);
-        const C dl = csub(a, b);
-        // w_(2h)^p = w_32^(p * 32 / (2h))
-        x[g + p + h] = (p == 0) ? dl : cmul(dl, w32<C>(p * (32 / (2 * h))));
-      }
-    }
-  }
-  // undo the bit reversal
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    int rv = 0;
-#pragma unroll
-    for (int b = 0; b < K; ++b) rv |= ((i >> b) & 1) << (K - 1 - b);
-    if (rv > i) {
-      const C t = x[i];
-      x[i] = x[rv];
-      x[rv] = t;
-    }
-  }
-}
-
-// One in-place DIF radix-2^K pass over the rows of tile (L rows, row stride
-// RS elements, D columns): sub-blocks of M = 2^hi rows, stride S = M / 2^K.
-// For each (block, q, column) the 2^K elements q + j S are transformed, the
-// output digit j' is twisted by w_M^(q j') and stored back at q + j' S.
-template <typename C, int K>
-__device__ __forceinline__ void radix_pass(C* tile, int RS, int D, int logd, int hi, const C* twL, int logL) {
-  constexpr int R = 1 << K;
-  const int M = 1 << hi;
-  const int S = M >> K;
-  const int logS = hi - K;
-  const int L = 1 << logL;
-  const int items = (L >> K) << logd;  // (L / R) groups x D columns
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it & (D - 1);
-    const int g = it >> logd;
-    const int b0 = g >> logS;
-    const int q = g & (S - 1);
-    const int base = b0 * M + q;
-    C x[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) x[j] = tile[(base + j * S) * RS + c];
-    dft_reg<C, K>(x);
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      C v = x[j];
-      if (j && q) {
-        const int e = ((q * j) & (M - 1)) << (logL - hi);  // w_M^(q j) = w_L^(q j L / M)
-        v = cmul(v, twL[e]);
-      }
-      tile[(base + j * S) * RS + c] = v;
-    }
-  }
-}
-
-template <typename C>
-__device__ __forceinline__ void radix_dispatch(int k, C* tile, int RS, int D, int logd, int hi, const C* twL,
-                                               int logL) {
-  switch (k) {
-    case 1: radix_pass<C, 1>(tile, RS, D, logd, hi, twL, logL); break;
-    case 2: radix_pass<C, 2>(tile, RS, D, logd, hi, twL, logL); break;
-    case 3: radix_pass<C, 3>(tile, RS, D, logd, hi, twL, logL); break;
-    case 4: radix_pass<C, 4>(tile, RS, D, logd, hi, twL, logL); break;
-    default: radix_pass<C, 5>(tile, RS, D, logd, hi, twL, logL); break;
-  }
-}
-
-__device__ __forceinline__ int brev_bits(int x, int bits) { return bits ? (int)(__brev((unsigned)x) >> (32 - bits)) : 0; }
-
-// Position p of the in-tile DIF output -> frequency index y_b: the pass that
-// ran first (top bits of p) produced the least significant digit.
-__device__ __forceinline__ int tile_pos_to_freq(int p, int r, int kmax) {
-  int y = 0, rem = r, sh = 0;
-  while (rem > 0) {
-    const int k = rem < kmax ? rem : kmax;
-    rem -= k;
-    const int dig = (p >> rem) & ((1 << k) - 1);
-    y |= dig << sh;
-    sh += k;
-  }
-  return y;
 }
 
 // float -> double by integer bit manipulation (for finite, non-negative
