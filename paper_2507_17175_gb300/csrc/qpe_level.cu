@@ -247,7 +247,6 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   using S = LvShape<LOGD, sizeof(C) == 16, MODE>;
   constexpr LvCfg cfg = S::c;
   constexpr int D = S::D, DI = S::DI, G = S::G, TR = cfg.TR, TG = cfg.TG, LMAX = S::LMAX;
-  constexpr int NCG = D / DI;  // column groups
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = a.r;
   const int L = 1 << r;
