@@ -255,6 +255,11 @@ def bench_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     launches_per_run = plan.query(qpe.INFO_LAST_LAUNCHES)
+    memory = {"workspace_bytes": int(plan.ws_bytes),
+              "state_bytes_if_materialised": int(inst.N * (1 << inst.nmat) * 8),
+              "peak_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
+              "note": "the library allocates nothing itself: its device footprint is the workspace; the peak "
+                      "includes U, psi and the 512 MiB L2-flush buffer"}
     value, total_ms = aggregate(world, args.steps, float(sum(times)), dev)
     ms_per_step = total_ms / args.steps
 
@@ -350,6 +355,7 @@ def bench_ours(args, rank, world, local_rank):
         "roofline": roofline, "stage_roofline": stage_roofline,
         "gpu_launches": int(launches_per_run * args.steps),
         "clocks": clocks,
+        "memory": memory,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rps, t_run, sample = time_oracle(inst, budget_s=args.cpu_budget)

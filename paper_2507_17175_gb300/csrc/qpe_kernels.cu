@@ -458,12 +458,13 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
     const int64_t p = p0 + lane / lpr;
     const int sub = lane % lpr;
     double acc = 0.0;
+    float fsum = 0.f;  // complex64: this lane's FP32 partial of the row
     if (p < N) {
       const C* row = X + (p << logd);
       if constexpr (sizeof(C) == 8) {
         // complex64: squares and the lane's partial sum (d / 32 <= 128 terms) in
-        // FP32, two elements per 16-byte load when a lane owns >= 2; the sum
-        // across lanes and rows is FP64
+        // FP32 with Kahan compensation, two elements per 16-byte load when a
+        // lane owns >= 2; the sum across rows (the readout) is FP64
         float f = 0.f;
         if (per >= 2) {
           float comp = 0.f;  // Kahan compensation of the running FP32 sum
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
           const C v = row[sub];
           f = fmaf(v.x, v.x, v.y * v.y);
         }
-        acc = (double)f;
+        fsum = f;
       } else {
         for (int k = 0; k < per; ++k) {
           const C v = row[sub + k * lpr];
@@ -487,7 +488,16 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
         }
       }
     }
-    for (int off = lpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    // sum over the row's lanes (every lane takes part; lanes past N carry 0)
+    if (sizeof(C) == 8 && lpr < 32) {
+      // rows narrower than a warp (d < 32, many rows): in FP32 (<= 4 rounding
+      // steps of nonnegative terms, < 3e-7 relative), off the FP64 units
+      for (int off = lpr >> 1; off > 0; off >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, off);
+      acc = (double)fsum;
+    } else {
+      if (sizeof(C) == 8) acc = (double)fsum;
+      for (int off = lpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    }
     if (sub == 0 && p < N) {
       const double v = acc * scale;
       const int64_t y = pos_to_y(g, n, p);
