@@ -165,8 +165,12 @@ qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan
  * every instance that needs it, and for nmat <= 6 grouped table, level and
  * readout launches whose CTAs walk a work list of (instance, level, column
  * group, pencil range) items built at qpe_bind; nmat > 6 instances run the
- * plain schedule one after another in the same stream (and graph). Only whole
- * runs (qpe_run) are supported. Host only, like qpe_plan.
+ * plain schedule one after another in the same stream (and graph). Under the
+ * split precisions (QPE_C64_BF16X3 / FP16X2 / TF32X3) instances with
+ * nmat <= 6 keep the fused complex64 schedule and the plain instances run
+ * their gate GEMMs on the tensor cores, so any nmat is accepted; with
+ * QPE_FLAG_SQUARE_TC the instances with d >= 256 square on the tensor cores.
+ * Only whole runs (qpe_run) are supported. Host only, like qpe_plan.
  */
 qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* workspace_bytes, qpe_plan_t* out);
 

@@ -121,3 +121,8 @@ def test_plan_batched_validation(q):
     assert q.plan_batched_workspace([(0, 4)], q.C64_FP32)[0] == q.ERR_ARG
     assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_GATE_SWEEP)[0] == q.ERR_UNSUPPORTED
     assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_TIMING)[0] == q.ERR_UNSUPPORTED
+    # split precisions: any nmat in a batched plan (nmat <= 6 runs fused in complex64), not in a single plan
+    st, ws, h = q.plan_batched_workspace([(3, 8), (8, 10)], q.C64_BF16X3, q.FLAG_SQUARE_TC)
+    assert st == q.OK and ws > 0
+    q.LIB.qpe_destroy(h)
+    assert q.plan_workspace(3, 8, q.C64_BF16X3, 0)[0] == q.ERR_UNSUPPORTED
