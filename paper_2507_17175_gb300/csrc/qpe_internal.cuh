@@ -33,6 +33,18 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// float -> double by integer bit manipulation (for finite, non-negative
+// normal or zero inputs, as squared magnitudes are), avoiding the FP64 pipe.
+__device__ __forceinline__ double widen_nonneg(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = u >> 23;
+  if (ex == 0) return 0.0;  // zero or subnormal: below 1.2e-38, far under every tolerance
+  if (ex == 0xff) return (double)f;
+  const unsigned long long bits =
+      ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 // ------------------------------------------------ programmatic dependent launch
 // Every kernel of a run starts with pdl_wait(), which returns once the
 // previous grid in the stream has completed and its writes are visible, and

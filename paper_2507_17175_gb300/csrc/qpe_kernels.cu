@@ -454,6 +454,11 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
   const int64_t tw = (int64_t)gridDim.x * 8;
   double best = -1.0, wsum = 0.0, psum = 0.0;
   int64_t by = INT64_MAX;
+  // complex64 rows narrower than a warp (many rows): the per-row readout stays
+  // off the FP64 units (float argmax, Kahan-compensated FP32 sums, bit-exact
+  // widening of the stored value)
+  const bool narrow32 = sizeof(C) == 8 && lpr < 32;
+  float best_f = -1.f, wsum_f = 0.f, wcomp_f = 0.f, psum_f = 0.f, pcomp_f = 0.f;
   for (int64_t p0 = gw * rpw; p0 < N; p0 += tw * rpw) {
     const int64_t p = p0 + lane / lpr;
     const int sub = lane % lpr;
@@ -499,13 +504,35 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
       for (int off = lpr >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     }
     if (sub == 0 && p < N) {
-      const double v = acc * scale;
       const int64_t y = pos_to_y(g, n, p);
-      hist[y] = v;
-      better(best, by, v, y);
-      wsum += v * (double)y;
-      psum += v;
+      if (narrow32) {
+        const float v = fsum * (float)scale;  // scale is a power of two
+        hist[y] = widen_nonneg(v);
+        if (v > best_f || (v == best_f && y < by)) {
+          best_f = v;
+          by = y;
+        }
+        float t1 = v * (float)y - wcomp_f;
+        float t2 = wsum_f + t1;
+        wcomp_f = (t2 - wsum_f) - t1;
+        wsum_f = t2;
+        t1 = v - pcomp_f;
+        t2 = psum_f + t1;
+        pcomp_f = (t2 - psum_f) - t1;
+        psum_f = t2;
+      } else {
+        const double v = acc * scale;
+        hist[y] = v;
+        better(best, by, v, y);
+        wsum += v * (double)y;
+        psum += v;
+      }
     }
+  }
+  if (narrow32) {
+    best = best_f < 0.f ? -1.0 : widen_nonneg(best_f);
+    wsum = (double)wsum_f;
+    psum = (double)psum_f;
   }
   // warp then block reduction (fixed order: deterministic)
   for (int off = 16; off > 0; off >>= 1) {

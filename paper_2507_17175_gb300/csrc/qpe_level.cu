@@ -58,18 +58,6 @@ __device__ __forceinline__ C czero() {
   return mk((typename real_of<C>::type)0, (typename real_of<C>::type)0);
 }
 
-// float -> double by integer bit manipulation (for finite, non-negative
-// normal or zero inputs, as squared magnitudes are), avoiding the FP64 pipe.
-__device__ __forceinline__ double widen_nonneg(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = u >> 23;
-  if (ex == 0) return 0.0;  // zero or subnormal: below 1.2e-38, far under every tolerance
-  if (ex == 0xff) return (double)f;
-  const unsigned long long bits =
-      ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)bits);
-}
-
 template <typename C>
 struct Acc;  // per-row |x|^2 accumulator type
 template <>
