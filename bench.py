@@ -1,12 +1,17 @@
 #!/usr/bin/env python
-"""QPE emulator benchmark: runs/s on the 22-qubit workload (Nmat=6, Nmeas=16,
-64 x 64 Haar-eigenbasis U with phases uniform in [0,1), psi = V[:,0]).
+"""QPE emulator benchmark: runs/s on the largest workload, 34 qubits (Nmat=4,
+Nmeas=30; 16 x 16 Haar-eigenbasis U with phases uniform in [0,1), psi a
+Dirichlet(1)-weighted superposition of all 16 eigenvectors with uniform
+phases), on the all-FP64 path (complex128 state, FP64 arithmetic: the
+paper's precision).
 
 One step = one whole QPE run (U^(2^k) squaring chain, Hadamard layer +
 controlled-U^(2^k) gates, QFT^-1, |amp|^2 histogram + readout) through the C
-ABI, U and psi resident on the device. The complex64 path (FP32 gates and
-transform, FP64 squaring and readout) is the headline; the all-FP64 path on
-the same device is reported beside it.
+ABI, U and psi resident on the device. Beside the headline: the complex64 and
+split-precision paths on the same workload with their L1 / max-abs histogram
+difference against the FP64 histogram, end-to-end runs/s with host buffers,
+the top-level kernel's roofline against the measured FP64 FMA peak, and the
+CPU oracle on a bounded sample.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica (weak scaling).
@@ -28,7 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QPE runs/s + % roofline; mixed-prec & batched vs FP64 at ≤1e-6 L1 prob error"
-WORKLOAD = "qpe Nmat=6 Nmeas=16 (22 qubits), Haar 64x64 U, phases U[0,1), psi=V[:,0]"
+WORKLOAD = ("qpe Nmat=4 Nmeas=30 (34 qubits), Haar 16x16 U, phases U[0,1), psi = Dirichlet(1)-weighted "
+            "superposition of the eigenvectors")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -40,16 +46,6 @@ def peaks():
         return {"hbm_gbs": j["hbm_gbs"], "bf16_tflops": j["bf16_tflops"], "sm_max_mhz": j.get("sm_max_mhz", 2070.0),
                 "source": "measured"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
-
-
-def fp32_alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-
-
-def fp64_alu_peak_tflops() -> float:
-    """Nominal GB300 FP64 rate (1.25 TFLOP/s); no measured figure exists."""
-    return 1.25
 
 
 def csrc_hash() -> str:
@@ -198,6 +194,15 @@ def host_cores():
 
 
 # ------------------------------------------------------------------ ours
+def level_flops(N: int, d: int, r_top: int) -> float:
+    """Algorithmic flops of the fused schedule's top level: every one of the N
+    rows receives one d x d complex matvec (8 d^2 flop: the controlled gates of
+    the top level's measurement qubits applied to Z) and every (y, column) one
+    length-2^r_top DFT share (5 r_top flop per complex point, the usual
+    5 n log2 n count)."""
+    return 8.0 * N * d * d + 5.0 * N * d * r_top
+
+
 def bench_ours(args, rank, world, local_rank):
     import torch
     import __graft_entry__ as g
@@ -206,7 +211,8 @@ def bench_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    inst = workloads.c2()
+    inst = workloads.c5()
+    N, d, n = inst.N, inst.d, inst.nmeas
     U_d = torch.from_numpy(inst.U).to(dev)
     psi_d = torch.from_numpy(inst.psi).to(dev)
     stream = torch.cuda.Stream(device=dev)
@@ -216,8 +222,6 @@ def bench_ours(args, rank, world, local_rank):
         p = qpe.Plan(inst.nmat, inst.nmeas, prec, flags, device=dev, stream=stream)
         p.load(U_d, psi_d)
         return p
-
-    plan = make(qpe.C64_FP32, qpe.FLAG_GRAPH | qpe.FLAG_TIMING)
 
     def timed_steps(p, K, W, stage_acc=None, kern_acc=None):
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
@@ -241,7 +245,8 @@ def bench_ours(args, rank, world, local_rank):
             stream.synchronize()
         return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
 
-    # ---------------- headline: complex64 path, K steps
+    # ---------------- headline: the FP64 path, K steps
+    plan = make(qpe.FP64, qpe.FLAG_GRAPH | qpe.FLAG_TIMING)
     stage_acc = [[], [], [], []]
     kern_acc = []
     if world > 1:
@@ -255,104 +260,118 @@ def bench_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     launches_per_run = plan.query(qpe.INFO_LAST_LAUNCHES)
-    memory = {"workspace_bytes": int(plan.ws_bytes),
-              "state_bytes_if_materialised": int(inst.N * (1 << inst.nmat) * 8),
-              "peak_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
-              "note": "the library allocates nothing itself: its device footprint is the workspace; the peak "
-                      "includes U, psi and the 512 MiB L2-flush buffer"}
+    r_top = plan.query(qpe.INFO_TOP_LEVEL_BITS)
+    levels = plan.query(qpe.INFO_LEVELS)
     value, total_ms = aggregate(world, args.steps, float(sum(times)), dev)
     ms_per_step = total_ms / args.steps
+    P64 = torch.empty(N, dtype=torch.float64, device=dev)
+    _, am64, pa64, pm64 = plan.probs(P64)
+    memory = {"workspace_bytes": int(plan.ws_bytes),
+              "state_bytes_if_materialised": int(N * d * 16),
+              "peak_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
+              "note": "the library allocates nothing itself: its device footprint is the workspace (powers, level "
+                      "buffers, histogram); the fused schedule never holds the N x d state"}
 
-    P, am, pa, pm = plan.probs()
-
-    # ---------------- FP64 path on the same device
-    plan64 = make(qpe.FP64, qpe.FLAG_GRAPH | qpe.FLAG_TIMING)
-    k64 = max(3, min(args.steps, 20))
-    st64 = [[], [], [], []]
-    t64 = timed_steps(plan64, k64, 3, st64)
-    P64, am64, _, _ = plan64.probs()
-    fp64 = {"runs_per_s": 1e3 / (sum(t64) / k64), "ms_per_run": sum(t64) / k64, "steps": k64,
-            "stage_ms": [statistics.median(s) for s in st64],
-            "argmax": int(am64)}
-    mixed_vs_fp64 = {"l1": float(np.abs(P - P64).sum()), "max_abs": float(np.abs(P - P64).max()),
-                     "argmax_equal": bool(am == am64),
-                     "phase_mean_diff": float(abs(pm - plan64.probs(want_hist=False)[3]))}
-    del plan64
-
-    # ---------------- end to end through the C ABI with host buffers
+    # ---------------- end to end through the C ABI with host buffers (FP64)
     U_h = torch.from_numpy(inst.U).pin_memory()
     psi_h = torch.from_numpy(inst.psi).pin_memory()
-    hist_h = torch.empty(inst.N, dtype=torch.float64).pin_memory()
-    e2e_plan = make(qpe.C64_FP32, qpe.FLAG_GRAPH)
-    ke = max(3, min(args.steps, 200))
+    hist_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    ke = max(1, min(args.steps, 3))
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            e2e_plan.load(U_h, psi_h)
-            e2e_plan.run()
-            e2e_plan.probs(hist_h)
+        plan.load(U_h, psi_h)
+        plan.run()
+        plan.probs(hist_h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
-            e2e_plan.load(U_h, psi_h)   # H2D of U and psi from pinned memory
-            e2e_plan.run()
-            e2e_plan.probs(hist_h)      # D2H of the histogram + readout (synchronises)
+            plan.load(U_h, psi_h)   # H2D of U and psi from pinned memory
+            plan.run()
+            plan.probs(hist_h)      # D2H of the histogram + readout (synchronises)
         t_e2e = time.perf_counter() - t0
     e2e_value, _ = aggregate(world, ke, t_e2e * 1e3, dev)
     e2e = {"value": e2e_value, "unit": "runs/s",
            "h2d_bytes_per_step": int(inst.U.nbytes + inst.psi.nbytes),
-           "d2h_bytes_per_step": int(inst.N * 8 + 40)}
+           "d2h_bytes_per_step": int(N * 8 + 40), "steps": ke}
+    del hist_h
 
-    # ---------------- roofline of the dominant stage
+    # ---------------- mixed precision on the same workload, against this FP64 histogram
+    def compare(P):
+        diff = (P - P64).abs()
+        return {"l1_vs_fp64": float(diff.sum().item()), "max_abs_vs_fp64": float(diff.max().item())}
+
+    k32 = max(3, min(4 * args.steps, 40))
+    plan32 = make(qpe.C64_FP32, qpe.FLAG_GRAPH | qpe.FLAG_TIMING)
+    kern32 = []
+    t32 = timed_steps(plan32, k32, 3, kern_acc=kern32)
+    P32 = torch.empty(N, dtype=torch.float64, device=dev)
+    _, am32, pa32, pm32 = plan32.probs(P32)
+    c64 = {"runs_per_s": 1e3 / (sum(t32) / k32), "ms_per_run": sum(t32) / k32, "steps": k32,
+           "top_level_kernel_ms": statistics.mean(k[0] for k in kern32 if k[1] == 1),
+           "precision": "complex64 state, FP32 gates + QFT^-1, FP64 squaring + readout",
+           "argmax_equal": bool(am32 == am64), "phase_mean_diff": float(abs(pm32 - pm64)), **compare(P32)}
+    c64["speedup_vs_fp64"] = c64["runs_per_s"] / (1e3 / ms_per_step)
+    del plan32, P32
+    split = {}
+    for name, prec in (("bf16x3", qpe.C64_BF16X3), ("fp16x2", qpe.C64_FP16X2), ("tf32x3", qpe.C64_TF32X3)):
+        try:
+            ps = make(prec, qpe.FLAG_GRAPH)
+        except qpe.QpeError as e:
+            split[name] = {"available": False, "reason": str(e)}
+            continue
+        ts = timed_steps(ps, k32, 3)
+        Ps = torch.empty(N, dtype=torch.float64, device=dev)
+        _, ams, _, _ = ps.probs(Ps)
+        split[name] = {"runs_per_s": 1e3 / (sum(ts) / k32), "ms_per_run": sum(ts) / k32,
+                       "argmax_equal": bool(ams == am64), **compare(Ps)}
+        del ps, Ps
+    torch.cuda.empty_cache()
+
+    # ---------------- roofline of the dominant kernel (top level of the fused schedule)
     pk = peaks()
+    fp64_peak = qpe.measure_fma_peak(True, 4096, 5, device=dev)
+    fp32_peak = qpe.measure_fma_peak(False, 65536, 5, device=dev)
     clocks = clk.summary()
     stage_names = ["powers", "sweep", "fft", "reduce"]
     stage_ms = [statistics.median(s) for s in stage_acc]
-    dom = int(np.argmax(stage_ms))
-    N, d, n = inst.N, inst.d, inst.nmeas
-    S_B = N * d * 8
-    fp32_peak = fp32_alu_peak_tflops(pk["sm_max_mhz"])
-    # algorithmic work per run of each stage
-    work = {
-        "powers": ("alu", (n - 1) * 8.0 * d ** 3, fp64_alu_peak_tflops() * 1e3, "GFLOP/s",
-                   "FP64 squaring: (n-1) x 8 d^3 flop vs nominal 1.25 TFLOP/s FP64"),
-        "sweep": ("alu", (N - 1) * 8.0 * d * d, fp32_peak * 1e3, "GFLOP/s",
-                  "controlled gates: (N-1) matvecs x 8 d^2 flop vs FP32 FMA peak from unit counts"),
-        "fft": ("hbm", 2.0 * S_B * plan.query(qpe.INFO_FFT_PASSES), pk["hbm_gbs"], "GB/s",
-                "QFT^-1: passes x (read + write of the state) vs measured HBM copy bandwidth"),
-        "reduce": ("hbm", float(S_B + N * 8), pk["hbm_gbs"], "GB/s",
-                   "histogram: one read of the state + N doubles vs measured HBM copy bandwidth"),
-    }
-    bound, amount, peak, unit, note = work[stage_names[dom]]
-    achieved = amount / (stage_ms[dom] * 1e-3) / 1e9
-    stage_roofline = {"bound": bound, "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": unit,
-                      "frac": round(achieved / peak, 4), "stage": stage_names[dom], "note": note}
-    # dominant kernel: the top level of the fused schedule, timed by its own
-    # CUDA event pair on the launching stream inside every timed step
     kms = [k[0] for k in kern_acc if k[1] == 1]
-    if kms:
-        t_k = statistics.mean(kms)
-        flops = 8.0 * N * d * d  # every one of the N rows receives one d x d complex matvec in this launch
-        ach = flops / (t_k * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak * 1e3, 2),
-                    "unit": "GFLOP/s", "frac": round(ach / (fp32_peak * 1e3), 4),
-                    "traffic": recorded_traffic("level2_top"), "kernel": "level2_kernel (top level, fused)",
-                    "kernel_ms": round(t_k, 5), "algorithmic_flop_per_launch": flops,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                    "note": "flop counts only the controlled-gate matvecs (8 d^2 per row), not the DFT"}
-    else:
-        roofline = dict(stage_roofline, traffic=recorded_traffic(stage_names[dom]))
+    t_k = statistics.mean(kms)
+    flops = level_flops(N, d, r_top)
+    ach = flops / (t_k * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp64_peak * 1e3, 2), "unit": "GFLOP/s",
+                "frac": round(ach / (fp64_peak * 1e3), 4),
+                "traffic": recorded_traffic("level2_top_c5_fp64"),
+                "kernel": "level2_kernel<double2, 4, 1> (top level of the fused schedule)",
+                "kernel_ms": round(t_k, 3), "algorithmic_flop_per_launch": flops,
+                "flop_count": f"8 N d^2 + 5 N d r_top with N = 2^{n}, d = {d}, r_top = {r_top}",
+                "peak_source": "measured: FP64 FMA loop on every SM, CUDA events (qpe_measure_fma_peak)",
+                "frac_of_nominal_fp64": round(ach / 1250.0, 4), "nominal_fp64_gflops": 1250.0,
+                "fp32_fma_peak_gflops_measured": round(fp32_peak * 1e3, 1)}
+    whole = flops / (ms_per_step * 1e-3) / 1e9
+    stage_roofline = {"bound": "alu", "achieved": round(whole, 2), "peak": round(fp64_peak * 1e3, 2),
+                      "unit": "GFLOP/s", "frac": round(whole / (fp64_peak * 1e3), 4),
+                      "note": "whole run (squaring chain, every level, readout) credited with the top level's "
+                              "flops only, against the same measured FP64 peak"}
+    c64_flops_ach = flops / (c64["top_level_kernel_ms"] * 1e-3) / 1e9
+    c64["roofline"] = {"bound": "alu", "achieved": round(c64_flops_ach, 1), "peak": round(fp32_peak * 1e3, 1),
+                       "unit": "GFLOP/s", "frac": round(c64_flops_ach / (fp32_peak * 1e3), 4),
+                       "kernel": "level2_kernel<float2, 4, 1> (top level)", "note": "same flop count as the FP64 line"}
+    hbm_term_ms = 2.0 * N * d * 16 / (pk["hbm_gbs"] * 1e9) * 1e3
 
     res = {
-        "metric": METRIC, "value": round(value, 2), "unit": "runs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": round(value, 4), "unit": "runs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nmat": inst.nmat, "nmeas": inst.nmeas,
-                   "precision": "complex64 state, FP32 gates + QFT^-1, FP64 squaring + readout",
+                   "precision": "complex128 state, FP64 arithmetic everywhere (the paper's)",
+                   "schedule": f"fused levels ({levels} levels, top level 2^{r_top}-point DFT)",
                    "parallelism": f"replicas x{world}", "graph": True,
-                   "l2": "flushed between timed steps (512 MiB write outside the timed events)"},
-        "stage_ms": dict(zip(stage_names, [round(x, 5) for x in stage_ms])),
-        "fp64_path": fp64, "complex64_vs_fp64": mixed_vs_fp64, "e2e": e2e,
+                   "l2": "inputs and level buffers far larger than L2; also flushed between timed steps "
+                         "(512 MiB write outside the timed events)"},
+        "stage_ms": dict(zip(stage_names, [round(x, 3) for x in stage_ms])),
+        "readout": {"argmax": int(am64), "phase_argmax": pa64, "phase_mean": pm64},
+        "complex64_path": c64, "split_precision_paths": split, "e2e": e2e,
         "roofline": roofline, "stage_roofline": stage_roofline,
+        "hbm_term_ms": round(hbm_term_ms, 2),
         "gpu_launches": int(launches_per_run * args.steps),
         "clocks": clocks,
         "memory": memory,
@@ -369,7 +388,7 @@ def bench_reference(args):
     """The CPU oracle as it stands (FP64 gate-by-gate numpy), each step a
     bounded sample of the same workload."""
     from paper_2507_17175_gb300 import workloads
-    inst = workloads.c2()
+    inst = workloads.c5()
     per_step = max(0.05, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     from oracle import gates
     # choose the sample size once, then time exactly K steps of it
@@ -405,8 +424,8 @@ def bench_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

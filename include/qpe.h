@@ -141,8 +141,12 @@ typedef enum {
   QPE_INFO_FFT_PASSES = 3,      /* passes over the state the QFT^-1 takes      */
   QPE_INFO_LAST_LAUNCHES = 4,   /* kernels enqueued by the last qpe_run*       */
   QPE_INFO_INSTANCES = 5,
-  QPE_INFO_SQUARE_TILE = 6      /* batched plans: output tile edge (8, 16, 32)  */
+  QPE_INFO_SQUARE_TILE = 6,     /* batched plans: output tile edge (8, 16, 32)  */
                                 /* of the grouped FP64 squaring in use         */
+  QPE_INFO_LEVELS = 7,          /* fused schedule: number of levels (0 when    */
+                                /* the plan runs another schedule)            */
+  QPE_INFO_TOP_LEVEL_BITS = 8   /* fused schedule: r of the top level, i.e.    */
+                                /* its DFT length is 2^r (0 otherwise)         */
 } qpe_info;
 
 /*
@@ -276,14 +280,31 @@ qpe_status qpe_kernel_time(qpe_plan_t plan, double* ms, int32_t* kernel_id);
 /* qpe_sync: wait for the bound stream and report device-side error flags. */
 qpe_status qpe_sync(qpe_plan_t plan);
 
+/*
+ * qpe_selftest_timeout: run the failure path of a bounded device-side wait on
+ * purpose. Enqueues one kernel that holds tensor memory while one thread
+ * waits, with a limit of `polls` polls (1 .. 2^20, else QPE_ERR_ARG), on an
+ * mbarrier that nothing arrives at; when the limit runs out the kernel does
+ * what every tcgen05 kernel of the library does on an expired wait: it
+ * records QPE_ERR_TIMEOUT in the instance's device error word, frees its
+ * tensor memory and returns. No copy or MMA is in flight while it waits. The
+ * next qpe_sync or qpe_probs reports QPE_ERR_TIMEOUT; the next whole qpe_run
+ * clears the word. Single-instance plans only (QPE_ERR_UNSUPPORTED for
+ * batched plans); requires qpe_bind. Not part of the paper's method: it
+ * tests the library's failure detection.
+ */
+qpe_status qpe_selftest_timeout(qpe_plan_t plan, int32_t instance, uint32_t polls);
+
 /* qpe_destroy: free the host-side plan (and its CUDA graph, if any). Does not
  * touch the caller's workspace. NULL is accepted. */
 qpe_status qpe_destroy(qpe_plan_t plan);
 
 /* Readout written by qpe_readout_static (device memory, caller-owned). */
 typedef struct {
-  int64_t argmax;      /* most probable outcome, lowest y on exact ties        */
-  double phase_argmax; /* argmax / N                                          */
+  int64_t argmax;      /* most probable outcome, lowest y on exact ties; -1    */
+                       /* when the histogram is not finite (a NaN or Inf in    */
+                       /* the state), which the caller tests through total     */
+  double phase_argmax; /* argmax / N (NaN when argmax is -1)                  */
   double phase_mean;   /* sum_y P[y] y / N                                    */
   double total;        /* sum_y P[y]                                          */
 } qpe_readout_t;

@@ -233,41 +233,15 @@ __global__ void seed_grouped_kernel(const SeedItem<C>* __restrict__ items) {
 __global__ void __launch_bounds__(256) finalize_grouped_kernel(const FinItem* __restrict__ items) {
   pdl_begin();
   const FinItem it = items[blockIdx.x];
-  __shared__ Partial sp[256];
-  Partial r{-1.0, INT64_MAX, 0.0, 0.0};
-  for (int i = threadIdx.x; i < it.count; i += 256) {
-    const Partial o = it.parts[i];
-    if (o.best > r.best || (o.best == r.best && o.besty < r.besty)) {
-      r.best = o.best;
-      r.besty = o.besty;
-    }
-    r.wsum += o.wsum;
-    r.psum += o.psum;
-  }
-  sp[threadIdx.x] = r;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      const Partial o = sp[threadIdx.x + s];
-      Partial& m = sp[threadIdx.x];
-      if (o.best > m.best || (o.best == m.best && o.besty < m.besty)) {
-        m.best = o.best;
-        m.besty = o.besty;
-      }
-      m.wsum += o.wsum;
-      m.psum += o.psum;
-    }
-    __syncthreads();
-  }
+  const Partial m = reduce_partials_256(it.parts, it.count);
   if (threadIdx.x == 0) {
     const double N = ldexp(1.0, it.nmeas);
-    const Partial m = sp[0];
     Scalars s;
     s.argmax = m.besty;
     s.phase_argmax = (double)m.besty / N;
     s.phase_mean = m.wsum / N;
     s.total = m.psum;
-    s.err = isfinite(m.psum) && isfinite(m.wsum) && isfinite(m.best) ? 0 : (int)QPE_ERR_NUMERIC;
+    s.err = readout_finite(m) ? 0 : (int)QPE_ERR_NUMERIC;
     s.pad = 0;
     *it.out = s;
   }

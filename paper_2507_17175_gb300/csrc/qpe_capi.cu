@@ -170,9 +170,9 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
   const bool check_u = (p->flags & QPE_FLAG_CHECK_UNITARY) != 0;
   for (Instance& in : p->inst) {
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
-    // the error word covers one run: cleared where the run's first checked stage begins
-    if ((first == QPE_STAGE_POWERS && (check_u || is_tc(p->prec) || in.oz_square)) ||
-        (first == QPE_STAGE_SWEEP && is_tc(p->prec))) {
+    // the error word covers one run: cleared where a whole run, or the first
+    // stage that can set it, begins
+    if (first == QPE_STAGE_POWERS || (first == QPE_STAGE_SWEEP && is_tc(p->prec))) {
       cudaError_t e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
     }
@@ -983,6 +983,8 @@ int64_t qpe_query(qpe_plan_t p, int32_t key) {
     case QPE_INFO_LAST_LAUNCHES: return p->last_launches;
     case QPE_INFO_INSTANCES: return (int64_t)p->inst.size();
     case QPE_INFO_SQUARE_TILE: return p->sq_variant == 1 ? 16 : (p->sq_variant == 2 ? 32 : 8);
+    case QPE_INFO_LEVELS: return p->inst[0].fused ? (int64_t)p->inst[0].levels.size() : 0;
+    case QPE_INFO_TOP_LEVEL_BITS: return p->inst[0].fused ? p->inst[0].levels[0].r : 0;
   }
   return -1;
 }
@@ -1017,6 +1019,21 @@ qpe_status qpe_kernel_time(qpe_plan_t p, double* ms, int32_t* kernel_id) {
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventElapsedTime");
   *ms = t;
   *kernel_id = 1;
+  return QPE_OK;
+}
+
+qpe_status qpe_selftest_timeout(qpe_plan_t p, int32_t instance, uint32_t polls) {
+  if (!p) return QPE_ERR_ARG;
+  if (!p->bound) return fail(p, QPE_ERR_STATE, "qpe_bind first");
+  if (p->batched) return fail(p, QPE_ERR_UNSUPPORTED, "the wait-expiry self-test takes single-instance plans");
+  if (polls < 1 || polls > (1u << 20)) return fail(p, QPE_ERR_ARG, "polls must be in 1 .. 2^20");
+  Instance* in;
+  qpe_status st = get_instance(p, instance, &in);
+  if (st != QPE_OK) return st;
+  cudaError_t e = qpe::configure_tc_kernels();
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute");
+  if (qpe::launch_wait_expiry(*in, p->ws, polls, p->stream) < 0)
+    return cuda_fail(p, cudaGetLastError(), "wait-expiry kernel");
   return QPE_OK;
 }
 

@@ -142,6 +142,40 @@ struct Partial {
 
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
 
+// The readout's merge rule, used by every kernel that combines partials: the
+// larger probability wins, an exact tie goes to the lower y, and a NaN best is
+// replaced by whatever comes next (so a non-finite histogram cannot freeze it).
+__device__ __forceinline__ void better(double& best, int64_t& by, double v, int64_t y) {
+  if (v > best || (v == best && y < by) || (best != best)) {
+    best = v;
+    by = y;
+  }
+}
+__device__ __forceinline__ void merge_partial(Partial& m, const Partial& o) {
+  better(m.best, m.besty, o.best, o.besty);
+  m.wsum += o.wsum;
+  m.psum += o.psum;
+}
+// parts[0 .. count) merged by one CTA of 256 threads in a fixed order (the
+// result is deterministic); every thread must call it; thread 0 gets the result.
+__device__ __forceinline__ Partial reduce_partials_256(const Partial* __restrict__ parts, int count) {
+  __shared__ Partial sp[256];
+  Partial r{-1.0, INT64_MAX, 0.0, 0.0};
+  for (int i = threadIdx.x; i < count; i += 256) merge_partial(r, parts[i]);
+  sp[threadIdx.x] = r;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) merge_partial(sp[threadIdx.x], sp[threadIdx.x + s]);
+    __syncthreads();
+  }
+  return sp[0];
+}
+// A readout whose sums are not finite (or that saw no bin at all) has no
+// defined argmax.
+__device__ __forceinline__ bool readout_finite(const Partial& m) {
+  return isfinite(m.psum) && isfinite(m.wsum) && isfinite(m.best) && m.besty != INT64_MAX;
+}
+
 // One level of the fused small-d schedule: the controlled gates of
 // measurement qubits off .. off + r - 1 and a length-2^r DFT, for N_a = 2^logna
 // seeds.
@@ -323,6 +357,8 @@ int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s);
 int launch_check_unitary(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, int prec = 1);
 int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s);
+// a bounded wait that runs out after `polls` polls (records QPE_ERR_TIMEOUT)
+int launch_wait_expiry(const Instance& in, char* ws, uint32_t polls, cudaStream_t s);
 size_t oz_square_bytes(int nmat);
 int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStream_t s);
 size_t tc_split_bytes(int prec, int nmat, int nmeas);

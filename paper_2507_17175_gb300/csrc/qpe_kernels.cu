@@ -432,13 +432,6 @@ __device__ __forceinline__ int64_t y_to_pos(const Digits& g, int n, int64_t y) {
   return p;
 }
 
-__device__ __forceinline__ void better(double& best, int64_t& by, double v, int64_t y) {
-  if (v > best || (v == best && y < by) || (best != best)) {
-    best = v;
-    by = y;
-  }
-}
-
 template <typename C>
 __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, double* __restrict__ hist,
                                                      Partial* __restrict__ parts, int64_t N, int logd, int n,
@@ -559,34 +552,15 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
 __global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict__ parts, int count,
                                                        Scalars* __restrict__ out, int n) {
   pdl_begin();
-  __shared__ Partial sp[256];
-  Partial r{-1.0, INT64_MAX, 0.0, 0.0};
-  for (int i = threadIdx.x; i < count; i += 256) {
-    better(r.best, r.besty, parts[i].best, parts[i].besty);
-    r.wsum += parts[i].wsum;
-    r.psum += parts[i].psum;
-  }
-  sp[threadIdx.x] = r;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      Partial o = sp[threadIdx.x + s];
-      Partial& m = sp[threadIdx.x];
-      better(m.best, m.besty, o.best, o.besty);
-      m.wsum += o.wsum;
-      m.psum += o.psum;
-    }
-    __syncthreads();
-  }
+  const Partial m = reduce_partials_256(parts, count);
   if (threadIdx.x == 0) {
     const double N = ldexp(1.0, n);
-    Partial m = sp[0];
     Scalars s;
     s.argmax = m.besty;
     s.phase_argmax = (double)m.besty / N;
     s.phase_mean = m.wsum / N;
     s.total = m.psum;
-    s.err = isfinite(m.psum) && isfinite(m.wsum) && isfinite(m.best) ? 0 : (int)QPE_ERR_NUMERIC;
+    s.err = readout_finite(m) ? 0 : (int)QPE_ERR_NUMERIC;
     s.pad = 0;
     *out = s;
   }

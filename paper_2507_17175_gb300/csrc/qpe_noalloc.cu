@@ -47,13 +47,6 @@ cudaError_t scratch_address(qpe::Partial** out) {
   return cudaSuccess;
 }
 
-__device__ __forceinline__ void take_best(double& best, int64_t& by, double v, int64_t y) {
-  if (v > best || (v == best && y < by)) {
-    best = v;
-    by = y;
-  }
-}
-
 // P[y] = sum_t |X[y][t]|^2 for the rows of this CTA; partial readout into parts[blockIdx.x]
 template <typename C>
 __global__ void __launch_bounds__(256) static_partials_kernel(const C* __restrict__ X, double* __restrict__ probs,
@@ -80,7 +73,7 @@ __global__ void __launch_bounds__(256) static_partials_kernel(const C* __restric
     for (int off = lanes >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (sub == 0 && rr + lane / lanes < kRowsPerBlock && y < N) {
       probs[y] = acc;
-      take_best(best, by, acc, y);
+      qpe::better(best, by, acc, y);
       wsum += acc * (double)y;
       psum += acc;
     }
@@ -88,7 +81,7 @@ __global__ void __launch_bounds__(256) static_partials_kernel(const C* __restric
   for (int off = 16; off > 0; off >>= 1) {
     const double ob = __shfl_xor_sync(0xffffffffu, best, off);
     const int64_t oy = __shfl_xor_sync(0xffffffffu, by, off);
-    take_best(best, by, ob, oy);
+    qpe::better(best, by, ob, oy);
     wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
     psum += __shfl_xor_sync(0xffffffffu, psum, off);
   }
@@ -98,7 +91,7 @@ __global__ void __launch_bounds__(256) static_partials_kernel(const C* __restric
   if (threadIdx.x == 0) {
     qpe::Partial r = sp[0];
     for (int w = 1; w < 8; ++w) {
-      take_best(r.best, r.besty, sp[w].best, sp[w].besty);
+      qpe::better(r.best, r.besty, sp[w].best, sp[w].besty);
       r.wsum += sp[w].wsum;
       r.psum += sp[w].psum;
     }
@@ -106,34 +99,20 @@ __global__ void __launch_bounds__(256) static_partials_kernel(const C* __restric
   }
 }
 
+// The same merge and readout as the plan path's finalize; a non-finite sum or
+// a histogram without any comparable bin reports argmax = -1 and a NaN
+// phase_argmax.
 __global__ void __launch_bounds__(256) static_finish_kernel(const qpe::Partial* __restrict__ parts, int count,
                                                             qpe_readout_t* __restrict__ out, int n) {
-  __shared__ qpe::Partial sp[256];
-  qpe::Partial r{-1.0, INT64_MAX, 0.0, 0.0};
-  for (int i = threadIdx.x; i < count; i += 256) {
-    take_best(r.best, r.besty, parts[i].best, parts[i].besty);
-    r.wsum += parts[i].wsum;
-    r.psum += parts[i].psum;
-  }
-  sp[threadIdx.x] = r;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      qpe::Partial& m = sp[threadIdx.x];
-      const qpe::Partial o = sp[threadIdx.x + s];
-      take_best(m.best, m.besty, o.best, o.besty);
-      m.wsum += o.wsum;
-      m.psum += o.psum;
-    }
-    __syncthreads();
-  }
+  const qpe::Partial m = qpe::reduce_partials_256(parts, count);
   if (threadIdx.x == 0) {
     const double N = ldexp(1.0, n);
+    const bool ok = qpe::readout_finite(m);
     qpe_readout_t o;
-    o.argmax = sp[0].besty;
-    o.phase_argmax = (double)sp[0].besty / N;
-    o.phase_mean = sp[0].wsum / N;
-    o.total = sp[0].psum;
+    o.argmax = ok ? m.besty : -1;
+    o.phase_argmax = ok ? (double)m.besty / N : __longlong_as_double(0x7ff8000000000000LL);
+    o.phase_mean = m.wsum / N;
+    o.total = m.psum;
     *out = o;
   }
 }

@@ -65,10 +65,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete: false after
+// `limit` polls without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -970,6 +971,49 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
 #undef QPE_TC_LAUNCH
   if (e != cudaSuccess) return -1;
   return launches + 1;
+}
+
+// ------------------------------------------- expiry of a bounded wait
+// The exit path every tensor-core kernel takes when one of its mbarrier waits
+// runs out, exercised on purpose: warp 0 holds tensor memory, warp 1 waits
+// with a poll limit of `polls` on a barrier that nothing arrives at (no TMA
+// copy and no MMA is in flight), the CTA records QPE_ERR_TIMEOUT in the error
+// word, warp 0 frees the tensor memory and the kernel returns.
+__global__ void __launch_bounds__(64, 1) wait_expiry_kernel(int* __restrict__ err, uint32_t polls) {
+  pdl_begin();
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(32u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (warp == 1 && lane == 0 && !mbar_wait(&bar, 0, polls)) atomicExch(&fail, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (fail && threadIdx.x == 0) atomicExch(err, (int)QPE_ERR_TIMEOUT);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32u) : "memory");
+  pdl_trigger();
+}
+
+int launch_wait_expiry(const Instance& in, char* ws, uint32_t polls, cudaStream_t s) {
+  return launch_k(wait_expiry_kernel, dim3(1), dim3(64), 0, s, reinterpret_cast<int*>(ws + in.off_err), polls) ==
+                 cudaSuccess
+             ? 1
+             : -1;
 }
 
 }  // namespace qpe

@@ -44,6 +44,7 @@ FLAG_SQUARE_TC = 0x100
 STAGE_POWERS, STAGE_SWEEP, STAGE_FFT, STAGE_REDUCE = 1, 2, 3, 4
 INFO_WORKSPACE_BYTES, INFO_STATE_BYTES, INFO_FFT_PASSES, INFO_LAST_LAUNCHES, INFO_INSTANCES = 1, 2, 3, 4, 5
 INFO_SQUARE_TILE = 6
+INFO_LEVELS, INFO_TOP_LEVEL_BITS = 7, 8
 
 
 class PlanDesc(ctypes.Structure):
@@ -71,7 +72,10 @@ _sig = {
     "qpe_stage_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "qpe_kernel_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "qpe_destroy": (ctypes.c_int, [_vp]),
+    "qpe_selftest_timeout": (ctypes.c_int, [_vp, _i32, ctypes.c_uint32]),
     "qpe_readout_static": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "qpe_measure_fma_peak": (ctypes.c_int, [_i32, _i32, _i32, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                                            ctypes.POINTER(ctypes.c_double), _vp]),
     "qpe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qpe_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -109,9 +113,42 @@ def readout_static(final_state, nmat: int, nmeas: int, prec: int, probs, readout
     float64 CUDA tensor of N elements and ``readout`` a 32-byte CUDA tensor
     receiving (int64 argmax, phase_argmax, phase_mean, total). Returns the
     qpe_status."""
+    import torch
+    if not (1 <= nmat <= 12 and 1 <= nmeas <= 30):
+        raise ValueError("nmat must be in 1..12 and nmeas in 1..30")
+    want = torch.complex128 if prec == FP64 else torch.complex64
+    n_amp, n_out = (1 << nmat) << nmeas, 1 << nmeas
+    for name, t, dt, count in (("final_state", final_state, want, n_amp), ("probs", probs, torch.float64, n_out),
+                               ("readout", readout, None, None)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if dt is not None and (t.dtype != dt or t.numel() < count):
+            raise ValueError(f"{name} must be {dt} with at least {count} elements")
+    if readout.numel() * readout.element_size() < 32:
+        raise ValueError("readout must hold at least 32 bytes")
     s = 0 if stream is None else stream.cuda_stream
     return _lib.qpe_readout_static(final_state.data_ptr(), nmat, nmeas, prec, probs.data_ptr(), readout.data_ptr(),
                                    s or None)
+
+
+def measure_fma_peak(fp64: bool, iters: int, repeats: int = 5, device=None, stream=None) -> float:
+    """TFLOP/s of fused multiply-adds on the FP64 (fp64=True) or FP32 units,
+    measured by the library's FMA loop kernel with CUDA events
+    (include/qpe_peak.h); scratch from torch."""
+    import torch
+    need = ctypes.c_size_t(0)
+    st = _lib.qpe_measure_fma_peak(int(fp64), iters, repeats, None, 0, ctypes.byref(need), None, None)
+    if st != OK:
+        raise QpeError(st, f"qpe_measure_fma_peak: {status_string(st)}")
+    dev = torch.device(device if device is not None else "cuda")
+    scratch = torch.empty(need.value, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream(dev) if stream is None else stream
+    tf = ctypes.c_double(0.0)
+    st = _lib.qpe_measure_fma_peak(int(fp64), iters, repeats, scratch.data_ptr(), need.value, None,
+                                   ctypes.byref(tf), s.cuda_stream)
+    if st != OK:
+        raise QpeError(st, f"qpe_measure_fma_peak: {status_string(st)}")
+    return tf.value
 
 
 def plan_batched_workspace(shapes, prec: int = C64_FP32, flags: int = 0):
@@ -243,6 +280,11 @@ class Plan:
         kid = ctypes.c_int32(0)
         self._check(_lib.qpe_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(kid)), "qpe_kernel_time")
         return ms.value, kid.value
+
+    def selftest_timeout(self, polls: int = 64, instance: int = 0):
+        """Enqueue the library's bounded-wait expiry on purpose: the next sync
+        or probs reports ERR_TIMEOUT, the next whole run clears it."""
+        self._check(_lib.qpe_selftest_timeout(self._h, instance, polls), "qpe_selftest_timeout")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -357,11 +357,11 @@ def test_c3_complex64_vs_fejer(q):
     assert am == cand[int(np.argmax(Q))]
 
 
-@pytest.mark.parametrize("prec,nmeas", [(1, 30), (0, 28)])
+@pytest.mark.parametrize("prec,nmeas", [(1, 30), (0, 30)])
 def test_c5_vs_fejer(q, prec, nmeas):
     """Nmat = 4, superposition input (Dirichlet weights): the histogram is the
-    weighted sum of Fejer kernels. complex64 at full size (34 qubits, 128 GiB),
-    FP64 at Nmeas = 28 (64 GiB)."""
+    weighted sum of Fejer kernels, at full size (34 qubits) on the complex64
+    and on the FP64 path, in the launch configuration the benchmark times."""
     import torch
     inst = W.c5(nmeas)
     plan = q.Plan(inst.nmat, inst.nmeas, prec)
@@ -393,6 +393,42 @@ def test_c5_vs_fejer(q, prec, nmeas):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nmat,nmeas", [(11, 4), (12, 3)])
+def test_largest_target_registers_vs_oracle(q, prec, nmat, nmeas):
+    """Nmat = 11 and 12 (d = 2048, 4096: the plain schedule with the doubling
+    GEMMs of the largest U) against the gate-by-gate oracle, whole histogram,
+    superposition input."""
+    rng = np.random.default_rng(31 * nmat + nmeas)
+    inst = W.haar_instance(rng, nmat, nmeas, superposition=True)
+    plan, P, am, pa, pm = run_plan(q, inst, prec)
+    ref = gates.qpe_probabilities(inst.U, inst.psi, nmeas)
+    assert np.abs(P - ref).max() <= TOL[prec]
+    top2 = np.sort(ref)[-2:]
+    if top2[1] - top2[0] > 10 * TOL[prec]:
+        assert am == readout.argmax_lowest(ref)
+    assert abs(pm - readout.phase_weighted_mean(ref)) <= (1e-9 if prec == 0 else 2e-5)
+
+
+def test_c3_fp64_vs_fejer(q):
+    """C3 (Nmat = 12, Nmeas = 20, 32 qubits, 64 GiB complex128 state) on the
+    all-FP64 path, every bin against the closed form; the tolerance is the FP64
+    floor max(1e-10, 8 N u) of a constructed unitary at Nmeas = 20."""
+    import torch
+    inst = W.c3()
+    plan, P, am, pa, pm = run_plan(q, inst, q.FP64)
+    Q = fejer.probabilities(inst.phases, inst.weights, inst.nmeas)
+    tol = max(1e-10, 8 * inst.N * U64)
+    assert np.abs(P - Q).max() <= tol
+    order = np.argsort(Q)
+    if Q[order[-1]] - Q[order[-2]] > 10 * tol:
+        assert am == order[-1]
+    assert abs(pm - readout.phase_weighted_mean(Q)) <= 1e-8
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+
+
 # ------------------------------------------------ paper-faithful variants
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("nmat,nmeas", [(2, 6), (3, 9), (5, 8)])
@@ -406,7 +442,11 @@ def test_repeated_u_gates(q, prec, nmat, nmeas):
     plan.load(inst.U, inst.psi)
     plan.run()
     P, am, _, _ = plan.probs()
-    assert np.abs(P - gates.qpe_probabilities(inst.U, inst.psi, nmeas)).max() <= TOL[prec] * (10 if prec == 0 else 1)
+    ref = gates.qpe_probabilities(inst.U, inst.psi, nmeas)
+    assert np.abs(P - ref).max() <= TOL[prec]
+    top2 = np.sort(ref)[-2:]
+    if top2[1] - top2[0] > 10 * TOL[prec]:
+        assert am == readout.argmax_lowest(ref)
 
 
 @pytest.mark.parametrize("prec", [0, 1])

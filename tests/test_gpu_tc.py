@@ -16,6 +16,10 @@ TF32X3, BF16X3, FP16X2 = 4, 2, 3
 ROW_TOL = {TF32X3: 5e-6, BF16X3: 2e-4, FP16X2: 5e-6}
 PROB_TOL = {TF32X3: 1e-5, BF16X3: 1e-4, FP16X2: 1e-5}
 ALL = [TF32X3, BF16X3, FP16X2]
+# The bound on the whole histogram's L1 error, sum_y |P(y) - P_FP64(y)|, that
+# the split-precision forms must meet against FP64 (the mixed-precision
+# acceptance criterion), with the most probable outcome unchanged.
+L1_BOUND = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -76,9 +80,10 @@ def test_c3_tensor_cores_vs_closed_form(q, prec):
     err = np.abs(P - Q)
     print(f"prec {prec}: max-abs {err.max():.3e} L1 {err.sum():.3e}")
     assert err.max() <= PROB_TOL[prec]
+    assert err.sum() <= L1_BOUND
     order = np.argsort(Q)
-    if Q[order[-1]] - Q[order[-2]] > 10 * PROB_TOL[prec]:
-        assert am == order[-1]
+    assert Q[order[-1]] - Q[order[-2]] > 10 * PROB_TOL[prec]  # no near-tie in this draw
+    assert am == order[-1]
 
 
 @pytest.mark.parametrize("prec", ALL)
@@ -92,9 +97,40 @@ def test_batched_split_precision(q, prec):
     bp = q.BatchedPlan(shapes, prec, q.FLAG_GRAPH | q.FLAG_SQUARE_TC)
     for i, inst in enumerate(insts):
         bp.load(i, inst.U, inst.psi)
+    refs = [gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas) for inst in insts]
     for _ in range(2):
         bp.run()
-        for i, inst in enumerate(insts):
-            P, *_ = bp.probs(i)
-            ref = gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas)
+        for i, (inst, ref) in enumerate(zip(insts, refs)):
+            P, am, *_ = bp.probs(i)
             assert np.abs(P - ref).max() <= PROB_TOL[prec], shapes[i]
+            assert np.abs(P - ref).sum() <= L1_BOUND, shapes[i]
+            top2 = np.sort(ref)[-2:]
+            if top2[1] - top2[0] > 10 * PROB_TOL[prec]:
+                assert am == readout.argmax_lowest(ref), shapes[i]
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_c4_split_precision_l1(q, prec):
+    """The 512-instance batch (Nmat 3..10, Nmeas 8..18) under each split
+    precision, graph-replayed, with tensor-core squaring: every instance's
+    whole histogram within L1 1e-6 of its closed form (single Fejer kernel;
+    the FP64 floor at Nmeas <= 18 is below 1e-9) and the same most probable
+    outcome."""
+    insts = W.c4()
+    shapes = [(i.nmat, i.nmeas) for i in insts]
+    bp = q.BatchedPlan(shapes, prec, q.FLAG_GRAPH | q.FLAG_SQUARE_TC)
+    for k, inst in enumerate(insts):
+        bp.load(k, inst.U, inst.psi)
+    bp.run()
+    worst, worst_shape = 0.0, None
+    for k, inst in enumerate(insts):
+        P, am, *_ = bp.probs(k)
+        Q = fejer.probabilities(inst.phases, inst.weights, inst.nmeas)
+        l1 = float(np.abs(P - Q).sum())
+        if l1 > worst:
+            worst, worst_shape = l1, shapes[k]
+        order = np.argsort(Q)
+        if Q[order[-1]] - Q[order[-2]] > 10 * PROB_TOL[prec]:
+            assert am == order[-1], (k, shapes[k])
+    print(f"prec {prec}: worst L1 {worst:.3e} at (nmat, nmeas) = {worst_shape}")
+    assert worst <= L1_BOUND, (worst, worst_shape)
