@@ -312,7 +312,7 @@ def bench_ours(args, rank, world, local_rank):
     c64["speedup_vs_fp64"] = c64["runs_per_s"] / (1e3 / ms_per_step)
     del plan32, P32
     split = {}
-    for name, prec in (("bf16x3", qpe.C64_BF16X3), ("fp16x2", qpe.C64_FP16X2), ("tf32x3", qpe.C64_TF32X3)):
+    for name, prec in (("fp16x2", qpe.C64_FP16X2), ("tf32x3", qpe.C64_TF32X3)):
         try:
             ps = make(prec, qpe.FLAG_GRAPH)
         except qpe.QpeError as e:

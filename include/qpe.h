@@ -62,15 +62,20 @@ typedef enum {
   QPE_C64_FP32 = 1,   /* complex64 state, FP32 arithmetic for the controlled    */
                       /* gates and QFT^-1; U^(2^k) squaring and the readout     */
                       /* stay FP64                                              */
-  QPE_C64_BF16X3 = 2, /* complex64 state; controlled gates on the tcgen05       */
-                      /* tensor cores as A_hi B_hi + A_hi B_lo + A_lo B_hi with  */
-                      /* bf16 hi/lo splits and FP32 accumulation (nmat >= 5,     */
-                      /* plain schedule); squaring and readout stay FP64         */
-  QPE_C64_FP16X2 = 3, /* as QPE_C64_BF16X3 with fp16 hi/lo splits (~22 bits)    */
-                      /* in two passes (hi.hi, then both cross products over a   */
-                      /* doubled K); rows of the state are scaled by powers of   */
-                      /* two into fp16's range and U's embedding by 2^14         */
-  QPE_C64_TF32X3 = 4  /* as QPE_C64_BF16X3 with tf32 hi/lo splits (~21 bits)    */
+  QPE_C64_BF16X3 = 2, /* refused by every plan (QPE_ERR_UNSUPPORTED): bf16      */
+                      /* hi/lo splits keep ~16 significand bits per operand,    */
+                      /* and the histogram's L1 error then grows past 1e-6 with  */
+                      /* the number of gate levels (measured up to 1.6e-6 at     */
+                      /* Nmeas = 18); the value stays reserved                   */
+  QPE_C64_FP16X2 = 3, /* complex64 state; controlled gates on the tcgen05       */
+                      /* tensor cores with fp16 hi/lo splits (~22 bits) and FP32 */
+                      /* accumulation in two passes (hi.hi, then both cross      */
+                      /* products over a doubled K); rows of the state are       */
+                      /* scaled by powers of two into fp16's range and U's       */
+                      /* embedding by 2^14 (nmat >= 5, plain schedule); squaring */
+                      /* and readout stay FP64                                   */
+  QPE_C64_TF32X3 = 4  /* as QPE_C64_FP16X2 with tf32 hi/lo splits (~21 bits)    */
+                      /* and three products A_hi B_hi + A_hi B_lo + A_lo B_hi    */
 } qpe_precision;
 
 /* Plan flags. */
@@ -154,7 +159,8 @@ typedef enum {
  * GPU. On success *out is a new plan and *workspace_bytes the device bytes
  * qpe_bind needs. Errors: QPE_ERR_ARG for null pointers or nmat/nmeas/prec
  * out of range; QPE_ERR_UNSUPPORTED for combinations not built
- * (tensor-core precisions with nmat < 5 or the gate-by-gate schedule;
+ * (QPE_C64_BF16X3 in any plan; tensor-core precisions with nmat < 5 or the
+ * gate-by-gate schedule;
  * QPE_FLAG_GATE_SWEEP with nmat > 6; QPE_FLAG_REPEAT_U without
  * QPE_FLAG_GATE_SWEEP or with nmeas > 14).
  */
@@ -170,13 +176,43 @@ qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan
  * readout launches whose CTAs walk a work list of (instance, level, column
  * group, pencil range) items built at qpe_bind; nmat > 6 instances run the
  * plain schedule one after another in the same stream (and graph). Under the
- * split precisions (QPE_C64_BF16X3 / FP16X2 / TF32X3) instances with
+ * split precisions (QPE_C64_FP16X2 / TF32X3) instances with
  * nmat <= 6 keep the fused complex64 schedule and the plain instances run
  * their gate GEMMs on the tensor cores, so any nmat is accepted; with
  * QPE_FLAG_SQUARE_TC the instances with d >= 256 square on the tensor cores.
  * Only whole runs (qpe_run) are supported. Host only, like qpe_plan.
  */
 qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* workspace_bytes, qpe_plan_t* out);
+
+/*
+ * qpe_plan_shard: the plan of rank `rank` of `world` processes (world a power
+ * of two, 1 .. 1024; 0 <= rank < world; QPE_ERR_ARG otherwise) that share one
+ * problem, one GPU each. The paper runs on one GPU and names its memory as
+ * the limit of the qubit count (Sec. 1); this splits the work of one run.
+ * Rank r computes only the outcomes y = r (mod world): the fused schedule's
+ * top level writes X[y] for y = y_a + N_a y_b from Z[y_a] alone (see
+ * qpe_run), and y = y_a (mod world) whenever world divides N_a, so every level
+ * with at least `world` pencils computes only this rank's y_a, from the
+ * same rank's share of the level below; smaller (deeper) levels are computed
+ * whole by every rank. No data moves between ranks during a run: each rank
+ * reads U and psi in full (qpe_load) and squares U itself.
+ * After qpe_run on every rank:
+ *   - qpe_probs returns this rank's N / world bins compactly: probs[j] =
+ *     P[rank + world j]; its argmax is the most probable of them (as a global
+ *     y), phase_mean their share of sum_y P[y] y / N;
+ *   - qpe_state (QPE_FLAG_KEEP_STATE) returns the N / world rows y = rank +
+ *     world j in that order;
+ *   - qpe_shard_readout gives the partial that qpe_merge_shard_readouts
+ *     combines into the readout of the whole histogram.
+ * Gathering the histograms is the caller's (e.g. an all-gather of N / world
+ * doubles per rank, then P[r + world j] = part_r[j]). Fused schedule only:
+ * nmat <= 6, QPE_FP64 or QPE_C64_FP32, no QPE_FLAG_PLAIN / GATE_SWEEP /
+ * REPEAT_U, and nmeas large enough that the top level has >= world pencils;
+ * QPE_ERR_UNSUPPORTED otherwise. Host only, like qpe_plan; world = 1 gives the
+ * ordinary plan.
+ */
+qpe_status qpe_plan_shard(const qpe_plan_desc* desc, int32_t rank, int32_t world, size_t* workspace_bytes,
+                          qpe_plan_t* out);
 
 /*
  * qpe_bind: attach caller-owned device memory and a CUDA stream (a
@@ -334,6 +370,32 @@ typedef struct {
  */
 qpe_status qpe_readout_static(const void* final_state, int32_t nmat, int32_t nmeas, int32_t prec, double* probs,
                               qpe_readout_t* readout, void* cuda_stream);
+
+/* One rank's share of the readout of a sharded run (qpe_plan_shard). */
+typedef struct {
+  int64_t argmax;         /* most probable outcome among this rank's bins (global y) */
+  double p_argmax;        /* its probability                                         */
+  double phase_mean_part; /* sum over this rank's bins of P[y] y / N                 */
+  double total;           /* sum over this rank's bins of P[y]                       */
+  int32_t nmeas;
+  int32_t rank;
+} qpe_shard_readout_t;
+
+/*
+ * qpe_shard_readout: this rank's readout partial after qpe_run (host output;
+ * synchronises the stream; QPE_ERR_NUMERIC / QPE_ERR_TIMEOUT as qpe_probs).
+ */
+qpe_status qpe_shard_readout(qpe_plan_t plan, qpe_shard_readout_t* out);
+
+/*
+ * qpe_merge_shard_readouts: the readout of the whole histogram from the
+ * `world` partials of one sharded run (host only, any order of parts): the
+ * argmax by the plan path's rule (larger probability, then the lower y on an
+ * exact tie), phase_argmax = argmax / N, phase_mean and total summed in the
+ * order of parts. QPE_ERR_SHAPE if the parts disagree on nmeas,
+ * QPE_ERR_NUMERIC if any part holds a value that is not finite.
+ */
+qpe_status qpe_merge_shard_readouts(const qpe_shard_readout_t* parts, int32_t world, qpe_readout_t* out);
 
 const char* qpe_status_string(qpe_status s);
 /* Last error message recorded on the plan ("" if none; static text for NULL). */

@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(256) finalize_grouped_kernel(const FinItem* __
     s.phase_argmax = (double)m.besty / N;
     s.phase_mean = m.wsum / N;
     s.total = m.psum;
+    s.best = m.best;
     s.err = readout_finite(m) ? 0 : (int)QPE_ERR_NUMERIC;
     s.pad = 0;
     *it.out = s;

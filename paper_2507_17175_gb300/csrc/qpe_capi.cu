@@ -33,7 +33,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 bool is_c64(int prec) { return prec != QPE_FP64; }
 // split-precision tensor-core plans (complex64 state, tcgen05 U-application)
-bool is_tc(int prec) { return prec == QPE_C64_TF32X3 || prec == QPE_C64_BF16X3 || prec == QPE_C64_FP16X2; }
+bool is_tc(int prec) { return prec == QPE_C64_TF32X3 || prec == QPE_C64_FP16X2; }
 size_t elem_size(int prec) { return is_c64(prec) ? 8 : 16; }
 
 qpe_status fail(qpe_plan_t p, qpe_status st, const std::string& msg) {
@@ -62,11 +62,13 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP)) &&
              (!is_tc(prec) || batched);
   in.keep_state = (flags & QPE_FLAG_KEEP_STATE) != 0;
-  // the fused schedule never materialises the N x d state unless asked to keep it
-  in.state_bytes = (size_t)N * d * elem_size(prec);
+  if (in.nmat <= QPE_MAX_FUSED_NMAT) in.levels = qpe::make_levels(in.nmeas, in.nmat, elem_size(prec), 0);
+  // the fused schedule never materialises the N x d state unless asked to keep
+  // it; a sharded plan keeps (and histograms) only its own N / 2^shard_log rows
+  in.state_bytes = (size_t)(N >> in.shard_log) * d * elem_size(prec);
   in.has_state = !in.fused || in.keep_state;
   in.off_state = in.has_state ? take(in.state_bytes) : 0;
-  in.off_hist = take((size_t)N * 8);
+  in.off_hist = take((size_t)(N >> in.shard_log) * 8);
   in.htw = (in.nmeas + 1) / 2;
   const size_t nlo = size_t(1) << in.htw, nhi = size_t(1) << (in.nmeas - in.htw);
   in.off_tw_lo64 = take(nlo * 16);
@@ -83,11 +85,11 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a
     // plan's layout does not depend on its schedule flags)
-    in.levels = qpe::make_levels(in.nmeas, in.nmat, elem_size(prec), 0);
     size_t zb[2] = {0, 0};
     for (size_t li = 1; li < in.levels.size(); ++li) {
       const qpe::Level& L = in.levels[li];
-      const size_t bytes = ((size_t)1 << (L.logna + L.r)) * d * elem_size(prec);
+      const int lsh = qpe::level_sharded(in, (int)li) ? in.shard_log : 0;
+      const size_t bytes = ((size_t)1 << (L.logna + L.r - lsh)) * d * elem_size(prec);
       zb[li & 1] = std::max(zb[li & 1], bytes);
     }
     in.off_zbuf[0] = take(zb[0] ? zb[0] : 16);
@@ -108,6 +110,10 @@ qpe_status check_desc(const qpe_plan_desc* desc, bool batched = false) {
     return QPE_ERR_ARG;
   if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
     return QPE_ERR_UNSUPPORTED;
+  // bf16 hi/lo splits keep ~16 bits per operand: the histogram's L1 error
+  // against FP64 then exceeds 1e-6 after enough gate levels (1.6e-6 measured
+  // at Nmeas = 18), so the library does not offer that precision
+  if (desc->prec == QPE_C64_BF16X3) return QPE_ERR_UNSUPPORTED;
   if (is_tc(desc->prec) && ((desc->nmat < 5 && !batched) || (desc->flags & QPE_FLAG_GATE_SWEEP)))
     return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
@@ -686,6 +692,87 @@ qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan
   return QPE_OK;
 }
 
+qpe_status qpe_plan_shard(const qpe_plan_desc* desc, int32_t rank, int32_t world, size_t* workspace_bytes,
+                          qpe_plan_t* out) {
+  if (!desc || !workspace_bytes || !out) return QPE_ERR_ARG;
+  *out = nullptr;
+  if (world < 1 || world > 1024 || (world & (world - 1)) != 0 || rank < 0 || rank >= world) return QPE_ERR_ARG;
+  const qpe_status st = check_desc(desc);
+  if (st != QPE_OK) return st;
+  int sh = 0;
+  while ((1 << sh) < world) ++sh;
+  // the sharded form partitions the fused schedule's outcomes; the top level
+  // must have at least `world` pencils
+  if (desc->nmat > QPE_MAX_FUSED_NMAT || (desc->flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP | QPE_FLAG_REPEAT_U)) ||
+      is_tc(desc->prec))
+    return QPE_ERR_UNSUPPORTED;
+  const std::vector<qpe::Level> lv = qpe::make_levels(desc->nmeas, desc->nmat, elem_size(desc->prec), 0);
+  if (lv.empty() || lv[0].logna < sh) return QPE_ERR_UNSUPPORTED;
+  qpe_plan_s* p = new (std::nothrow) qpe_plan_s();
+  if (!p) return QPE_ERR_ARG;
+  p->prec = desc->prec;
+  p->flags = desc->flags;
+  Instance in{};
+  in.nmat = desc->nmat;
+  in.nmeas = desc->nmeas;
+  in.d = int64_t(1) << desc->nmat;
+  in.N = int64_t(1) << desc->nmeas;
+  in.shard_log = sh;
+  in.shard_rank = rank;
+  p->ws_bytes = layout_instance(in, p->prec, p->flags, 0);
+  p->inst.push_back(in);
+  *workspace_bytes = p->ws_bytes;
+  *out = p;
+  return QPE_OK;
+}
+
+qpe_status qpe_shard_readout(qpe_plan_t p, qpe_shard_readout_t* out) {
+  if (!p || !out) return fail(p, QPE_ERR_ARG, "null pointer");
+  if (!p->bound) return fail(p, QPE_ERR_STATE, "qpe_bind first");
+  if (p->batched) return fail(p, QPE_ERR_UNSUPPORTED, "batched plans have no shard readout");
+  Instance& in = p->inst[0];
+  if (in.state_stage != QPE_STAGE_REDUCE) return fail(p, QPE_ERR_STATE, "REDUCE has not run");
+  qpe::Scalars s;
+  int derr = 0;
+  cudaError_t e = cudaMemcpyAsync(&s, p->ws + in.off_scalars, sizeof(s), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, p->ws + in.off_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "qpe_shard_readout copy");
+  if (derr) return fail(p, (qpe_status)derr, err_word_message(derr));
+  out->argmax = s.argmax;
+  out->p_argmax = s.best;
+  out->phase_mean_part = s.phase_mean;
+  out->total = s.total;
+  out->nmeas = in.nmeas;
+  out->rank = in.shard_rank;
+  if (s.err) return fail(p, (qpe_status)s.err, "device flagged a non-finite histogram");
+  return QPE_OK;
+}
+
+qpe_status qpe_merge_shard_readouts(const qpe_shard_readout_t* parts, int32_t world, qpe_readout_t* out) {
+  if (!parts || !out || world < 1) return QPE_ERR_ARG;
+  int64_t am = -1;
+  double best = -1.0, mean = 0.0, total = 0.0;
+  for (int32_t i = 0; i < world; ++i) {
+    const qpe_shard_readout_t& q = parts[i];
+    if (q.nmeas != parts[0].nmeas) return QPE_ERR_SHAPE;
+    if (!std::isfinite(q.p_argmax) || !std::isfinite(q.phase_mean_part) || !std::isfinite(q.total))
+      return QPE_ERR_NUMERIC;
+    // the plan path's rule: larger probability, then lower outcome on a tie
+    if (am < 0 || q.p_argmax > best || (q.p_argmax == best && q.argmax < am)) {
+      best = q.p_argmax;
+      am = q.argmax;
+    }
+    mean += q.phase_mean_part;
+    total += q.total;
+  }
+  out->argmax = am;
+  out->phase_argmax = std::ldexp((double)am, -parts[0].nmeas);
+  out->phase_mean = mean;
+  out->total = total;
+  return QPE_OK;
+}
+
 qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* workspace_bytes, qpe_plan_t* out) {
   if (!descs || !workspace_bytes || !out || count < 1) return QPE_ERR_ARG;
   *out = nullptr;
@@ -884,7 +971,8 @@ qpe_status qpe_probs(qpe_plan_t p, int32_t instance, double* probs, int64_t* arg
   if (in->state_stage != QPE_STAGE_REDUCE) return fail(p, QPE_ERR_STATE, "REDUCE has not run");
   cudaError_t e = cudaSuccess;
   if (probs)
-    e = cudaMemcpyAsync(probs, p->ws + in->off_hist, (size_t)in->N * 8, kind_from_device(ptr_is_device), p->stream);
+    e = cudaMemcpyAsync(probs, p->ws + in->off_hist, (size_t)(in->N >> in->shard_log) * 8,
+                        kind_from_device(ptr_is_device), p->stream);
   qpe::Scalars s;
   int derr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&s, p->ws + in->off_scalars, sizeof(s), cudaMemcpyDeviceToHost, p->stream);

@@ -128,6 +128,7 @@ struct Scalars {
   double phase_argmax;
   double phase_mean;
   double total;      // sum_y P[y]
+  double best;       // P[argmax]
   int32_t err;       // qpe_status raised on the device, 0 if none
   int32_t pad;
 };
@@ -203,11 +204,18 @@ struct GroupItem {
   int64_t part;
 };
 
+// Sharded levels (a plan for rank rk of 2^sh ranks): the level computes only
+// the y_a = rk + 2^sh j, j < N_a / 2^sh, and keeps its outputs compact: the
+// value of outcome y (y = rk mod 2^sh) sits at local index y >> sh. Seeds are
+// read at seed_rk + (j << seed_sh): (0, 0) when the level below is sharded
+// too (compact), (rk, sh) when it was computed whole. Unsharded levels have
+// sh = rk = seed_sh = seed_rk = 0.
 template <typename C>
 struct LevelArgs {
   const C* seeds;  // N_a x d: Z of the level below (psi for the deepest level)
   const C* tab;    // [k][m_b d + i] = (U_l^(m_b))[i][k]
   int off, r, logna, logd, nmeas, htw;
+  int sh, rk, seed_sh, seed_rk;
   const C* tw_lo;
   const C* tw_hi;
   C* xout;         // MODE 0: X of this level; MODE 2: physical final state
@@ -244,6 +252,10 @@ struct Instance {
   size_t off_zbuf[2] = {0, 0};
   size_t zbuf_seed_off = 0;
   int64_t level_grid = 0;     // persistent grid (set at bind)
+  // sharded plans: this rank (shard_rank of 2^shard_log) owns the outcomes
+  // y = shard_rank mod 2^shard_log; its histogram (and kept state) hold them
+  // compactly, y at local index y >> shard_log
+  int shard_log = 0, shard_rank = 0;
   bool keep_state = false;
   bool loaded = false;
   bool powers_done = false;
@@ -377,6 +389,9 @@ inline void finalize_readout(const Instance& in, char* ws, int count, cudaStream
 size_t level_smem_bytes(int logd, int mode, size_t esize);
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
+// a level of a sharded plan computes only this rank's outcomes when it has at
+// least 2^shard_log pencils; smaller (deeper) levels are computed whole
+bool level_sharded(const Instance& in, int li);
 cudaError_t configure_level_kernels();
 template <typename C> int level_occupancy(int logd, int r);
 

@@ -560,6 +560,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict
     s.phase_argmax = (double)m.besty / N;
     s.phase_mean = m.wsum / N;
     s.total = m.psum;
+    s.best = m.best;
     s.err = readout_finite(m) ? 0 : (int)QPE_ERR_NUMERIC;
     s.pad = 0;
     *out = s;
@@ -690,7 +691,7 @@ static int launch_rows_times_pt(C* S, const C* P, int64_t M, int d, Rows rows, c
 
 template <typename C>
 int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, int prec) {
-  const bool tc = prec == QPE_C64_TF32X3 || prec == QPE_C64_BF16X3 || prec == QPE_C64_FP16X2;
+  const bool tc = prec == QPE_C64_TF32X3 || prec == QPE_C64_FP16X2;
   C* S = at<C>(ws, in.off_state);
   const C* P = (sizeof(C) == 16) ? at<C>(ws, in.off_pow64) : at<C>(ws, in.off_pow32);
   const int64_t dd = in.d * in.d;

@@ -271,7 +271,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
     }
   }
 
-  const int64_t Na = int64_t(1) << a.logna;
+  const int lna = a.logna - a.sh;              // local pencils: 2^lna (all of them when not sharded)
+  const int64_t Na = int64_t(1) << lna;
   const int lvl_shift = a.nmeas - a.logna - r;
   const int64_t lvl_mask = (int64_t(1) << (a.logna + r)) - 1;
 
@@ -279,11 +280,13 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   int64_t besty = INT64_MAX;
   float wsum_f = 0.f, wcomp_f = 0.f, psum_f = 0.f, pcomp_f = 0.f;
 
-  // histogram bin y <- s / N^2, with the readout partials (argmax, Kahan sums)
-  auto account = [&](A_t s, int64_t y) {
+  // histogram bin of local index yl (outcome y = rk + (yl << sh)) <- s / N^2,
+  // with the readout partials (argmax, Kahan sums) over the outcome y
+  auto account = [&](A_t s, int64_t yl) {
+    const int64_t y = a.rk + (yl << a.sh);
     if (sizeof(C) == 8) {
       const float v = (float)s * (float)a.pscale;  // pscale = 1/N^2, a power of two
-      a.hist[y] = widen_nonneg(v);
+      a.hist[yl] = widen_nonneg(v);
       if ((double)v > best || ((double)v == best && y < besty)) {
         best = v;
         besty = y;
@@ -299,7 +302,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
       psum_f = t2;
     } else {
       const double v = (double)s * a.pscale;
-      a.hist[y] = v;
+      a.hist[yl] = v;
       if (v > best || (v == best && y < besty)) {
         best = v;
         besty = y;
@@ -318,11 +321,13 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
     for (int e = tid; e < G * D; e += blockDim.x) {
       const int g = e / D, k = e - g * D;
       const bool valid = g < gv;
-      cp_async_elem(ZsT + k * G + g, a.seeds + (valid ? ((yg + g) << LOGD) + k : 0), valid);
+      cp_async_elem(ZsT + k * G + g, a.seeds + (valid ? ((a.seed_rk + ((yg + g) << a.seed_sh)) << LOGD) + k : 0),
+                    valid);
     }
     for (int e = tid; e < G * L; e += blockDim.x) {
       const int g = e >> r, mb = e & (L - 1);
-      const int64_t ex = (((int64_t)mb * (yg + g)) & lvl_mask) << lvl_shift;
+      const int64_t ya_true = a.rk + ((yg + g) << a.sh);
+      const int64_t ex = (((int64_t)mb * ya_true) & lvl_mask) << lvl_shift;
       cp_async_elem(twLo + e, a.tw_lo + (ex & tw_mask), true);
       cp_async_elem(twHi + e, a.tw_hi + (ex >> a.htw), true);
     }
@@ -425,14 +430,14 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
         if (MODE == 2 && valid) {
 #pragma unroll
           for (int yb = 0; yb < LMAX; ++yb)
-            a.xout[((ya0 + g + ((int64_t)yb << a.logna)) << LOGD) + ii] = cscale(x[yb], (R_t)a.xscale);
+            a.xout[((ya0 + g + ((int64_t)yb << lna)) << LOGD) + ii] = cscale(x[yb], (R_t)a.xscale);
         }
         int yb0 = 0;
         reduce_scatter<D / 2, LMAX>(v, ii, yb0);
         constexpr int NV = LMAX >= D ? LMAX / D : 1;  // column sums left on each lane
         if (valid && (LMAX >= D || ii % (D / LMAX) == 0)) {
 #pragma unroll
-          for (int j = 0; j < NV; ++j) account(v[j], ya0 + g + ((int64_t)(yb0 + j) << a.logna));
+          for (int j = 0; j < NV; ++j) account(v[j], ya0 + g + ((int64_t)(yb0 + j) << lna));
         }
       }
       continue;
@@ -449,7 +454,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
       if (MODE == 0) {
 #pragma unroll
         for (int yb = 0; yb < LMAX; ++yb)
-          if (yb < L) a.xout[((ya + ((int64_t)yb << a.logna)) << LOGD) + i] = x[yb];
+          if (yb < L) a.xout[((ya + ((int64_t)yb << lna)) << LOGD) + i] = x[yb];
       } else {
 #pragma unroll
         for (int yb = 0; yb < LMAX; ++yb)
@@ -457,7 +462,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
         if (MODE == 2) {
 #pragma unroll
           for (int yb = 0; yb < LMAX; ++yb)
-            if (yb < L) a.xout[((ya + ((int64_t)yb << a.logna)) << LOGD) + i] = cscale(x[yb], (R_t)a.xscale);
+            if (yb < L) a.xout[((ya + ((int64_t)yb << lna)) << LOGD) + i] = cscale(x[yb], (R_t)a.xscale);
         }
       }
     }
@@ -469,7 +474,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
         A_t s = 0;
 #pragma unroll 8
         for (int i = 0; i < D; ++i) s += sq[(yb * D + i) * (G + 1) + g];
-        account(s, ya0 + g + ((int64_t)yb << a.logna));
+        account(s, ya0 + g + ((int64_t)yb << lna));
       }
     }
   }
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
   pdl_begin();
   using S = LvShape<LOGD, sizeof(C) == 16, MODE>;
   constexpr int NCG = S::D / S::DI;
-  const int64_t iters = ((int64_t(1) << a.logna) + S::G - 1) / S::G;
+  const int64_t iters = ((int64_t(1) << (a.logna - a.sh)) + S::G - 1) / S::G;
   level_body<C, LOGD, MODE>(a, (int)(blockIdx.x % NCG), blockIdx.x / NCG, iters, gridDim.x / NCG,
                             a.parts + blockIdx.x);
   pdl_trigger();
@@ -656,6 +661,10 @@ int level_max_bits(int logd, size_t esize, size_t smem_cap) {
   return lv_cfg(logd, esize == 16).logl;
 }
 
+bool level_sharded(const Instance& in, int li) {
+  return in.shard_log > 0 && in.levels[li].logna >= in.shard_log;
+}
+
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop) {
   const int rmax = level_max_bits(logd, esize, kLevelSmemCap);
   std::vector<Level> lv;
@@ -773,7 +782,13 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s,
   const C* cur_seed = seed;
   for (int li = nl - 1; li >= 0; --li) {
     const Level& L = in.levels[li];
+    const bool sharded = level_sharded(in, li);
+    const bool below_sharded = li + 1 < nl && level_sharded(in, li + 1);
     LevelArgs<C> a{};
+    a.sh = sharded ? in.shard_log : 0;
+    a.rk = sharded ? in.shard_rank : 0;
+    a.seed_sh = (sharded && !below_sharded) ? in.shard_log : 0;
+    a.seed_rk = (sharded && !below_sharded) ? in.shard_rank : 0;
     a.seeds = cur_seed;
     a.tab = reinterpret_cast<const C*>(ws + L.tab_off);
     a.off = L.off;
@@ -787,7 +802,7 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s,
     a.pscale = ldexp(1.0, -2 * in.nmeas);
     a.inv_n = ldexp(1.0, -in.nmeas);
     a.xscale = 1.0;
-    const int64_t Na = int64_t(1) << L.logna;
+    const int64_t Na = int64_t(1) << (L.logna - a.sh);  // pencils this rank computes
     if (li > 0) {
       // column groups x pencil groups; the grid is a multiple of the group count
       const int64_t ncg = in.d / cfg.DI0;

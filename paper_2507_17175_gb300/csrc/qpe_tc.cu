@@ -1,6 +1,6 @@
 // Tensor-core controlled-gate GEMM for large target registers (sm_103a
 // tcgen05 + TMA), used by the split-precision plans (QPE_C64_TF32X3,
-// QPE_C64_BF16X3, QPE_C64_FP16X2) in the doubling schedule:
+// QPE_C64_FP16X2) in the doubling schedule:
 //
 //   rows [2^j, 2^(j+1)) of the state  =  rows [0, 2^j)  x  P_j^T,
 //
@@ -9,8 +9,8 @@
 // B[2i][2k+1] = -Im P[i][k], B[2i+1][2k] = Im P[i][k], B[2i+1][2k+1] = Re P[i][k]
 // (stored n-major: row n holds the weights of output column n), so
 // out[m][n] = sum_kk A[m][kk] B[n][kk]. Each operand x is split into
-// hi = round(x) and lo = round(x - hi) in the tensor type (tf32, bf16 or
-// fp16); the product A B^T is accumulated in FP32 in tensor memory as
+// hi = round(x) and lo = round(x - hi) in the tensor type (tf32 or fp16);
+// the product A B^T is accumulated in FP32 in tensor memory as
 // A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the lo lo term is below the FP32
 // accumulator's resolution). The hi.hi pass and the cross pass (the two cross
 // products into one accumulator, i.e. [A_hi | A_lo] [B_lo ; B_hi]^T over a
@@ -383,22 +383,15 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// A rows (complex64 = 2d interleaved floats) -> hi / lo in the tensor type
-template <int KIND>
-__global__ void split_rows_kernel(const float* __restrict__ src, void* __restrict__ hi, void* __restrict__ lo,
-                                  int64_t count) {
+// A rows (complex64 = 2d interleaved floats) -> tf32 hi / lo
+__global__ void split_rows_tf32_kernel(const float* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo,
+                                       int64_t count) {
   pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const float x = src[i];
-    if constexpr (KIND == kTcTF32) {
-      const float h = tf32_round(x);
-      reinterpret_cast<float*>(hi)[i] = h;
-      reinterpret_cast<float*>(lo)[i] = tf32_round(x - h);
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      reinterpret_cast<__nv_bfloat16*>(hi)[i] = h;
-      reinterpret_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn(x - __bfloat162float(h));
-    }
+    const float h = tf32_round(x);
+    hi[i] = h;
+    lo[i] = tf32_round(x - h);
   }
   pdl_trigger();
 }
@@ -456,15 +449,12 @@ __global__ void embed_split_kernel(const double2* __restrict__ P, void* __restri
       const float h = tf32_round((float)v);
       reinterpret_cast<float*>(hi)[e] = h;
       reinterpret_cast<float*>(lo)[e] = tf32_round((float)(v - (double)h));
-    } else if constexpr (KIND == kTcFP16) {
+    } else {
+      static_assert(KIND == kTcFP16, "gate GEMM operands are tf32 or fp16");
       const double vs = v * 16384.0;  // 2^14, exact
       const __half h = __float2half_rn((float)vs);
       reinterpret_cast<__half*>(hi)[e] = h;
       reinterpret_cast<__half*>(lo)[e] = __float2half_rn((float)(vs - (double)__half2float(h)));
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-      reinterpret_cast<__nv_bfloat16*>(hi)[e] = h;
-      reinterpret_cast<__nv_bfloat16*>(lo)[e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
     }
   }
   pdl_trigger();
@@ -838,8 +828,6 @@ cudaError_t configure_tc_kernels() {
   if (e != cudaSuccess) return e;
   QPE_TC_ATTR(kTcTF32, 64)
   QPE_TC_ATTR(kTcTF32, 128)
-  QPE_TC_ATTR(kTcBF16, 64)
-  QPE_TC_ATTR(kTcBF16, 128)
   QPE_TC_ATTR(kTcFP16, 64)
   QPE_TC_ATTR(kTcFP16, 128)
 #undef QPE_TC_ATTR
@@ -893,7 +881,7 @@ int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStr
 
 // Split buffers (bytes) a plan of this precision needs for the largest level.
 size_t tc_split_bytes(int prec, int nmat, int nmeas) {
-  if (prec != QPE_C64_TF32X3 && prec != QPE_C64_BF16X3 && prec != QPE_C64_FP16X2) return 0;
+  if (prec != QPE_C64_TF32X3 && prec != QPE_C64_FP16X2) return 0;
   const size_t esz = prec == QPE_C64_TF32X3 ? 4 : 2;
   const size_t d2 = (size_t)2 << nmat;
   const size_t rows = nmeas >= 1 ? ((size_t)1 << (nmeas - 1)) : 1;
@@ -904,7 +892,7 @@ size_t tc_split_bytes(int prec, int nmat, int nmeas) {
 // One doubling level j on the tensor cores: rows [half, 2 half) = rows
 // [0, half) x P_j^T. Returns launches, or -1 (launch error / tensor map).
 int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s) {
-  const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : (prec == QPE_C64_BF16X3 ? kTcBF16 : kTcFP16);
+  const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : kTcFP16;
   const size_t esz = kind == kTcTF32 ? 4 : 2;
   const int64_t half = int64_t(1) << j;
   const int64_t d2 = 2 * in.d;
@@ -924,20 +912,16 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
     e = launch_k(split_rows_fp16_kernel, dim3(rblocks), dim3(256), 0, s, (const float*)S,
                  reinterpret_cast<__half*>(Ahi), reinterpret_cast<__half*>(Alo), inv_scale, half, (int)d2);
   } else {
-    e = kind == kTcTF32 ? launch_k(split_rows_kernel<kTcTF32>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
-                                   (void*)Ahi, (void*)Alo, cnt)
-                        : launch_k(split_rows_kernel<kTcBF16>, dim3(gblocks), dim3(256), 0, s, (const float*)S,
-                                   (void*)Ahi, (void*)Alo, cnt);
+    e = launch_k(split_rows_tf32_kernel, dim3(gblocks), dim3(256), 0, s, (const float*)S, reinterpret_cast<float*>(Ahi),
+                 reinterpret_cast<float*>(Alo), cnt);
   }
   if (e != cudaSuccess) return -1;
   ++launches;
   const int eblocks = (int)std::min<int64_t>((d2 * d2 + 255) / 256, 152 * 16);
-  e = kind == kTcTF32   ? launch_k(embed_split_kernel<kTcTF32>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
-                                   (void*)Blo, (int)in.d)
-      : kind == kTcBF16 ? launch_k(embed_split_kernel<kTcBF16>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
-                                   (void*)Blo, (int)in.d)
-                        : launch_k(embed_split_kernel<kTcFP16>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
-                                   (void*)Blo, (int)in.d);
+  e = kind == kTcTF32 ? launch_k(embed_split_kernel<kTcTF32>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
+                                 (void*)Blo, (int)in.d)
+                      : launch_k(embed_split_kernel<kTcFP16>, dim3(eblocks), dim3(256), 0, s, Pj, (void*)Bhi,
+                                 (void*)Blo, (int)in.d);
   if (e != cudaSuccess) return -1;
   ++launches;
   const int BN = d2 >= 128 ? 128 : (int)d2;
@@ -957,11 +941,6 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
       QPE_TC_LAUNCH(kTcTF32, 128);
     else
       QPE_TC_LAUNCH(kTcTF32, 64);
-  } else if (kind == kTcBF16) {
-    if (BN == 128)
-      QPE_TC_LAUNCH(kTcBF16, 128);
-    else
-      QPE_TC_LAUNCH(kTcBF16, 64);
   } else {
     if (BN == 128)
       QPE_TC_LAUNCH(kTcFP16, 128);

@@ -52,12 +52,34 @@ class PlanDesc(ctypes.Structure):
                 ("prec", ctypes.c_int32), ("flags", ctypes.c_uint32)]
 
 
+class Readout(ctypes.Structure):
+    _fields_ = [("argmax", ctypes.c_int64), ("phase_argmax", ctypes.c_double),
+                ("phase_mean", ctypes.c_double), ("total", ctypes.c_double)]
+
+
+class ShardReadout(ctypes.Structure):
+    _fields_ = [("argmax", ctypes.c_int64), ("p_argmax", ctypes.c_double), ("phase_mean_part", ctypes.c_double),
+                ("total", ctypes.c_double), ("nmeas", ctypes.c_int32), ("rank", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (int(self.argmax), float(self.p_argmax), float(self.phase_mean_part), float(self.total),
+                int(self.nmeas), int(self.rank))
+
+    @classmethod
+    def from_tuple(cls, t):
+        return cls(int(t[0]), float(t[1]), float(t[2]), float(t[3]), int(t[4]), int(t[5]))
+
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _sig = {
     "qpe_plan": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_vp)]),
     "qpe_plan_batched": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t),
                                         ctypes.POINTER(_vp)]),
+    "qpe_plan_shard": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _i32, _i32, ctypes.POINTER(ctypes.c_size_t),
+                                      ctypes.POINTER(_vp)]),
+    "qpe_shard_readout": (ctypes.c_int, [_vp, ctypes.POINTER(ShardReadout)]),
+    "qpe_merge_shard_readouts": (ctypes.c_int, [ctypes.POINTER(ShardReadout), _i32, ctypes.POINTER(Readout)]),
     "qpe_bind": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "qpe_load": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _i32]),
     "qpe_run": (ctypes.c_int, [_vp]),
@@ -105,6 +127,60 @@ def plan_workspace(nmat: int, nmeas: int, prec: int = C64_FP32, flags: int = 0):
     h = _vp()
     st = _lib.qpe_plan(ctypes.byref(desc), ctypes.byref(ws), ctypes.byref(h))
     return st, ws.value, h
+
+
+def plan_shard_workspace(nmat: int, nmeas: int, prec: int, flags: int, rank: int, world: int):
+    """Host-only: (status, workspace_bytes, raw plan handle) of rank ``rank``
+    of ``world`` (qpe_plan_shard)."""
+    desc = PlanDesc(nmat, nmeas, prec, flags)
+    ws = ctypes.c_size_t(0)
+    h = _vp()
+    st = _lib.qpe_plan_shard(ctypes.byref(desc), rank, world, ctypes.byref(ws), ctypes.byref(h))
+    return st, ws.value, h
+
+
+def merge_shard_readouts(parts):
+    """Readout of the whole histogram from every rank's ShardReadout (or its
+    as_tuple()): (argmax, phase_argmax, phase_mean, total); host only."""
+    parts = [p if isinstance(p, ShardReadout) else ShardReadout.from_tuple(p) for p in parts]
+    arr = (ShardReadout * len(parts))(*parts)
+    out = Readout()
+    st = _lib.qpe_merge_shard_readouts(arr, len(parts), ctypes.byref(out))
+    if st != OK:
+        raise QpeError(st, f"qpe_merge_shard_readouts: {status_string(st)}")
+    return int(out.argmax), float(out.phase_argmax), float(out.phase_mean), float(out.total)
+
+
+def interleave_shards(parts):
+    """The whole histogram from the ranks' compact slices (rank r holds
+    P[r + world j] at j): P[r + world j] = parts[r][j]. Works on numpy arrays
+    or torch tensors of equal length."""
+    world = len(parts)
+    if isinstance(parts[0], np.ndarray):
+        return np.stack(parts, axis=1).reshape(-1)
+    import torch
+    return torch.stack(list(parts), dim=1).reshape(-1)
+
+
+def gather_shards(dist, local, part: ShardReadout, group=None):
+    """(whole histogram, argmax, phase_argmax, phase_mean) of a sharded run:
+    every rank's compact histogram slice ``local`` (a float64 tensor, N / world
+    bins) is all-gathered and interleaved, and the ranks' readout partials
+    merged by qpe_merge_shard_readouts. NCCL groups gather device tensors,
+    others (gloo) host tensors."""
+    import torch
+    world = dist.get_world_size(group)
+    if dist.get_backend(group) != "nccl":
+        local = local.cpu()
+    parts = [torch.empty_like(local) for _ in range(world)]
+    dist.all_gather(parts, local.contiguous(), group=group)
+    mine = torch.tensor(part.as_tuple()[:4], dtype=torch.float64, device=local.device)
+    allp = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(allp, mine, group=group)
+    pieces = [ShardReadout(int(t[0].item()), float(t[1]), float(t[2]), float(t[3]), part.nmeas, r)
+              for r, t in enumerate(allp)]
+    am, pa, pm, _ = merge_shard_readouts(pieces)
+    return interleave_shards(parts), am, pa, pm
 
 
 def readout_static(final_state, nmat: int, nmeas: int, prec: int, probs, readout, stream=None) -> int:
@@ -296,6 +372,56 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class ShardedPlan(Plan):
+    """Rank ``rank`` of ``world`` processes sharing one QPE problem
+    (qpe_plan_shard): this rank computes the outcomes y = rank (mod world).
+    ``probs()`` returns its N / world bins compactly; ``shard_readout()`` its
+    readout partial for merge_shard_readouts; ``gather(dist)`` all-gathers the
+    whole histogram over a torch.distributed process group."""
+
+    def __init__(self, nmat: int, nmeas: int, prec: int, flags: int, rank: int, world: int,
+                 device=None, stream=None, workspace=None):
+        import torch
+        self.nmat, self.nmeas, self.prec, self.flags = nmat, nmeas, prec, flags
+        self.rank, self.world = rank, world
+        self.d, self.N = 1 << nmat, 1 << nmeas
+        st, self.ws_bytes, self._h = plan_shard_workspace(nmat, nmeas, prec, flags, rank, world)
+        if st != OK:
+            raise QpeError(st, f"qpe_plan_shard: {status_string(st)}")
+        self.device = torch.device(device if device is not None else "cuda")
+        if stream is None:
+            stream = torch.cuda.Stream(device=self.device) if (flags & FLAG_GRAPH) else \
+                torch.cuda.current_stream(self.device)
+        self.stream = stream
+        if workspace is None:
+            workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.workspace = workspace
+        self._check(_lib.qpe_bind(self._h, workspace.data_ptr(), self.ws_bytes, stream.cuda_stream), "qpe_bind")
+
+    def probs(self, out=None, instance: int = 0, want_hist: bool = True):
+        if want_hist and out is None:
+            out = np.empty(self.N // self.world, dtype=np.float64)
+        return super().probs(out, instance, want_hist)
+
+    def state(self, out=None, instance: int = 0):
+        if out is None:
+            out = np.empty((self.N // self.world, self.d), dtype=self.state_dtype)
+        return super().state(out, instance)
+
+    def shard_readout(self) -> ShardReadout:
+        r = ShardReadout()
+        self._check(_lib.qpe_shard_readout(self._h, ctypes.byref(r)), "qpe_shard_readout")
+        return r
+
+    def gather(self, dist, group=None):
+        """(whole histogram, argmax, phase_argmax, phase_mean) over the process
+        group (see gather_shards)."""
+        import torch
+        local = torch.empty(self.N // self.world, dtype=torch.float64, device=self.device)
+        super().probs(local)
+        return gather_shards(dist, local, self.shard_readout(), group)
 
 
 class BatchedPlan(Plan):

@@ -18,7 +18,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--prec", choices=["fp64", "c64", "bf16x3", "fp16x2", "tf32x3"], default="c64")
+    ap.add_argument("--prec", choices=["fp64", "c64", "fp16x2", "tf32x3"], default="c64")
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--single", action="store_true", help="also time one plan per instance")
@@ -31,7 +31,7 @@ def main(argv=None):
     import torch
     from . import qpe, workloads
     insts = workloads.c4(args.count)
-    prec = {"fp64": qpe.FP64, "c64": qpe.C64_FP32, "bf16x3": qpe.C64_BF16X3, "fp16x2": qpe.C64_FP16X2,
+    prec = {"fp64": qpe.FP64, "c64": qpe.C64_FP32, "fp16x2": qpe.C64_FP16X2,
             "tf32x3": qpe.C64_TF32X3}[args.prec]
     shapes = [(i.nmat, i.nmeas) for i in insts]
     stream = torch.cuda.Stream()

@@ -20,7 +20,7 @@ def main(argv=None):
     ap.add_argument("--nmeas", type=int, default=None)
     ap.add_argument("--workload", choices=["c2", "c3", "c5"], default=None,
                     help="one of the seeded workloads instead of a random superposition input")
-    ap.add_argument("--prec", choices=["fp64", "c64", "tf32x3", "bf16x3", "fp16x2"], default="c64")
+    ap.add_argument("--prec", choices=["fp64", "c64", "tf32x3", "fp16x2"], default="c64")
     ap.add_argument("--flags", type=lambda s: int(s, 0), default=0)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--seed", type=int, default=12345)
@@ -34,7 +34,7 @@ def main(argv=None):
         if args.nmat is None or args.nmeas is None:
             ap.error("--nmat and --nmeas, or --workload")
         inst = workloads.haar_instance(np.random.default_rng(args.seed), args.nmat, args.nmeas, superposition=True)
-    prec = {"fp64": qpe.FP64, "c64": qpe.C64_FP32, "tf32x3": qpe.C64_TF32X3, "bf16x3": qpe.C64_BF16X3,
+    prec = {"fp64": qpe.FP64, "c64": qpe.C64_FP32, "tf32x3": qpe.C64_TF32X3,
             "fp16x2": qpe.C64_FP16X2}[args.prec]
     plan = qpe.Plan(args.nmat, args.nmeas, prec, args.flags | qpe.FLAG_TIMING)
     plan.load(inst.U, inst.psi)

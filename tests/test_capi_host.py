@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -122,7 +123,77 @@ def test_plan_batched_validation(q):
     assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_GATE_SWEEP)[0] == q.ERR_UNSUPPORTED
     assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_TIMING)[0] == q.ERR_UNSUPPORTED
     # split precisions: any nmat in a batched plan (nmat <= 6 runs fused in complex64), not in a single plan
-    st, ws, h = q.plan_batched_workspace([(3, 8), (8, 10)], q.C64_BF16X3, q.FLAG_SQUARE_TC)
+    st, ws, h = q.plan_batched_workspace([(3, 8), (8, 10)], q.C64_FP16X2, q.FLAG_SQUARE_TC)
     assert st == q.OK and ws > 0
     q.LIB.qpe_destroy(h)
-    assert q.plan_workspace(3, 8, q.C64_BF16X3, 0)[0] == q.ERR_UNSUPPORTED
+    assert q.plan_workspace(3, 8, q.C64_FP16X2, 0)[0] == q.ERR_UNSUPPORTED
+
+
+def test_bf16x3_is_refused_everywhere(q):
+    """bf16 hi/lo splits (~16 bits) cannot keep the histogram's L1 error within
+    1e-6 of FP64, so no plan accepts QPE_C64_BF16X3."""
+    for nmat, nmeas in ((5, 8), (8, 10), (12, 20), (3, 8)):
+        assert q.plan_workspace(nmat, nmeas, q.C64_BF16X3, 0)[0] == q.ERR_UNSUPPORTED
+    assert q.plan_batched_workspace([(3, 8), (8, 10)], q.C64_BF16X3, q.FLAG_SQUARE_TC)[0] == q.ERR_UNSUPPORTED
+    assert q.plan_batched_workspace([(3, 8)], q.C64_BF16X3)[0] == q.ERR_UNSUPPORTED
+    assert q.plan_shard_workspace(4, 12, q.C64_BF16X3, 0, 0, 2)[0] == q.ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------ sharded plans
+@pytest.mark.parametrize("nmat,nmeas,prec,flags,rank,world,want", [
+    (4, 12, 0, 0, 0, 3, "ERR_ARG"),        # world not a power of two
+    (4, 12, 0, 0, 2, 2, "ERR_ARG"),        # rank out of range
+    (4, 12, 0, 0, -1, 2, "ERR_ARG"),
+    (7, 12, 1, 0, 0, 2, "ERR_UNSUPPORTED"),  # plain schedule
+    (4, 12, 1, 0x8, 0, 2, "ERR_UNSUPPORTED"),
+    (5, 12, 2, 0, 0, 2, "ERR_UNSUPPORTED"),  # tensor-core precision
+    (4, 3, 0, 0, 0, 2, "ERR_UNSUPPORTED"),   # top level with fewer pencils than ranks
+    (4, 12, 0, 0, 1, 2, "OK"),
+    (2, 20, 1, 0x10, 7, 8, "OK"),
+])
+def test_plan_shard_validation(q, nmat, nmeas, prec, flags, rank, world, want):
+    st, ws, h = q.plan_shard_workspace(nmat, nmeas, prec, flags, rank, world)
+    assert st == getattr(q, want), q.status_string(st)
+    if st == q.OK:
+        q.LIB.qpe_destroy(h)
+
+
+def test_shard_workspace_shrinks_with_world(q):
+    """A rank holds N / world histogram bins and its share of the level buffers."""
+    sizes = []
+    for world in (1, 2, 4, 8):
+        st, ws, h = q.plan_shard_workspace(4, 24, q.FP64, 0, 0, world)
+        assert st == q.OK
+        sizes.append(ws)
+        q.LIB.qpe_destroy(h)
+    st, ws1, h = q.plan_workspace(4, 24, q.FP64)
+    q.LIB.qpe_destroy(h)
+    assert sizes[0] == ws1
+    for a, b in zip(sizes, sizes[1:]):
+        assert b < a
+    assert sizes[3] < sizes[0] / 4
+
+
+def test_merge_shard_readouts_rule(q):
+    """Larger probability wins; an exact tie goes to the lower outcome in any
+    order of the parts; sums add; mismatched shapes and NaN are reported."""
+    R = q.ShardReadout
+    a = R(5, 0.25, 0.1, 0.4, 4, 1)
+    b = R(2, 0.25, 0.05, 0.35, 4, 0)
+    c = R(9, 0.10, 0.2, 0.25, 4, 2)
+    for parts in ([a, b, c], [c, a, b], [b, c, a]):
+        am, pa, pm, tot = q.merge_shard_readouts(parts)
+        assert am == 2 and pa == 2 / 16
+        assert pm == pytest.approx(0.35) and tot == pytest.approx(1.0)
+    with pytest.raises(q.QpeError) as e:
+        q.merge_shard_readouts([a, R(2, 0.3, 0.0, 0.1, 5, 0)])
+    assert e.value.status == q.ERR_SHAPE
+    with pytest.raises(q.QpeError) as e:
+        q.merge_shard_readouts([a, R(2, float("nan"), 0.0, 0.1, 4, 0)])
+    assert e.value.status == q.ERR_NUMERIC
+
+
+def test_interleave_shards(q):
+    P = np.arange(32, dtype=np.float64)
+    parts = [P[r::4] for r in range(4)]
+    assert np.array_equal(q.interleave_shards(parts), P)

@@ -80,10 +80,12 @@ def test_end_to_end_against_oracle(q, prec, tol):
     assert np.abs(P - ref).max() <= tol
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 3])
 def test_c3_with_tensor_core_squaring(q, prec):
-    """Nmat = 12, Nmeas = 20 (32 qubits), squarings on the tensor cores:
-    the whole histogram against the Fejer closed form."""
+    """Nmat = 12, Nmeas = 20 (32 qubits), squarings on the tensor cores, gates
+    in complex64 on the CUDA cores or as FP16x2 products on the tensor cores:
+    the whole histogram against the Fejer closed form (max-abs, and for the
+    split precision the L1 bound 1e-6)."""
     inst = W.c3()
     plan = q.Plan(inst.nmat, inst.nmeas, prec, q.FLAG_SQUARE_TC | q.FLAG_TIMING)
     plan.load(inst.U, inst.psi)
@@ -93,7 +95,9 @@ def test_c3_with_tensor_core_squaring(q, prec):
     Q = fejer.probabilities(inst.phases, inst.weights, inst.nmeas)
     err = np.abs(P - Q)
     print(f"prec {prec}: squaring {st[0]:.1f} ms, max-abs {err.max():.3e} L1 {err.sum():.3e}")
-    assert err.max() <= (1e-5 if prec == 1 else 1e-4)
+    assert err.max() <= 1e-5
+    if prec == 3:
+        assert err.sum() <= 1e-6
     assert am == int(np.argmax(Q))
 
 

@@ -27,9 +27,9 @@ def q():
     return qpe
 
 
-# FP64 fused, complex64 plain, BF16x3 on the tensor cores (with tensor-core
+# FP64 fused, complex64 plain, FP16x2 on the tensor cores (with tensor-core
 # squaring), and a graph-replayed plan
-CASES = [(0, 2, 6, 0), (1, 3, 9, 0x8), (2, 8, 8, 0x100), (1, 4, 10, 0x2)]
+CASES = [(0, 2, 6, 0), (1, 3, 9, 0x8), (3, 8, 8, 0x100), (1, 4, 10, 0x2)]
 
 
 @pytest.mark.parametrize("prec,nmat,nmeas,flags", CASES)

@@ -1,7 +1,12 @@
-"""Multi-rank logic on CPU ranks (gloo, world size 2, 127.0.0.1).
+"""Multi-rank logic on CPU ranks (gloo, world size 2 and 4, 127.0.0.1).
 
 * bench.py's replica aggregation: the job time is the slowest rank's, the
   throughput counts every rank's runs.
+* The library's sharded-plan host path (qpe_plan_shard): each rank holds the
+  outcomes y = rank (mod world) compactly, as a sharded plan's qpe_probs
+  returns them (here cut from the oracle's histogram, since these ranks have
+  no GPU); qpe.gather_shards all-gathers and interleaves the slices and merges
+  the ranks' readout partials with the library's qpe_merge_shard_readouts.
 * The row-sharded layout of the statevector across ranks (each rank owns the
   rows whose lowest measurement bit equals its rank): local controlled gates
   and a local DFT over the high bits, then one exchange of N/4 rows per rank
@@ -124,3 +129,36 @@ def test_row_sharded_exchange_matches_oracle(nmat, nmeas):
     assert np.array_equal(hist0, res[1][1])
     ref = gates.qpe_probabilities(res[0][2], res[0][3], nmeas)
     assert np.abs(hist0 - ref).max() < 1e-12
+
+
+def _gather_worker(rank, world, port, q, nmat, nmeas, seed):
+    import sys
+    sys.path.insert(0, ROOT)
+    dist = _init(rank, world, port)
+    import torch
+    from oracle import gates
+    from paper_2507_17175_gb300 import qpe, workloads as W
+    rng = np.random.default_rng(seed)
+    inst = W.haar_instance(rng, nmat, nmeas, superposition=True)
+    P = gates.qpe_probabilities(inst.U, inst.psi, nmeas)
+    N = 1 << nmeas
+    local = np.ascontiguousarray(P[rank::world])  # what this rank's plan returns
+    ys = np.arange(rank, N, world)
+    j = int(np.argmax(local))
+    part = qpe.ShardReadout(int(ys[j]), float(local[j]), float(np.sum(local * ys) / N), float(local.sum()),
+                            nmeas, rank)
+    hist, am, pa, pm = qpe.gather_shards(dist, torch.from_numpy(local), part)
+    q.put((rank, hist.numpy(), am, pa, pm, P))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,nmat,nmeas", [(2, 3, 9), (4, 2, 10)])
+def test_sharded_histogram_gather_and_readout_merge(world, nmat, nmeas):
+    from oracle import readout
+    res = _run(_gather_worker, world, nmat, nmeas, 7)
+    P = res[0][5]
+    for rank, hist, am, pa, pm, _ in res:
+        assert np.array_equal(hist, P)
+        assert am == readout.argmax_lowest(P)
+        assert pa == readout.phase_max_norm(P)
+        assert abs(pm - readout.phase_weighted_mean(P)) <= 1e-12
