@@ -314,15 +314,22 @@ def bench_ours(args, rank, world, local_rank):
     split = {}
     for name, prec in (("fp16x2", qpe.C64_FP16X2), ("tf32x3", qpe.C64_TF32X3)):
         try:
-            ps = make(prec, qpe.FLAG_GRAPH)
+            ps = make(prec, qpe.FLAG_GRAPH | qpe.FLAG_TIMING)
         except qpe.QpeError as e:
             split[name] = {"available": False, "reason": str(e)}
             continue
-        ts = timed_steps(ps, k32, 3)
+        ks = []
+        ts = timed_steps(ps, k32, 3, kern_acc=ks)
         Ps = torch.empty(N, dtype=torch.float64, device=dev)
         _, ams, _, _ = ps.probs(Ps)
-        split[name] = {"runs_per_s": 1e3 / (sum(ts) / k32), "ms_per_run": sum(ts) / k32,
+        tc_top = bool(ps.query(qpe.INFO_TC_TOP_LEVEL))
+        split[name] = {"runs_per_s": 1e3 / (sum(ts) / k32), "ms_per_run": sum(ts) / k32, "steps": k32,
+                       "top_level_kernel_ms": statistics.mean(k[0] for k in ks if k[1] == 1),
+                       "top_level_on_tensor_cores": tc_top,
                        "argmax_equal": bool(ams == am64), **compare(Ps)}
+        split[name]["speedup_vs_fp64"] = split[name]["runs_per_s"] / (1e3 / ms_per_step)
+        if not tc_top:
+            split[name]["note"] = "Nmat = 4 under this precision runs the fused complex64 levels on the CUDA cores"
         del ps, Ps
     torch.cuda.empty_cache()
 
@@ -355,6 +362,23 @@ def bench_ours(args, rank, world, local_rank):
     c64["roofline"] = {"bound": "alu", "achieved": round(c64_flops_ach, 1), "peak": round(fp32_peak * 1e3, 1),
                        "unit": "GFLOP/s", "frac": round(c64_flops_ach / (fp32_peak * 1e3), 4),
                        "kernel": "level2_kernel<float2, 4, 1> (top level)", "note": "same flop count as the FP64 line"}
+    if split.get("fp16x2", {}).get("top_level_on_tensor_cores"):
+        # the contraction runs as fp16 products on the tensor cores (hi.hi over K = 2d, cross terms over
+        # K = 4d: 3 x 2 x N x 2d x 2d flop); the twiddle, the 16-point DFT and |X|^2 (31 flop per complex
+        # point: 6 + 20 + 3, plus 2 for the operand scale) run on the FP32 units of the drain warps
+        t_tc = split["fp16x2"]["top_level_kernel_ms"] * 1e-3
+        tensor_flop = 3.0 * 2.0 * N * (2 * d) * (2 * d)
+        alu_flop = 31.0 * N * d
+        split["fp16x2"]["roofline"] = {
+            "bound": "alu", "achieved": round(alu_flop / t_tc / 1e9, 1), "peak": round(fp32_peak * 1e3, 1),
+            "unit": "GFLOP/s", "frac": round(alu_flop / t_tc / 1e9 / (fp32_peak * 1e3), 4),
+            "tensor_tflops": round(tensor_flop / t_tc / 1e12, 1),
+            "tensor_frac_of_bf16_peak": round(tensor_flop / t_tc / 1e12 / pk["bf16_tflops"], 4),
+            "kernel": "level_tc_top_kernel (tcgen05 fp16 split products + FP32 drain)",
+            "algorithmic_equiv_gflops": round(flops / t_tc / 1e9, 1),
+            "note": "FP32 work of the drain (31 flop per complex point) against the measured FP32 FMA peak; the "
+                    "contraction's tensor-core flops beside it against the measured bf16 peak (fp16 runs at the "
+                    "same rate)"}
     hbm_term_ms = 2.0 * N * d * 16 / (pk["hbm_gbs"] * 1e9) * 1e3
 
     res = {

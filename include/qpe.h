@@ -72,10 +72,17 @@ typedef enum {
                       /* accumulation in two passes (hi.hi, then both cross      */
                       /* products over a doubled K); rows of the state are       */
                       /* scaled by powers of two into fp16's range and U's       */
-                      /* embedding by 2^14 (nmat >= 5, plain schedule); squaring */
-                      /* and readout stay FP64                                   */
+                      /* embedding by 2^14; squaring and readout stay FP64.      */
+                      /* nmat >= 5: plain schedule, gate GEMMs on the tensor    */
+                      /* cores; nmat = 4: fused schedule with its top level     */
+                      /* (gates of the 4 low measurement qubits, 16-point DFT,  */
+                      /* histogram) on the tensor cores when it has >= 128      */
+                      /* pencils; otherwise (nmat <= 3, or too few pencils) the  */
+                      /* fused complex64 schedule on the CUDA cores              */
   QPE_C64_TF32X3 = 4  /* as QPE_C64_FP16X2 with tf32 hi/lo splits (~21 bits)    */
-                      /* and three products A_hi B_hi + A_hi B_lo + A_lo B_hi    */
+                      /* and three products A_hi B_hi + A_hi B_lo + A_lo B_hi;   */
+                      /* nmat <= 4 runs the fused complex64 schedule on the      */
+                      /* CUDA cores                                              */
 } qpe_precision;
 
 /* Plan flags. */
@@ -150,8 +157,10 @@ typedef enum {
                                 /* of the grouped FP64 squaring in use         */
   QPE_INFO_LEVELS = 7,          /* fused schedule: number of levels (0 when    */
                                 /* the plan runs another schedule)            */
-  QPE_INFO_TOP_LEVEL_BITS = 8   /* fused schedule: r of the top level, i.e.    */
+  QPE_INFO_TOP_LEVEL_BITS = 8,  /* fused schedule: r of the top level, i.e.    */
                                 /* its DFT length is 2^r (0 otherwise)         */
+  QPE_INFO_TC_TOP_LEVEL = 9     /* 1 when the fused top level runs on the      */
+                                /* tensor cores (QPE_C64_FP16X2, nmat = 4)      */
 } qpe_info;
 
 /*
@@ -159,8 +168,8 @@ typedef enum {
  * GPU. On success *out is a new plan and *workspace_bytes the device bytes
  * qpe_bind needs. Errors: QPE_ERR_ARG for null pointers or nmat/nmeas/prec
  * out of range; QPE_ERR_UNSUPPORTED for combinations not built
- * (QPE_C64_BF16X3 in any plan; tensor-core precisions with nmat < 5 or the
- * gate-by-gate schedule;
+ * (QPE_C64_BF16X3 in any plan; the split precisions with the gate-by-gate
+ * schedule;
  * QPE_FLAG_GATE_SWEEP with nmat > 6; QPE_FLAG_REPEAT_U without
  * QPE_FLAG_GATE_SWEEP or with nmeas > 14).
  */

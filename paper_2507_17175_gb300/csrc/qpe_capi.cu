@@ -60,7 +60,7 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   in.off_pow32 = is_c64(prec) ? take((size_t)in.nmeas * d * d * 8) : 0;
   in.off_psi = take((size_t)d * 16);
   in.fused = in.nmat <= QPE_MAX_FUSED_NMAT && !(flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP)) &&
-             (!is_tc(prec) || batched);
+             (!is_tc(prec) || batched || in.nmat <= 4);
   in.keep_state = (flags & QPE_FLAG_KEEP_STATE) != 0;
   if (in.nmat <= QPE_MAX_FUSED_NMAT) in.levels = qpe::make_levels(in.nmeas, in.nmat, elem_size(prec), 0);
   // the fused schedule never materialises the N x d state unless asked to keep
@@ -81,6 +81,11 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   if (is_tc(prec) && !in.fused) in.off_tcsplit = take(qpe::tc_split_bytes(prec, in.nmat, in.nmeas));
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
   if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
+  // the fused top level on the tensor cores: FP16x2, d = 16 (a 16-point top
+  // level), at least one tile of 128 pencils per rank, histogram only
+  in.tc_top = in.fused && !batched && prec == QPE_C64_FP16X2 && in.nmat == 4 && !in.keep_state &&
+              !in.levels.empty() && in.levels[0].r == 4 && in.levels[0].logna - in.shard_log >= 7;
+  if (in.tc_top) in.off_tctab = take(qpe::tc_top_table_bytes());
   in.fft = qpe::make_fft_plan(in.nmeas, d, elem_size(prec));
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a
@@ -114,8 +119,7 @@ qpe_status check_desc(const qpe_plan_desc* desc, bool batched = false) {
   // against FP64 then exceeds 1e-6 after enough gate levels (1.6e-6 measured
   // at Nmeas = 18), so the library does not offer that precision
   if (desc->prec == QPE_C64_BF16X3) return QPE_ERR_UNSUPPORTED;
-  if (is_tc(desc->prec) && ((desc->nmat < 5 && !batched) || (desc->flags & QPE_FLAG_GATE_SWEEP)))
-    return QPE_ERR_UNSUPPORTED;
+  if (is_tc(desc->prec) && (desc->flags & QPE_FLAG_GATE_SWEEP)) return QPE_ERR_UNSUPPORTED;
   if ((desc->flags & QPE_FLAG_GATE_SWEEP) && desc->nmat > 6) return QPE_ERR_UNSUPPORTED;
   return QPE_OK;
 }
@@ -704,7 +708,7 @@ qpe_status qpe_plan_shard(const qpe_plan_desc* desc, int32_t rank, int32_t world
   // the sharded form partitions the fused schedule's outcomes; the top level
   // must have at least `world` pencils
   if (desc->nmat > QPE_MAX_FUSED_NMAT || (desc->flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP | QPE_FLAG_REPEAT_U)) ||
-      is_tc(desc->prec))
+      (is_tc(desc->prec) && desc->nmat > 4))
     return QPE_ERR_UNSUPPORTED;
   const std::vector<qpe::Level> lv = qpe::make_levels(desc->nmeas, desc->nmat, elem_size(desc->prec), 0);
   if (lv.empty() || lv[0].logna < sh) return QPE_ERR_UNSUPPORTED;
@@ -840,6 +844,7 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(p, e, "device query");
   for (Instance& in : p->inst) {
+    in.nsm = nsm;
     if (!in.levels.empty()) {
       int occ = 1;
       for (const qpe::Level& L : in.levels) {
@@ -1073,6 +1078,7 @@ int64_t qpe_query(qpe_plan_t p, int32_t key) {
     case QPE_INFO_SQUARE_TILE: return p->sq_variant == 1 ? 16 : (p->sq_variant == 2 ? 32 : 8);
     case QPE_INFO_LEVELS: return p->inst[0].fused ? (int64_t)p->inst[0].levels.size() : 0;
     case QPE_INFO_TOP_LEVEL_BITS: return p->inst[0].fused ? p->inst[0].levels[0].r : 0;
+    case QPE_INFO_TC_TOP_LEVEL: return p->inst[0].tc_top ? 1 : 0;
   }
   return -1;
 }

@@ -256,6 +256,10 @@ struct Instance {
   // y = shard_rank mod 2^shard_log; its histogram (and kept state) hold them
   // compactly, y at local index y >> shard_log
   int shard_log = 0, shard_rank = 0;
+  // top level of the fused schedule on the tensor cores (QPE_C64_FP16X2, d = 16)
+  bool tc_top = false;
+  size_t off_tctab = 0;  // its fp16 table operands (both orders)
+  int nsm = 0;           // multiprocessors of the bound device
   bool keep_state = false;
   bool loaded = false;
   bool powers_done = false;
@@ -387,6 +391,7 @@ inline void finalize_readout(const Instance& in, char* ws, int count, cudaStream
   launch_finalize(in, ws, count, s);
 }
 size_t level_smem_bytes(int logd, int mode, size_t esize);
+size_t tc_top_table_bytes();
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 // a level of a sharded plan computes only this rank's outcomes when it has at

@@ -27,7 +27,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cuda_fp16.h>
+
 #include "qpe_internal.cuh"
+#include "qpe_tcgen05.cuh"
 
 namespace qpe {
 
@@ -57,6 +60,29 @@ template <typename C>
 __device__ __forceinline__ C czero() {
   return mk((typename real_of<C>::type)0, (typename real_of<C>::type)0);
 }
+
+// The complex64 schedules' readout of one thread: bin values in FP32 (the
+// histogram stores them widened, bit-exactly), the argmax compared in FP32,
+// and Kahan-compensated FP32 sums of P y and P (off GB300's slow FP64 units).
+struct HistAcc32 {
+  float best = -1.f;
+  int64_t besty = INT64_MAX;
+  float wsum = 0.f, wcomp = 0.f, psum = 0.f, pcomp = 0.f;
+  __device__ __forceinline__ void add(float v, int64_t y) {
+    if (v > best || (v == best && y < besty)) {
+      best = v;
+      besty = y;
+    }
+    float t1 = v * (float)y - wcomp;  // P y (the finalize divides by N)
+    float t2 = wsum + t1;
+    wcomp = (t2 - wsum) - t1;
+    wsum = t2;
+    t1 = v - pcomp;
+    t2 = psum + t1;
+    pcomp = (t2 - psum) - t1;
+    psum = t2;
+  }
+};
 
 template <typename C>
 struct Acc;  // per-row |x|^2 accumulator type
@@ -278,7 +304,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
 
   double best = -1.0, wsum = 0.0, psum = 0.0;
   int64_t besty = INT64_MAX;
-  float wsum_f = 0.f, wcomp_f = 0.f, psum_f = 0.f, pcomp_f = 0.f;
+  HistAcc32 h32;
 
   // histogram bin of local index yl (outcome y = rk + (yl << sh)) <- s / N^2,
   // with the readout partials (argmax, Kahan sums) over the outcome y
@@ -287,19 +313,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
     if (sizeof(C) == 8) {
       const float v = (float)s * (float)a.pscale;  // pscale = 1/N^2, a power of two
       a.hist[yl] = widen_nonneg(v);
-      if ((double)v > best || ((double)v == best && y < besty)) {
-        best = v;
-        besty = y;
-      }
-      const float yv = v * (float)y;  // P y (finalize divides by N), Kahan-compensated
-      float t1 = yv - wcomp_f;
-      float t2 = wsum_f + t1;
-      wcomp_f = (t2 - wsum_f) - t1;
-      wsum_f = t2;
-      t1 = v - pcomp_f;
-      t2 = psum_f + t1;
-      pcomp_f = (t2 - psum_f) - t1;
-      psum_f = t2;
+      h32.add(v, y);
     } else {
       const double v = (double)s * a.pscale;
       a.hist[yl] = v;
@@ -481,8 +495,10 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   cp_async_wait<0>();  // a share with no iterations still issued its slice copies
   if (MODE != 0) {
     if (sizeof(C) == 8) {
-      wsum = (double)wsum_f;
-      psum = (double)psum_f;
+      best = h32.best;
+      besty = h32.besty;
+      wsum = (double)h32.wsum;
+      psum = (double)h32.psum;
     }
     for (int off = 16; off > 0; off >>= 1) {
       const double ob = __shfl_xor_sync(0xffffffffu, best, off);
@@ -638,7 +654,365 @@ __global__ void seed_psi_kernel(const double2* __restrict__ psi, C* __restrict__
   pdl_trigger();
 }
 
+// ------------------------------------------- top level on the tensor cores
+// The top level of the fused schedule for d = 16 (L = 16) under the split
+// precision QPE_C64_FP16X2. The level's contraction
+//   T[y_a][m_b][i] = sum_k M[m_b][i][k] Z[y_a][k]
+// is one real GEMM per tile of 128 pencils y_a:
+//   A (128 x 32): row y_a = the 32 floats (re, im interleaved) of Z[y_a],
+//   B (512 x 32): row n = (i, m_b, c) = the real embedding of M, n-major
+//                 (c = 0 real part: (Re M, -Im M); c = 1: (Im M, Re M)),
+//   D = A B^T (128 x 512, FP32 in tensor memory): column n of row y_a is the
+//       real (c = 0) or imaginary part of T[y_a][m_b][i],
+// as fp16 hi/lo products in two passes: A_hi B_hi, then [A_hi | A_lo] times
+// [B_lo | B_hi] over K = 64 (both cross products in one pass). Each A row is
+// scaled by a power of two into fp16's range (largest |entry| in
+// [2^14, 2^15)) and B by 2^14; the drain multiplies by the exact inverse. The
+// 128-byte rows [hi | lo] are the K-major, 128-byte-swizzled layout the MMA
+// reads. B (both orders) stays in shared memory for the whole launch.
+//
+// Roles (416 threads, one CTA per SM, persistent over tiles):
+//   warps 0..3   load the tile's Z rows (one row per thread), split and store
+//                them into one of two A stages
+//   warp 4       allocates tensor memory; lane 0 issues the MMAs: columns
+//                [0, 256) (i < 8) into tensor-memory half 0, [256, 512) into
+//                half 1, so the MMAs of one half overlap the drain of the other
+//   warps 5..12  drain: thread (set s, lane group q, lane) owns pencil
+//                y_a = 32 q + lane of the tile and the columns i of set s
+//                (4 per half); for each i it loads the 16 values T[m_b]
+//                (32 floats, one tcgen05.ld), multiplies by w_N^(m_b y_a),
+//                runs the length-16 DFT over m_b in registers and adds |X|^2
+//                into 16 bin sums; set 1 hands its sums to set 0 through
+//                shared memory, set 0 writes the histogram and the readout.
+// Every wait is an mbarrier wait with a poll limit; on expiry the CTA records
+// QPE_ERR_TIMEOUT, frees its tensor memory and returns.
+constexpr int kTcL = 16, kTcD = 16;   // DFT length and target dimension of this kernel
+constexpr int kTcRows = 128;          // pencils per tile (MMA M)
+constexpr int kTcN = 2 * kTcD * kTcL; // 512 GEMM columns
+constexpr int kTcThreads = 416;
+constexpr int kTcSqStride = 17;       // padded row of the hand-over buffer
+constexpr size_t kTcBBytes = (size_t)kTcN * 128;  // one B order, 64 KiB
+constexpr size_t kTcABytes = (size_t)kTcRows * 128;
+constexpr size_t kTcSmem = 2 * kTcBBytes + 2 * kTcABytes + 2 * (size_t)kTcRows * kTcSqStride * 4 +
+                           2 * (size_t)kTcRows * 4 + 1024;
+
+struct TcTopArgs {
+  const float2* seeds;       // Z of the level below (compact when the level below is sharded)
+  const __half* btab;        // [2][512][64]: rows [hi | lo], then [lo | hi]
+  const float2* tw_lo;
+  const float2* tw_hi;
+  double* hist;
+  Partial* parts;
+  int* err;
+  int64_t ntiles;            // local pencils / 128
+  int nmeas, logna, htw, sh, rk, seed_sh, seed_rk;
+  double pscale;
+};
+
+// B rows of the top level's table (tab[k][m_b d + i] = M[m_b][i][k],
+// complex64), scaled by 2^14 and split into fp16 hi / lo.
+__global__ void __launch_bounds__(256) tc_top_table_kernel(const float2* __restrict__ tab, __half* __restrict__ out) {
+  pdl_begin();
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kTcN * 32; e += gridDim.x * blockDim.x) {
+    const int n = e >> 5, kk = e & 31;
+    const int i = n >> 5, mb = (n >> 1) & 15, c = n & 1;
+    const int k = kk >> 1, cp = kk & 1;
+    const float2 m = tab[k * (kTcL * kTcD) + mb * kTcD + i];
+    const float v = c == 0 ? (cp == 0 ? m.x : -m.y) : (cp == 0 ? m.y : m.x);
+    const float vs = v * 16384.0f;  // 2^14, exact
+    const __half hi = __float2half_rn(vs);
+    const __half lo = __float2half_rn(vs - __half2float(hi));
+    out[(size_t)n * 64 + kk] = hi;             // [hi | lo]
+    out[(size_t)n * 64 + 32 + kk] = lo;
+    out[(size_t)(kTcN + n) * 64 + kk] = lo;    // [lo | hi]
+    out[(size_t)(kTcN + n) * 64 + 32 + kk] = hi;
+  }
+  pdl_trigger();
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a) {
+  using namespace tcg;
+  pdl_begin();
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  unsigned char* Bs = base;                            // B1 then B2, 64 KiB each
+  unsigned char* As = base + 2 * kTcBBytes;            // two A stages, 16 KiB each
+  float* sq = reinterpret_cast<float*>(As + 2 * kTcABytes);   // [2][128][17]
+  float* inv = sq + 2 * kTcRows * kTcSqStride;                // [2][128]
+  __shared__ uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2], sq_full[2], sq_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ Partial sp[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&a_full[b], kTcRows);
+      mbar_init(&a_empty[b], 1 + 8);
+      mbar_init(&t_full[b], 1);
+      mbar_init(&t_empty[b], 8);
+      mbar_init(&sq_full[b], kTcRows);
+      mbar_init(&sq_empty[b], kTcRows);
+    }
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // both orders of B into shared memory, swizzled (16-byte chunks)
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.btab);
+    for (int q = threadIdx.x; q < 2 * kTcN * 8; q += kTcThreads) {
+      const int which = q / (kTcN * 8), n = (q >> 3) % kTcN, c = q & 7;
+      *reinterpret_cast<uint4*>(Bs + which * kTcBBytes + sw128_offset(n, c)) = __ldg(src + q);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const int lna = a.logna - a.sh;
+  volatile int* vfail = &fail;
+
+  if (warp < 4) {
+    // ---------------------------------------------------------- producer
+    const int p = threadIdx.x;  // tile row
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+      const int b = it & 1;
+      if (it >= 2 && !mbar_wait(&a_empty[b], ((it >> 1) - 1) & 1)) {
+        atomicExch(&fail, 1);
+        break;
+      }
+      if (*vfail) break;
+      const int64_t j = t * kTcRows + p;
+      const float4* src = reinterpret_cast<const float4*>(a.seeds + ((a.seed_rk + (j << a.seed_sh)) << 4));
+      float x[32];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 v = __ldg(src + c);
+        x[4 * c] = v.x;
+        x[4 * c + 1] = v.y;
+        x[4 * c + 2] = v.z;
+        x[4 * c + 3] = v.w;
+      }
+      float mx = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) mx = fmaxf(mx, fabsf(x[c]));
+      // floor(log2(mx)) from the exponent field; zero or tiny rows keep scale 1
+      const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
+      const int e = (ex < -100 || ex > 100) ? 0 : 14 - ex;
+      const float sc = __uint_as_float((uint32_t)(127 + e) << 23);
+      inv[b * kTcRows + p] = __uint_as_float((uint32_t)(127 - e - 14) << 23);
+      unsigned char* row = As + b * kTcABytes;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float x0 = x[8 * c + 2 * h] * sc, x1 = x[8 * c + 2 * h + 1] * sc;
+          const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+          const __half l0 = __float2half_rn(x0 - __half2float(h0)), l1 = __float2half_rn(x1 - __half2float(h1));
+          hw[h] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+          lw[h] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+        }
+        *reinterpret_cast<uint4*>(row + sw128_offset(p, c)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(row + sw128_offset(p, 4 + c)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&a_full[b]);
+    }
+  } else if (warp == 4) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc<kTcFP16, 256>();
+      const uint32_t b1 = smem_u32(Bs), b2 = smem_u32(Bs + kTcBBytes);
+      int it = 0;
+      for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+        const int b = it & 1;
+        if (!mbar_wait(&a_full[b], (it >> 1) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        if (*vfail) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ad = sw128_desc(smem_u32(As + b * kTcABytes));
+        bool ok = true;
+        for (int h = 0; h < 2; ++h) {
+          if (it >= 1 && !mbar_wait(&t_empty[h], (it - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t bd1 = sw128_desc(b1 + (uint32_t)h * 32768u), bd2 = sw128_desc(b2 + (uint32_t)h * 32768u);
+          const uint32_t d = tmem + (uint32_t)(h * 256);
+          umma_k<kTcFP16>(d, ad, bd1, idesc, 0u);          // A_hi B_hi, K = 0..15
+          umma_k<kTcFP16>(d, ad + 2, bd1 + 2, idesc, 1u);  //            K = 16..31
+#pragma unroll
+          for (int k = 0; k < 4; ++k) umma_k<kTcFP16>(d, ad + 2 * k, bd2 + 2 * k, idesc, 1u);  // cross, K = 64
+          umma_commit(&t_full[h]);
+        }
+        if (!ok) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        umma_commit(&a_empty[b]);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- drain
+    const int dw = warp - 5;
+    const int set = dw >> 2, lg = warp & 3;
+    const int row = lg * 32 + lane;
+    const int64_t tw_mask = (int64_t(1) << a.htw) - 1;
+    const int lvl_shift = a.nmeas - a.logna - 4;
+    const int64_t lvl_mask = (int64_t(1) << (a.logna + 4)) - 1;
+    HistAcc32 h32;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+      const int b = it & 1;
+      const int64_t j = t * kTcRows + row;
+      const int64_t ya = a.rk + (j << a.sh);
+      float2 tw[kTcL];
+#pragma unroll
+      for (int mb = 0; mb < kTcL; ++mb) {
+        const int64_t ex = (((int64_t)mb * ya) & lvl_mask) << lvl_shift;
+        tw[mb] = cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
+      }
+      float acc[kTcL];
+#pragma unroll
+      for (int yb = 0; yb < kTcL; ++yb) acc[yb] = 0.f;
+      float invr = 0.f;
+      bool ok = true;
+      for (int h = 0; h < 2 && ok; ++h) {
+        bool got = mbar_wait(&t_full[h], it & 1);
+        got = __all_sync(0xffffffffu, got && !*vfail) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!got) {
+          ok = false;
+          break;
+        }
+        if (h == 0) {
+          invr = inv[b * kTcRows + row];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&a_empty[b]);  // this warp is done with the stage's scales
+        }
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+          const int il = set * 4 + q;  // column i = 8 h + il
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * 256 + il * 32), v);
+          float2 x[kTcL];
+#pragma unroll
+          for (int mb = 0; mb < kTcL; ++mb)
+            x[mb] = cmul(make_float2(__uint_as_float(v[2 * mb]) * invr, __uint_as_float(v[2 * mb + 1]) * invr),
+                         tw[mb]);
+          dft_k<float2, 4, kTcL>(x);
+#pragma unroll
+          for (int yb = 0; yb < kTcL; ++yb) acc[yb] = fmaf(x[yb].x, x[yb].x, fmaf(x[yb].y, x[yb].y, acc[yb]));
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&t_empty[h]);
+      }
+      if (!ok || *vfail) {
+        atomicExch(&fail, 1);
+        break;
+      }
+      float* sqb = sq + b * kTcRows * kTcSqStride + row * kTcSqStride;
+      if (set == 1) {
+        if (it >= 2 && !mbar_wait(&sq_empty[b], ((it >> 1) - 1) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+#pragma unroll
+        for (int yb = 0; yb < kTcL; ++yb) sqb[yb] = acc[yb];
+        mbar_arrive(&sq_full[b]);
+      } else {
+        if (!mbar_wait(&sq_full[b], (it >> 1) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+#pragma unroll
+        for (int yb = 0; yb < kTcL; ++yb) acc[yb] += sqb[yb];
+        mbar_arrive(&sq_empty[b]);
+#pragma unroll
+        for (int yb = 0; yb < kTcL; ++yb) {
+          const int64_t yl = j + ((int64_t)yb << lna);
+          const float pv = acc[yb] * (float)a.pscale;  // pscale = 1/N^2, a power of two
+          a.hist[yl] = widen_nonneg(pv);
+          h32.add(pv, a.rk + (yl << a.sh));
+        }
+      }
+    }
+    if (set == 0) {  // readout partial of this CTA: the four set-0 warps
+      double best = h32.best, wsum = (double)h32.wsum, psum = (double)h32.psum;
+      int64_t besty = h32.besty;
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int64_t oy = __shfl_xor_sync(0xffffffffu, besty, off);
+        better(best, besty, ob, oy);
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+        psum += __shfl_xor_sync(0xffffffffu, psum, off);
+      }
+      if (lane == 0) sp[lg] = Partial{best, besty, wsum, psum};
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial r = sp[0];
+    for (int w = 1; w < 4; ++w) merge_partial(r, sp[w]);
+    a.parts[blockIdx.x] = r;
+    if (fail) atomicExch(a.err, (int)QPE_ERR_TIMEOUT);
+  }
+  if (warp == 4)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  pdl_trigger();
+}
+
 // --------------------------------------------------------------- host side
+size_t tc_top_table_bytes() { return 2 * kTcBBytes; }
+
+// The tensor-core top level: its table operands, then the persistent kernel
+// (one CTA per SM, at most one per tile). Returns launches or -1.
+static int launch_tc_top(const Instance& in, char* ws, const LevelArgs<float2>& la, cudaStream_t s,
+                         cudaEvent_t* top_ev, int64_t* grid_out) {
+  __half* btab = reinterpret_cast<__half*>(ws + in.off_tctab);
+  if (launch_k(tc_top_table_kernel, dim3(64), dim3(256), 0, s, la.tab, btab) != cudaSuccess) return -1;
+  TcTopArgs a{};
+  a.seeds = la.seeds;
+  a.btab = btab;
+  a.tw_lo = la.tw_lo;
+  a.tw_hi = la.tw_hi;
+  a.hist = la.hist;
+  a.parts = la.parts;
+  a.err = reinterpret_cast<int*>(ws + in.off_err);
+  a.ntiles = (int64_t(1) << (la.logna - la.sh)) / kTcRows;
+  a.nmeas = la.nmeas;
+  a.logna = la.logna;
+  a.htw = la.htw;
+  a.sh = la.sh;
+  a.rk = la.rk;
+  a.seed_sh = la.seed_sh;
+  a.seed_rk = la.seed_rk;
+  a.pscale = la.pscale;
+  int64_t grid = in.nsm > 0 ? in.nsm : 1;
+  if (grid > a.ntiles) grid = a.ntiles;
+  if (grid > kReduceBlocks) grid = kReduceBlocks;
+  if (top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
+  if (launch_k(level_tc_top_kernel, dim3((unsigned)grid), dim3(kTcThreads), kTcSmem, s, a) != cudaSuccess) return -1;
+  if (top_ev && record_event(top_ev[1], s) != cudaSuccess) return -1;
+  *grid_out = grid;
+  return 2;
+}
+
 template <int LD, int M>
 static size_t smem_of(size_t esize) {
   return esize == 16 ? LvShape<LD, true, M>::smem(esize) : LvShape<LD, false, M>::smem(esize);
@@ -725,6 +1099,8 @@ cudaError_t configure_level_kernels() {
   cudaError_t e = cudaMemcpyToSymbol(c_w32_64, w64, sizeof(w64));
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_w32_32, w32v, sizeof(w32v));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(level_tc_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   return set_level_attrs();
 }
@@ -821,6 +1197,17 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s,
       a.hist = reinterpret_cast<double*>(ws + in.off_hist);
       a.parts = reinterpret_cast<Partial*>(ws + in.off_partials);
       if (grid > kReduceBlocks) grid = kReduceBlocks;
+      if constexpr (sizeof(C) == 8) {
+        if (in.tc_top) {
+          const int r = launch_tc_top(in, ws, a, s, top_ev, &grid);
+          if (r < 0) return -1;
+          launches += r;
+          finalize_readout(in, ws, (int)grid, s);
+          if (cudaPeekAtLastError() != cudaSuccess) return -1;
+          ++launches;
+          break;
+        }
+      }
       if (top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
       if (keep_state) {
         a.xout = reinterpret_cast<C*>(ws + in.off_state);

@@ -38,6 +38,7 @@
 #include <cudaTypedefs.h>
 
 #include "qpe_internal.cuh"
+#include "qpe_tcgen05.cuh"
 
 namespace qpe {
 
@@ -49,93 +50,9 @@ constexpr int kStages = 4;  // most stages of any ring below
 // tiles of a K-block (A_hi, A_lo, B_hi, B_lo), 64 KiB for BN = 128.
 template <int BN>
 __host__ __device__ constexpr int tc_stages() { return BN == 128 ? 3 : 4; }
-constexpr int kBM = 128;
-constexpr uint32_t kWaitLimit = 1u << 24;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the phase with the given parity to complete: false after
-// `limit` polls without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t i = 0; i < limit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor for a K-major, 128-byte-swizzled tile:
-// start address >> 4, leading offset 16 B (unused for swizzled K-major),
-// stride offset 1024 B between 8-row groups, descriptor version 1,
-// swizzle mode 2 (128 B).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
-  return d;
-}
-
 }  // namespace
 
-// Element kinds of the split products.
-enum TcKind { kTcTF32 = 0, kTcBF16 = 1, kTcFP16 = 2 };
-
-template <int KIND>
-__device__ __forceinline__ void umma_k(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  if constexpr (KIND == kTcTF32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-  }
-}
-
-// Instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = BN;
-// operand format 2 = TF32 (kind::tf32), 1 = BF16 or 0 = FP16 (kind::f16).
-template <int KIND, int BN>
-__device__ __forceinline__ uint32_t make_idesc() {
-  const uint32_t fmt = KIND == kTcTF32 ? 2u : (KIND == kTcBF16 ? 1u : 0u);
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
+using namespace tcg;
 
 // D[m][n] (FP32, leading dimension ldd floats) for rows m < M of the tile grid
 // = sum over the 3 operand pairs of A_pair[m][:] . B_pair[n][:], K = 2d.

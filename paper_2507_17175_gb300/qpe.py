@@ -44,7 +44,7 @@ FLAG_SQUARE_TC = 0x100
 STAGE_POWERS, STAGE_SWEEP, STAGE_FFT, STAGE_REDUCE = 1, 2, 3, 4
 INFO_WORKSPACE_BYTES, INFO_STATE_BYTES, INFO_FFT_PASSES, INFO_LAST_LAUNCHES, INFO_INSTANCES = 1, 2, 3, 4, 5
 INFO_SQUARE_TILE = 6
-INFO_LEVELS, INFO_TOP_LEVEL_BITS = 7, 8
+INFO_LEVELS, INFO_TOP_LEVEL_BITS, INFO_TC_TOP_LEVEL = 7, 8, 9
 
 
 class PlanDesc(ctypes.Structure):

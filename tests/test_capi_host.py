@@ -71,7 +71,8 @@ def test_plan_sizes_workspace(q):
     (1, 1, 0, 0, "OK"),
     (6, 16, 1, 0x40, "OK"),   # QPE_FLAG_CHECK_UNITARY
     (7, 10, 3, 0, "OK"),      # QPE_C64_FP16X2
-    (4, 10, 3, 0, "ERR_UNSUPPORTED"),  # tensor-core precisions need nmat >= 5
+    (4, 10, 3, 0, "OK"),      # FP16x2 with nmat = 4: fused schedule
+    (4, 10, 3, 1, "ERR_UNSUPPORTED"),  # split precisions are not gate by gate
     (6, 16, 0, 0x42, "OK"),
 ])
 def test_plan_validation(q, nmat, nmeas, prec, flags, want):
@@ -122,11 +123,18 @@ def test_plan_batched_validation(q):
     assert q.plan_batched_workspace([(0, 4)], q.C64_FP32)[0] == q.ERR_ARG
     assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_GATE_SWEEP)[0] == q.ERR_UNSUPPORTED
     assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_TIMING)[0] == q.ERR_UNSUPPORTED
-    # split precisions: any nmat in a batched plan (nmat <= 6 runs fused in complex64), not in a single plan
+    # split precisions: any nmat in a batched plan (nmat <= 6 runs fused in complex64); single plans with
+    # nmat <= 4 run fused (FP16x2 at nmat = 4 with the top level on the tensor cores), not gate by gate
     st, ws, h = q.plan_batched_workspace([(3, 8), (8, 10)], q.C64_FP16X2, q.FLAG_SQUARE_TC)
     assert st == q.OK and ws > 0
     q.LIB.qpe_destroy(h)
-    assert q.plan_workspace(3, 8, q.C64_FP16X2, 0)[0] == q.ERR_UNSUPPORTED
+    st, ws, h = q.plan_workspace(4, 12, q.C64_FP16X2, 0)
+    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 1
+    q.LIB.qpe_destroy(h)
+    st, ws, h = q.plan_workspace(3, 8, q.C64_FP16X2, 0)
+    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0
+    q.LIB.qpe_destroy(h)
+    assert q.plan_workspace(3, 8, q.C64_FP16X2, q.FLAG_GATE_SWEEP)[0] == q.ERR_UNSUPPORTED
 
 
 def test_bf16x3_is_refused_everywhere(q):
