@@ -198,14 +198,30 @@ qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* w
  * of two, 1 .. 1024; 0 <= rank < world; QPE_ERR_ARG otherwise) that share one
  * problem, one GPU each. The paper runs on one GPU and names its memory as
  * the limit of the qubit count (Sec. 1); this splits the work of one run.
- * Rank r computes only the outcomes y = r (mod world): the fused schedule's
- * top level writes X[y] for y = y_a + N_a y_b from Z[y_a] alone (see
- * qpe_run), and y = y_a (mod world) whenever world divides N_a, so every level
- * with at least `world` pencils computes only this rank's y_a, from the
- * same rank's share of the level below; smaller (deeper) levels are computed
- * whole by every rank. No data moves between ranks during a run: each rank
- * reads U and psi in full (qpe_load) and squares U itself.
- * After qpe_run on every rank:
+ * Rank r ends up with the outcomes y = r (mod world). Each rank reads U and
+ * psi in full (qpe_load) and squares U itself. Two forms:
+ *   - fused schedule (nmat <= 6, not QPE_FLAG_PLAIN; QPE_FP64, QPE_C64_FP32,
+ *     or a split precision with nmat <= 4): the top level writes X[y] for
+ *     y = y_a + N_a y_b from Z[y_a] alone (see qpe_run), and y = y_a
+ *     (mod world) whenever world divides N_a, so every level with at least
+ *     `world` pencils computes only this rank's y_a, from the same rank's
+ *     share of the level below; smaller (deeper) levels are computed whole
+ *     by every rank. No data moves between ranks during a run. Needs a top
+ *     level with at least `world` pencils.
+ *   - plain schedule (nmat > 6, QPE_FLAG_PLAIN, or a split precision with
+ *     nmat >= 5): rank r holds the state rows m = r + world i (the low
+ *     log2(world) measurement bits fixed), applies their controlled gates,
+ *     and transforms them locally (QFT^-1 over the high bits); qpe_run stops
+ *     there, with this rank's twiddled transform sorted by owner rank in a
+ *     send buffer (qpe_shard_buffers). The caller then exchanges N / world^2
+ *     rows with every other rank (an all-to-all of equal chunks: send chunk
+ *     s goes to rank s, which stores it as its receive chunk r), and
+ *     qpe_shard_finish runs the cross-rank length-world DFT, the histogram and
+ *     the readout of this rank's outcomes. Needs N >= world^2; no
+ *     QPE_FLAG_KEEP_STATE, no stage-by-stage runs, no qpe_state (the final
+ *     state stays distributed).
+ * After qpe_run (and, for the plain form, the exchange and qpe_shard_finish)
+ * on every rank:
  *   - qpe_probs returns this rank's N / world bins compactly: probs[j] =
  *     P[rank + world j]; its argmax is the most probable of them (as a global
  *     y), phase_mean their share of sum_y P[y] y / N;
@@ -214,11 +230,9 @@ qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* w
  *   - qpe_shard_readout gives the partial that qpe_merge_shard_readouts
  *     combines into the readout of the whole histogram.
  * Gathering the histograms is the caller's (e.g. an all-gather of N / world
- * doubles per rank, then P[r + world j] = part_r[j]). Fused schedule only:
- * nmat <= 6, QPE_FP64 or QPE_C64_FP32, no QPE_FLAG_PLAIN / GATE_SWEEP /
- * REPEAT_U, and nmeas large enough that the top level has >= world pencils;
- * QPE_ERR_UNSUPPORTED otherwise. Host only, like qpe_plan; world = 1 gives the
- * ordinary plan.
+ * doubles per rank, then P[r + world j] = part_r[j]). QPE_FLAG_GATE_SWEEP,
+ * REPEAT_U and the requirements above not met: QPE_ERR_UNSUPPORTED. Host
+ * only, like qpe_plan; world = 1 gives the ordinary plan.
  */
 qpe_status qpe_plan_shard(const qpe_plan_desc* desc, int32_t rank, int32_t world, size_t* workspace_bytes,
                           qpe_plan_t* out);
@@ -395,6 +409,25 @@ typedef struct {
  * synchronises the stream; QPE_ERR_NUMERIC / QPE_ERR_TIMEOUT as qpe_probs).
  */
 qpe_status qpe_shard_readout(qpe_plan_t plan, qpe_shard_readout_t* out);
+
+/*
+ * qpe_shard_buffers: device pointers of a sharded plain plan's all-to-all
+ * buffers in its workspace and the bytes exchanged with each rank: send holds
+ * world chunks of *bytes_per_peer bytes (chunk s for rank s), recv receives
+ * world chunks (chunk r from rank r). After qpe_run the send buffer is ready
+ * on the bound stream; the receive buffer must be filled before
+ * qpe_shard_finish is enqueued. Fused sharded plans exchange nothing: NULL
+ * pointers and 0 bytes.
+ */
+qpe_status qpe_shard_buffers(qpe_plan_t plan, void** send, void** recv, size_t* bytes_per_peer);
+
+/*
+ * qpe_shard_finish: after the exchange, enqueue the rest of a sharded plain
+ * run on the bound stream (the cross-rank DFT, this rank's histogram and
+ * readout partial); QPE_ERR_STATE unless qpe_run came first. For a fused
+ * sharded plan it only checks that qpe_run came first.
+ */
+qpe_status qpe_shard_finish(qpe_plan_t plan);
 
 /*
  * qpe_merge_shard_readouts: the readout of the whole histogram from the

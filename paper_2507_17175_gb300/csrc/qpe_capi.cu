@@ -79,6 +79,12 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   in.off_scalars = take(sizeof(qpe::Scalars));
   in.off_err = take(sizeof(int));
   if (is_tc(prec) && !in.fused) in.off_tcsplit = take(qpe::tc_split_bytes(prec, in.nmat, in.nmeas));
+  // sharded plain schedule: all-to-all buffers of the local transform
+  in.shard_plain = !in.fused && in.shard_log > 0;
+  if (in.shard_plain) {
+    in.off_send = take(in.state_bytes);
+    in.off_recv = take(in.state_bytes);
+  }
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
   if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
   // the fused top level on the tensor cores: FP16x2, d = 16 (a 16-point top
@@ -86,7 +92,7 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   in.tc_top = in.fused && !batched && prec == QPE_C64_FP16X2 && in.nmat == 4 && !in.keep_state &&
               !in.levels.empty() && in.levels[0].r == 4 && in.levels[0].logna - in.shard_log >= 7;
   if (in.tc_top) in.off_tctab = take(qpe::tc_top_table_bytes());
-  in.fft = qpe::make_fft_plan(in.nmeas, d, elem_size(prec));
+  in.fft = qpe::make_fft_plan(in.nmeas - (in.shard_plain ? in.shard_log : 0), d, elem_size(prec));
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a
     // plan's layout does not depend on its schedule flags)
@@ -189,6 +195,35 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
     if (check_u && first == QPE_STAGE_POWERS) {
       if (qpe::launch_check_unitary(in, p->ws, p->stream) < 0) return cuda_fail(p, cudaGetLastError(), "unitarity check");
       ++n;
+    }
+    if (in.shard_plain) {
+      // this rank's part of a run up to the exchange: powers, the controlled
+      // gates of its rows, its local QFT^-1 passes, the sorted send buffer
+      if (first != QPE_STAGE_POWERS || last != QPE_STAGE_REDUCE)
+        return fail(p, QPE_ERR_UNSUPPORTED, "sharded plans of the plain schedule run whole (qpe_run)");
+      const int prec_arg = p->prec;
+      int r = qpe::launch_powers(in, p->ws, c64, p->stream);
+      if (r >= 0) {
+        n += r;
+        r = c64 ? qpe::launch_sweep<float2>(in, p->ws, false, p->stream, prec_arg)
+                : qpe::launch_sweep<double2>(in, p->ws, false, p->stream, prec_arg);
+      }
+      if (r >= 0) {
+        n += r;
+        r = c64 ? qpe::launch_fft<float2>(in, p->ws, p->stream) : qpe::launch_fft<double2>(in, p->ws, p->stream);
+      }
+      if (r >= 0) {
+        n += r;
+        r = c64 ? qpe::launch_shard_pack<float2>(in, p->ws, p->stream)
+                : qpe::launch_shard_pack<double2>(in, p->ws, p->stream);
+      }
+      if (r < 0) return cuda_fail(p, cudaGetLastError(), "kernel launch");
+      n += r;
+      in.powers_done = true;
+      in.state_stage = qpe::kStageExchange;
+      in.state_natural = false;
+      in.state_valid = false;
+      continue;
     }
     if (in.fused && first <= QPE_STAGE_SWEEP && last == QPE_STAGE_REDUCE) {
       // fused schedule: POWERS, then the levels (gates + QFT^-1 + histogram)
@@ -705,13 +740,19 @@ qpe_status qpe_plan_shard(const qpe_plan_desc* desc, int32_t rank, int32_t world
   if (st != QPE_OK) return st;
   int sh = 0;
   while ((1 << sh) < world) ++sh;
-  // the sharded form partitions the fused schedule's outcomes; the top level
-  // must have at least `world` pencils
-  if (desc->nmat > QPE_MAX_FUSED_NMAT || (desc->flags & (QPE_FLAG_PLAIN | QPE_FLAG_GATE_SWEEP | QPE_FLAG_REPEAT_U)) ||
-      (is_tc(desc->prec) && desc->nmat > 4))
-    return QPE_ERR_UNSUPPORTED;
-  const std::vector<qpe::Level> lv = qpe::make_levels(desc->nmeas, desc->nmat, elem_size(desc->prec), 0);
-  if (lv.empty() || lv[0].logna < sh) return QPE_ERR_UNSUPPORTED;
+  if (desc->flags & (QPE_FLAG_GATE_SWEEP | QPE_FLAG_REPEAT_U)) return QPE_ERR_UNSUPPORTED;
+  const bool plain = desc->nmat > QPE_MAX_FUSED_NMAT || (desc->flags & QPE_FLAG_PLAIN) ||
+                     (is_tc(desc->prec) && desc->nmat > 4);
+  if (plain) {
+    // rows m = rank (mod world), one exchange of N / world^2 rows per pair of
+    // ranks: needs N >= world^2; the final state stays distributed
+    if (desc->nmeas < 2 * sh || (desc->flags & QPE_FLAG_KEEP_STATE)) return QPE_ERR_UNSUPPORTED;
+  } else {
+    // the fused form partitions the outcomes; the top level must have at
+    // least `world` pencils
+    const std::vector<qpe::Level> lv = qpe::make_levels(desc->nmeas, desc->nmat, elem_size(desc->prec), 0);
+    if (lv.empty() || lv[0].logna < sh) return QPE_ERR_UNSUPPORTED;
+  }
   qpe_plan_s* p = new (std::nothrow) qpe_plan_s();
   if (!p) return QPE_ERR_ARG;
   p->prec = desc->prec;
@@ -750,6 +791,36 @@ qpe_status qpe_shard_readout(qpe_plan_t p, qpe_shard_readout_t* out) {
   out->nmeas = in.nmeas;
   out->rank = in.shard_rank;
   if (s.err) return fail(p, (qpe_status)s.err, "device flagged a non-finite histogram");
+  return QPE_OK;
+}
+
+qpe_status qpe_shard_buffers(qpe_plan_t p, void** send, void** recv, size_t* bytes_per_peer) {
+  if (!p || !send || !recv || !bytes_per_peer) return fail(p, QPE_ERR_ARG, "null pointer");
+  if (!p->bound) return fail(p, QPE_ERR_STATE, "qpe_bind first");
+  if (p->batched) return fail(p, QPE_ERR_UNSUPPORTED, "batched plans are not sharded");
+  const Instance& in = p->inst[0];
+  *send = in.shard_plain ? p->ws + in.off_send : nullptr;
+  *recv = in.shard_plain ? p->ws + in.off_recv : nullptr;
+  *bytes_per_peer = in.shard_plain ? in.state_bytes >> in.shard_log : 0;
+  return QPE_OK;
+}
+
+qpe_status qpe_shard_finish(qpe_plan_t p) {
+  if (!p) return QPE_ERR_ARG;
+  if (!p->bound) return fail(p, QPE_ERR_STATE, "qpe_bind first");
+  if (p->batched) return fail(p, QPE_ERR_UNSUPPORTED, "batched plans are not sharded");
+  Instance& in = p->inst[0];
+  if (!in.shard_plain) {
+    if (in.state_stage != QPE_STAGE_REDUCE) return fail(p, QPE_ERR_STATE, "qpe_run has not run");
+    return QPE_OK;  // the fused form needs no exchange
+  }
+  if (in.state_stage != qpe::kStageExchange) return fail(p, QPE_ERR_STATE, "qpe_run (and the exchange) first");
+  int blocks = 0;
+  const int r = is_c64(p->prec) ? qpe::launch_shard_combine<float2>(in, p->ws, p->stream, &blocks)
+                                : qpe::launch_shard_combine<double2>(in, p->ws, p->stream, &blocks);
+  if (r < 0 || qpe::launch_finalize(in, p->ws, blocks, p->stream) < 0)
+    return cuda_fail(p, cudaGetLastError(), "shard combine");
+  in.state_stage = QPE_STAGE_REDUCE;
   return QPE_OK;
 }
 
@@ -938,7 +1009,7 @@ qpe_status qpe_run(qpe_plan_t p) {
     // stage bookkeeping in step with it
     for (Instance& in : p->inst) {
       in.powers_done = true;
-      in.state_stage = QPE_STAGE_REDUCE;
+      in.state_stage = in.shard_plain ? qpe::kStageExchange : QPE_STAGE_REDUCE;
     }
   }
   cudaError_t e = cudaGraphLaunch(p->graph_exec, p->stream);
@@ -998,6 +1069,7 @@ qpe_status qpe_state(qpe_plan_t p, int32_t instance, void* out, int32_t ptr_is_d
   Instance* in;
   qpe_status st = get_instance(p, instance, &in);
   if (st != QPE_OK) return st;
+  if (in->shard_plain) return fail(p, QPE_ERR_UNSUPPORTED, "a sharded plain plan's final state stays distributed");
   if (in->state_stage == 0) return fail(p, QPE_ERR_STATE, "no state computed yet");
   if (!in->state_valid)
     return fail(p, QPE_ERR_STATE, "the fused schedule keeps the final state only with QPE_FLAG_KEEP_STATE");
@@ -1041,6 +1113,7 @@ qpe_status qpe_load_state(qpe_plan_t p, int32_t instance, const void* src, int32
   qpe_status st = get_instance(p, instance, &in);
   if (st != QPE_OK) return st;
   if (!in->has_state) return fail(p, QPE_ERR_STATE, "this fused plan has no state buffer; plan with QPE_FLAG_PLAIN");
+  if (in->shard_plain) return fail(p, QPE_ERR_UNSUPPORTED, "sharded plans run whole");
   cudaError_t e =
       cudaMemcpyAsync(p->ws + in->off_state, src, in->state_bytes, kind_to_device(ptr_is_device), p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "qpe_load_state copy");

@@ -186,6 +186,8 @@ struct Level {
 };
 
 constexpr int kMaxLevels = 32;
+// state_stage of a sharded plain plan between qpe_run and qpe_shard_finish
+constexpr int kStageExchange = 5;
 struct TableJobs {
   int count;
   int off[kMaxLevels];
@@ -256,6 +258,8 @@ struct Instance {
   // y = shard_rank mod 2^shard_log; its histogram (and kept state) hold them
   // compactly, y at local index y >> shard_log
   int shard_log = 0, shard_rank = 0;
+  bool shard_plain = false;           // sharded plain schedule: one exchange per run
+  size_t off_send = 0, off_recv = 0;  // its all-to-all buffers, [2^shard_log][N / 4^shard_log][d] each
   // top level of the fused schedule on the tensor cores (QPE_C64_FP16X2, d = 16)
   bool tc_top = false;
   size_t off_tctab = 0;  // its fp16 table operands (both orders)
@@ -372,7 +376,8 @@ int launch_powers(const Instance& in, char* ws, bool want_c64, cudaStream_t s);
 // U^dagger U = I to 1e-8 per entry, else the instance's error word = QPE_ERR_NUMERIC
 int launch_check_unitary(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, int prec = 1);
-int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s);
+// doubling level j on the tensor cores with the power P_(j + pow_off)
+int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s, int pow_off = 0);
 // a bounded wait that runs out after `polls` polls (records QPE_ERR_TIMEOUT)
 int launch_wait_expiry(const Instance& in, char* ws, uint32_t polls, cudaStream_t s);
 size_t oz_square_bytes(int nmat);
@@ -381,6 +386,11 @@ size_t tc_split_bytes(int prec, int nmat, int nmeas);
 cudaError_t configure_tc_kernels();
 template <typename C> int launch_fft(const Instance& in, char* ws, cudaStream_t s);
 template <typename C> int launch_reduce(const Instance& in, char* ws, cudaStream_t s);
+// sharded plain schedule: twiddle and sort the local transform by owner rank
+// into the send buffer; after the caller's all-to-all, the cross-rank DFT,
+// histogram and readout partials of this rank's outcomes
+template <typename C> int launch_shard_pack(const Instance& in, char* ws, cudaStream_t s);
+template <typename C> int launch_shard_combine(const Instance& in, char* ws, cudaStream_t s, int* blocks);
 template <typename C> int launch_unpermute(const Instance& in, const char* ws, void* out, cudaStream_t s);
 
 template <typename C>

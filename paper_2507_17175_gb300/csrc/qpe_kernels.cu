@@ -289,10 +289,11 @@ struct FftArgs {
   int logw;    // W = 2^logw columns per CTA
   int logq;    // Q = 2^logq
   int logd;
-  int n;       // log2 N
+  int n;       // log2 of the transform length
   int htw;
   int logb;    // B = 2^logb blocks
   int last;    // 1: no inter-pass twiddle
+  int tw_sh;   // log2(N / transform length): a shard's local transform reads the N-point tables
   double scale;
 };
 
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const 
   }
   cp_async_commit();
   for (int e = threadIdx.x; e < (R >> 1); e += blockDim.x)
-    twp[e] = twiddle(tw_lo, tw_hi, a.htw, (int64_t)e << (a.n - a.logr));
+    twp[e] = twiddle(tw_lo, tw_hi, a.htw, (int64_t)e << (a.n + a.tw_sh - a.logr));
   cp_async_wait<0>();
   __syncthreads();
   // Radix-2 DIF stages s = 0 .. logr - 1 (stage s pairs rows p and p + h,
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const 
     if (!a.last) {
       const int64_t q = (qs << a.logw) + w;
       const int64_t b = q >> a.logd;
-      const int64_t e = ((b * ya) & rl_mask) << a.logb;  // omega_(RL)^(b ya) = omega_N^(b ya B)
+      const int64_t e = ((b * ya) & rl_mask) << (a.logb + a.tw_sh);  // omega_(RL)^(b ya) = omega_N^(b ya B)
       if (e) v = cmul(v, twiddle(tw_lo, tw_hi, a.htw, e));
     }
     if (a.scale != 1.0) v = cscale(v, (R_t)a.scale);
@@ -607,6 +608,94 @@ Digits digits_of(const FftPlan& f) {
 
 }  // namespace
 
+// ------------------------------------------------------ sharded plain schedule
+// Rank r of G = 2^sh holds the rows m = r + G i (i < N / G). Its local state
+// after the controlled gates is row i = 2^(-n/2) U^(r + G i) psi; the local
+// QFT^-1 passes give F_r[y'] = 2^(-n/2) sum_i w_(N/G)^(i y') S[r + G i] for
+// y' < N / G (positions in digit order), and
+//   X[y' + (N / G) q] = sum_r w_G^(r q) (w_N^(r y') F_r[y']),
+// one length-G DFT across the ranks per (y', column). The pack kernel forms
+// w_N^(r y') F_r[y'] and sorts it by the rank that owns y' (y' = s mod G):
+// send[s][y' >> sh][t]. After the all-to-all, rank s holds recv[r][i][t] =
+// w_N^(r y') F_r[y'] for y' = s + G i, and the combine kernel runs the G-point
+// DFTs, the |.|^2 sums over t and the readout of its outcomes
+// y = s + G (i + (N / G^2) q).
+template <typename C>
+__global__ void __launch_bounds__(256) shard_pack_kernel(const C* __restrict__ F, C* __restrict__ send, int64_t nloc,
+                                                         int logd, int nloc_bits, int sh, int rank, Digits g,
+                                                         const C* __restrict__ tw_lo, const C* __restrict__ tw_hi,
+                                                         int htw, int n) {
+  pdl_begin();
+  const int64_t total = nloc << logd;
+  const int64_t per_peer = nloc >> sh;
+  const int64_t dmask = (int64_t(1) << logd) - 1;
+  const int64_t nmask = (int64_t(1) << n) - 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e >> logd, t = e & dmask;
+    const int64_t yp = pos_to_y(g, nloc_bits, p);
+    C v = F[e];
+    const int64_t ex = ((int64_t)rank * yp) & nmask;
+    if (ex) v = cmul(v, twiddle(tw_lo, tw_hi, htw, ex));
+    const int64_t dest = yp & ((int64_t(1) << sh) - 1);
+    send[((dest * per_peer + (yp >> sh)) << logd) + t] = v;
+  }
+  pdl_trigger();
+}
+
+// One warp per local row i of this rank's outcomes; G-point DFT over the
+// source ranks for every column, |.|^2 summed over the columns.
+template <typename C>
+__global__ void __launch_bounds__(256) shard_combine_kernel(const C* __restrict__ recv, double* __restrict__ hist,
+                                                            Partial* __restrict__ parts, int64_t per_peer, int logd,
+                                                            int sh, int rank, int n, const C* __restrict__ tw_lo,
+                                                            const C* __restrict__ tw_hi, int htw) {
+  pdl_begin();
+  const int d = 1 << logd, G = 1 << sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double best = -1.0, wsum = 0.0, psum = 0.0;
+  int64_t by = INT64_MAX;
+  const int64_t warps = (int64_t)gridDim.x * 8;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < per_peer; i += warps) {
+    for (int q = 0; q < G; ++q) {
+      double acc = 0.0;
+      for (int t = lane; t < d; t += 32) {
+        C x = mk((typename real_of<C>::type)0, (typename real_of<C>::type)0);
+        for (int r = 0; r < G; ++r) {
+          const C v = recv[(((int64_t)r * per_peer + i) << logd) + t];
+          const int64_t ex = (int64_t)((r * q) & (G - 1)) << (n - sh);  // w_G^(r q) = w_N^(r q N / G)
+          x = cadd(x, ex ? cmul(v, twiddle(tw_lo, tw_hi, htw, ex)) : v);
+        }
+        acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+      }
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) {
+        const int64_t j = i + per_peer * q;
+        const int64_t y = rank + ((int64_t)j << sh);
+        hist[j] = acc;
+        better(best, by, acc, y);
+        wsum += acc * (double)y;
+        psum += acc;
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int64_t oy = __shfl_xor_sync(0xffffffffu, by, off);
+    better(best, by, ob, oy);
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+    psum += __shfl_xor_sync(0xffffffffu, psum, off);
+  }
+  __shared__ Partial sp[8];
+  if (lane == 0) sp[warp] = Partial{best, by, wsum, psum};
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial r = sp[0];
+    for (int w = 1; w < 8; ++w) merge_partial(r, sp[w]);
+    parts[blockIdx.x] = r;
+  }
+  pdl_trigger();
+}
+
 // ============================================================ launchers
 int launch_twiddles(const Instance& in, char* ws, cudaStream_t s) {
   const int64_t total = (int64_t(1) << in.htw) + (int64_t(1) << (in.nmeas - in.htw));
@@ -703,6 +792,32 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, i
                (const double2*)at<double2>(ws, in.off_psi), init_rows, logd, scale) != cudaSuccess)
     return -1;
   ++launches;
+  if (in.shard_log > 0) {
+    // rank r: rows 0 .. G-1 = U^m psi (m < G) by the doubling of the low sh
+    // measurement qubits, row r moved to row 0, then the doubling of the high
+    // n - sh qubits over the local rows (local row i = U^(r + G i) psi)
+    const int sh = in.shard_log;
+    for (int j = 0; j < sh; ++j) {
+      const int r = launch_rows_times_pt<C>(S, P + j * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j}, s);
+      if (r < 0) return -1;
+      launches += r;
+    }
+    if (in.shard_rank != 0 &&
+        cudaMemcpyAsync(S, S + ((int64_t)in.shard_rank << logd), sizeof(C) << logd, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+      return -1;
+    for (int j = 0; j < in.nmeas - sh; ++j) {
+      int r;
+      if (tc && (int64_t(1) << j) >= 128)
+        r = launch_tc_level(in, ws, prec, j, s, sh);
+      else
+        r = launch_rows_times_pt<C>(S, P + (j + sh) * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j},
+                                    s);
+      if (r < 0) return -1;
+      launches += r;
+    }
+    return launches;
+  }
   const bool repeat_u = prec < 0;  // controlled-U applied 2^j times (gate schedule only)
   for (int j = 0; j < in.nmeas; ++j) {
     int r = 0;
@@ -775,7 +890,8 @@ int launch_fft(const Instance& in, char* ws, cudaStream_t s) {
     a.logw = ilog2(p.W);
     a.logq = ilog2(p.Q);
     a.logd = in.nmat;
-    a.n = in.nmeas;
+    a.n = in.nmeas - in.shard_log;  // a sharded plan transforms its N / 2^shard_log local rows
+    a.tw_sh = in.shard_log;
     a.htw = in.htw;
     a.logb = ilog2(p.B);
     a.last = (i == in.fft.passes - 1);
@@ -787,6 +903,34 @@ int launch_fft(const Instance& in, char* ws, cudaStream_t s) {
     ++launches;
   }
   return launches;
+}
+
+template <typename C>
+int launch_shard_pack(const Instance& in, char* ws, cudaStream_t s) {
+  const int nb = in.nmeas - in.shard_log;
+  const int64_t nloc = int64_t(1) << nb;
+  const C* lo = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_lo64) : at<C>(ws, in.off_tw_lo32);
+  const C* hi = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_hi64) : at<C>(ws, in.off_tw_hi32);
+  return launch_k(shard_pack_kernel<C>, dim3(grid_for(nloc << in.nmat, 256)), dim3(256), 0, s,
+                  (const C*)at<C>(ws, in.off_state), at<C>(ws, in.off_send), nloc, in.nmat, nb, in.shard_log,
+                  in.shard_rank, digits_of(in.fft), lo, hi, in.htw, in.nmeas) == cudaSuccess
+             ? 1
+             : -1;
+}
+
+template <typename C>
+int launch_shard_combine(const Instance& in, char* ws, cudaStream_t s, int* blocks_out) {
+  const int64_t per_peer = int64_t(1) << (in.nmeas - 2 * in.shard_log);
+  const C* lo = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_lo64) : at<C>(ws, in.off_tw_lo32);
+  const C* hi = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_hi64) : at<C>(ws, in.off_tw_hi32);
+  int blocks = (int)std::min<int64_t>(kReduceBlocks, (per_peer + 7) / 8);
+  if (blocks < 1) blocks = 1;
+  *blocks_out = blocks;
+  return launch_k(shard_combine_kernel<C>, dim3(blocks), dim3(256), 0, s, (const C*)at<C>(ws, in.off_recv),
+                  at<double>(ws, in.off_hist), at<Partial>(ws, in.off_partials), per_peer, in.nmat, in.shard_log,
+                  in.shard_rank, in.nmeas, lo, hi, in.htw) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 template <typename C>
@@ -836,6 +980,10 @@ template int launch_sweep<double2>(const Instance&, char*, bool, cudaStream_t, i
 template int launch_fft<float2>(const Instance&, char*, cudaStream_t);
 template int launch_fft<double2>(const Instance&, char*, cudaStream_t);
 template int launch_reduce<float2>(const Instance&, char*, cudaStream_t);
+template int launch_shard_pack<float2>(const Instance&, char*, cudaStream_t);
+template int launch_shard_pack<double2>(const Instance&, char*, cudaStream_t);
+template int launch_shard_combine<float2>(const Instance&, char*, cudaStream_t, int*);
+template int launch_shard_combine<double2>(const Instance&, char*, cudaStream_t, int*);
 template int launch_reduce<double2>(const Instance&, char*, cudaStream_t);
 template int launch_unpermute<float2>(const Instance&, const char*, void*, cudaStream_t);
 template int launch_unpermute<double2>(const Instance&, const char*, void*, cudaStream_t);

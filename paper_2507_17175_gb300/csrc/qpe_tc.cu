@@ -808,7 +808,7 @@ size_t tc_split_bytes(int prec, int nmat, int nmeas) {
 
 // One doubling level j on the tensor cores: rows [half, 2 half) = rows
 // [0, half) x P_j^T. Returns launches, or -1 (launch error / tensor map).
-int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s) {
+int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s, int pow_off) {
   const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : kTcFP16;
   const size_t esz = kind == kTcTF32 ? 4 : 2;
   const int64_t half = int64_t(1) << j;
@@ -819,7 +819,7 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
   char* Blo = Bhi + (size_t)d2 * d2 * esz;
   float* inv_scale = reinterpret_cast<float*>(Blo + (size_t)d2 * d2 * esz);  // FP16x2 only
   float* S = reinterpret_cast<float*>(ws + in.off_state);
-  const double2* Pj = reinterpret_cast<const double2*>(ws + in.off_pow64) + (int64_t)j * in.d * in.d;
+  const double2* Pj = reinterpret_cast<const double2*>(ws + in.off_pow64) + (int64_t)(j + pow_off) * in.d * in.d;
   int launches = 0;
   cudaError_t e;
   const int64_t cnt = half * d2;

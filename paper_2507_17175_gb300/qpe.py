@@ -80,6 +80,8 @@ _sig = {
                                       ctypes.POINTER(_vp)]),
     "qpe_shard_readout": (ctypes.c_int, [_vp, ctypes.POINTER(ShardReadout)]),
     "qpe_merge_shard_readouts": (ctypes.c_int, [ctypes.POINTER(ShardReadout), _i32, ctypes.POINTER(Readout)]),
+    "qpe_shard_buffers": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)]),
+    "qpe_shard_finish": (ctypes.c_int, [_vp]),
     "qpe_bind": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "qpe_load": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _i32]),
     "qpe_run": (ctypes.c_int, [_vp]),
@@ -409,6 +411,44 @@ class ShardedPlan(Plan):
         if out is None:
             out = np.empty((self.N // self.world, self.d), dtype=self.state_dtype)
         return super().state(out, instance)
+
+    def buffers(self):
+        """(send, recv) uint8 views of the all-to-all buffers inside the
+        workspace (world chunks of equal size each), or (None, None) when the
+        plan exchanges nothing (fused form)."""
+        sp, rp, nb = _vp(), _vp(), ctypes.c_size_t(0)
+        self._check(_lib.qpe_shard_buffers(self._h, ctypes.byref(sp), ctypes.byref(rp), ctypes.byref(nb)),
+                    "qpe_shard_buffers")
+        if nb.value == 0:
+            return None, None
+        base = self.workspace.data_ptr()
+        n = nb.value * self.world
+        so, ro = sp.value - base, rp.value - base
+        return self.workspace[so:so + n], self.workspace[ro:ro + n]
+
+    def finish(self):
+        self._check(_lib.qpe_shard_finish(self._h), "qpe_shard_finish")
+
+    def run_exchange(self, dist, group=None):
+        """One whole sharded run with its exchange over a torch.distributed
+        group: qpe_run, an all-to-all of the send buffer (NCCL on device
+        buffers; other backends through host copies), qpe_shard_finish."""
+        import torch
+        self.run()
+        send, recv = self.buffers()
+        if send is not None:
+            if dist.get_backend(group) == "nccl":
+                torch.cuda.current_stream(self.device).wait_stream(self.stream)
+                dist.all_to_all_single(recv, send, group=group)
+                self.stream.wait_stream(torch.cuda.current_stream(self.device))
+            else:
+                self.stream.synchronize()
+                hs = send.cpu()
+                hr = torch.empty_like(hs)
+                dist.all_to_all_single(hr, hs, group=group)
+                with torch.cuda.stream(self.stream):
+                    recv.copy_(hr, non_blocking=False)
+        self.finish()
 
     def shard_readout(self) -> ShardReadout:
         r = ShardReadout()

@@ -152,9 +152,13 @@ def test_bf16x3_is_refused_everywhere(q):
     (4, 12, 0, 0, 0, 3, "ERR_ARG"),        # world not a power of two
     (4, 12, 0, 0, 2, 2, "ERR_ARG"),        # rank out of range
     (4, 12, 0, 0, -1, 2, "ERR_ARG"),
-    (7, 12, 1, 0, 0, 2, "ERR_UNSUPPORTED"),  # plain schedule
-    (4, 12, 1, 0x8, 0, 2, "ERR_UNSUPPORTED"),
-    (5, 12, 2, 0, 0, 2, "ERR_UNSUPPORTED"),  # tensor-core precision
+    (7, 12, 1, 0, 0, 2, "OK"),               # plain schedule, one exchange
+    (4, 12, 1, 0x8, 0, 2, "OK"),
+    (5, 12, 3, 0, 1, 2, "OK"),               # FP16x2 gate GEMMs on the tensor cores
+    (7, 3, 1, 0, 0, 4, "ERR_UNSUPPORTED"),   # plain form needs N >= world^2
+    (7, 12, 1, 0x10, 0, 2, "ERR_UNSUPPORTED"),  # the final state stays distributed
+    (7, 12, 1, 0x1, 0, 2, "ERR_UNSUPPORTED"),   # not gate by gate
+    (5, 12, 2, 0, 0, 2, "ERR_UNSUPPORTED"),  # BF16x3 is refused
     (4, 3, 0, 0, 0, 2, "ERR_UNSUPPORTED"),   # top level with fewer pencils than ranks
     (4, 12, 0, 0, 1, 2, "OK"),
     (2, 20, 1, 0x10, 7, 8, "OK"),
