@@ -133,10 +133,15 @@ struct LvShape {
   static constexpr int G = MODE == 0 ? c.G0 : c.G;
   static constexpr int LMAX = 1 << c.logl;
   static constexpr bool TAB_SMEM = MODE == 0 ? true : c.tab_smem;
+  // FP64 with the table in shared memory: complex products with three real
+  // multiplications (Gauss), the table's Re + Im kept beside it (d >= 8: the
+  // short-DFT shapes have the registers for the third accumulator)
+  static constexpr bool THREE_M = DBL && TAB_SMEM && LOGD >= 3;
   static constexpr size_t smem(size_t esize) {
     const size_t acc = esize == 8 ? 4 : 8;
     size_t b = (size_t)G * LMAX * DI * esize + (size_t)G * D * esize + 2 * (size_t)G * LMAX * esize;
     if (TAB_SMEM) b += (size_t)D * LMAX * DI * esize;
+    if (THREE_M) b += (size_t)D * LMAX * DI * (esize / 2);
     if (MODE != 0) b += (size_t)LMAX * D * (G + 1) * acc;
     return b;
   }
@@ -270,7 +275,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   C* twLo = ZsT + G * D;                  // [G][L] low factor of w^(m_b y_a)
   C* twHi = twLo + G * LMAX;              // [G][L] high factor
   C* tabS = twHi + G * LMAX;              // [D][L DI] (TAB_SMEM)
-  A_t* sq = reinterpret_cast<A_t*>(tabS + (S::TAB_SMEM ? D * LMAX * DI : 0));  // [L][D][G+1] (MODE != 0)
+  R_t* tabSum = reinterpret_cast<R_t*>(tabS + (S::TAB_SMEM ? D * LMAX * DI : 0));  // [D][L DI] Re + Im (THREE_M)
+  A_t* sq = reinterpret_cast<A_t*>(tabSum + (S::THREE_M ? D * LMAX * DI : 0));      // [L][D][G+1] (MODE != 0)
   const C* tab = S::TAB_SMEM ? tabS : a.tab;
   const int tab_ld = S::TAB_SMEM ? ROWS : L * D;  // row stride (per k) of the table in use
   const int tid = threadIdx.x;
@@ -354,6 +360,12 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
     const int gvalid = (int)(Na - ya0 < G ? Na - ya0 : G);
     cp_async_wait<0>();
     __syncthreads();  // this group's copies (and the table slice) landed; the previous iteration is consumed
+    if constexpr (S::THREE_M) {
+      if (it == it_begin) {  // Re + Im of the table slice, once per share
+        for (int e = tid; e < D * ROWS; e += blockDim.x) tabSum[e] = tabS[e].x + tabS[e].y;
+        __syncthreads();
+      }
+    }
     // T[g][m_b][ii] = w^(m_b y_a) sum_k M[m_b][i_base + ii][k] Z[g][k]
     {
       const int nrg = ROWS / TR;
@@ -370,6 +382,45 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
         for (int t = 0; t < TR; ++t)
 #pragma unroll
           for (int g = 0; g < TG; ++g) acc[t][g] = czero<C>();
+        if constexpr (S::THREE_M) {
+          // (a_r + i a_i)(z_r + i z_i) = (a_r z_r - a_i z_i) + i ((a_r + a_i)(z_r + z_i) - a_r z_r - a_i z_i):
+          // three FMA chains per output instead of four
+          R_t p1[TR][TG], p2[TR][TG], p3[TR][TG];
+#pragma unroll
+          for (int t = 0; t < TR; ++t)
+#pragma unroll
+            for (int g = 0; g < TG; ++g) p1[t][g] = p2[t][g] = p3[t][g] = (R_t)0;
+#pragma unroll 4
+          for (int k = 0; k < D; ++k) {
+            const C* tp = tab + k * tab_ld + trow;
+            const R_t* sp3 = tabSum + k * tab_ld + trow;
+            const C* zp = ZsT + k * G + gg * TG;
+            C av[TR], zv[TG];
+            R_t as[TR], zs[TG];
+#pragma unroll
+            for (int t = 0; t < TR; ++t) {
+              av[t] = tp[t];
+              as[t] = sp3[t];
+            }
+#pragma unroll
+            for (int g = 0; g < TG; ++g) {
+              zv[g] = zp[g];
+              zs[g] = zv[g].x + zv[g].y;
+            }
+#pragma unroll
+            for (int t = 0; t < TR; ++t)
+#pragma unroll
+              for (int g = 0; g < TG; ++g) {
+                p1[t][g] = fma(av[t].x, zv[g].x, p1[t][g]);
+                p2[t][g] = fma(av[t].y, zv[g].y, p2[t][g]);
+                p3[t][g] = fma(as[t], zs[g], p3[t][g]);
+              }
+          }
+#pragma unroll
+          for (int t = 0; t < TR; ++t)
+#pragma unroll
+            for (int g = 0; g < TG; ++g) acc[t][g] = mk(p1[t][g] - p2[t][g], p3[t][g] - p1[t][g] - p2[t][g]);
+        } else {
 #pragma unroll 4
         for (int k = 0; k < D; ++k) {
           C av[TR], zv[TG];
@@ -402,6 +453,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
           for (int t = 0; t < TR; ++t)
 #pragma unroll
             for (int g = 0; g < TG; ++g) cfma(acc[t][g], av[t], zv[g]);
+        }
         }
 #pragma unroll
         for (int g = 0; g < TG; ++g) {
@@ -530,8 +582,16 @@ __device__ __forceinline__ void level_body(const LevelArgs<C>& a, int cg, int64_
   }
 }
 
+// CTAs per SM the register allocation aims for: two for complex64 and for the
+// FP64 d = 16 levels (whose shared memory also admits two), one for the other
+// FP64 shapes (their register tiles and DFTs need more than 128 registers)
+template <typename C, int LOGD>
+__host__ __device__ constexpr int level_min_blocks() {
+  return (sizeof(C) == 8 || LOGD == 4) ? 2 : 1;
+}
+
 template <typename C, int LOGD, int MODE>
-__global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(LevelArgs<C> a) {
+__global__ void __launch_bounds__(256, level_min_blocks<C, LOGD>()) level2_kernel(LevelArgs<C> a) {
   pdl_begin();
   using S = LvShape<LOGD, sizeof(C) == 16, MODE>;
   constexpr int NCG = S::D / S::DI;
@@ -544,7 +604,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1) level2_kernel(Lev
 // Grouped form: one launch runs many (instance, level) shares listed in
 // items[]; each CTA walks the list with a grid stride.
 template <typename C, int LOGD, int MODE>
-__global__ void __launch_bounds__(256, sizeof(C) == 8 ? 2 : 1)
+__global__ void __launch_bounds__(256, level_min_blocks<C, LOGD>())
     level2_grouped_kernel(const LevelArgs<C>* __restrict__ args, const GroupItem* __restrict__ items, int nitems) {
   pdl_begin();
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
@@ -673,15 +733,17 @@ __global__ void seed_psi_kernel(const double2* __restrict__ psi, C* __restrict__
 //
 // Roles (416 threads, one CTA per SM, persistent over tiles):
 //   warps 0..3   load the tile's Z rows (one row per thread), split and store
-//                them into one of two A stages
+//                them into one of two A stages, and store the row's 16
+//                twiddles w_N^(m_b y_a) times the row's inverse scale
 //   warp 4       allocates tensor memory; lane 0 issues the MMAs: columns
 //                [0, 256) (i < 8) into tensor-memory half 0, [256, 512) into
 //                half 1, so the MMAs of one half overlap the drain of the other
 //   warps 5..12  drain: thread (set s, lane group q, lane) owns pencil
 //                y_a = 32 q + lane of the tile and the columns i of set s
 //                (4 per half); for each i it loads the 16 values T[m_b]
-//                (32 floats, one tcgen05.ld), multiplies by w_N^(m_b y_a),
-//                runs the length-16 DFT over m_b in registers and adds |X|^2
+//                (32 floats, one tcgen05.ld, issued while the previous column's
+//                DFT runs), multiplies by the stored twiddles, runs the
+//                length-16 DFT over m_b in registers and adds |X|^2
 //                into 16 bin sums; set 1 hands its sums to set 0 through
 //                shared memory, set 0 writes the histogram and the readout.
 // Every wait is an mbarrier wait with a poll limit; on expiry the CTA records
@@ -691,10 +753,11 @@ constexpr int kTcRows = 128;          // pencils per tile (MMA M)
 constexpr int kTcN = 2 * kTcD * kTcL; // 512 GEMM columns
 constexpr int kTcThreads = 416;
 constexpr int kTcSqStride = 17;       // padded row of the hand-over buffer
+constexpr int kTcTwStride = 18;       // padded twiddle row (complex; 16-byte aligned, no bank conflicts)
 constexpr size_t kTcBBytes = (size_t)kTcN * 128;  // one B order, 64 KiB
 constexpr size_t kTcABytes = (size_t)kTcRows * 128;
-constexpr size_t kTcSmem = 2 * kTcBBytes + 2 * kTcABytes + 2 * (size_t)kTcRows * kTcSqStride * 4 +
-                           2 * (size_t)kTcRows * 4 + 1024;
+constexpr size_t kTcSmem = 2 * kTcBBytes + 2 * kTcABytes + 2 * (size_t)kTcRows * kTcTwStride * 8 +
+                           2 * (size_t)kTcRows * kTcSqStride * 4 + 1024;
 
 struct TcTopArgs {
   const float2* seeds;       // Z of the level below (compact when the level below is sharded)
@@ -738,8 +801,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   unsigned char* Bs = base;                            // B1 then B2, 64 KiB each
   unsigned char* As = base + 2 * kTcBBytes;            // two A stages, 16 KiB each
-  float* sq = reinterpret_cast<float*>(As + 2 * kTcABytes);   // [2][128][17]
-  float* inv = sq + 2 * kTcRows * kTcSqStride;                // [2][128]
+  float2* twS = reinterpret_cast<float2*>(As + 2 * kTcABytes);  // [2][128][18]: scaled twiddles per row
+  float* sq = reinterpret_cast<float*>(twS + 2 * kTcRows * kTcTwStride);  // [2][128][17]
   __shared__ uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2], sq_full[2], sq_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
@@ -779,6 +842,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
   const uint32_t tmem = tmem_slot;
   const int lna = a.logna - a.sh;
   volatile int* vfail = &fail;
+  const int64_t tw_mask = (int64_t(1) << a.htw) - 1;
+  const int lvl_shift = a.nmeas - a.logna - 4;
+  const int64_t lvl_mask = (int64_t(1) << (a.logna + 4)) - 1;
 
   if (warp < 4) {
     // ---------------------------------------------------------- producer
@@ -809,7 +875,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
       const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
       const int e = (ex < -100 || ex > 100) ? 0 : 14 - ex;
       const float sc = __uint_as_float((uint32_t)(127 + e) << 23);
-      inv[b * kTcRows + p] = __uint_as_float((uint32_t)(127 - e - 14) << 23);
+      const float invr = __uint_as_float((uint32_t)(127 - e - 14) << 23);  // undoes both operand scales
+      {
+        const int64_t ya = a.rk + (j << a.sh);
+        float2* tw = twS + (b * kTcRows + p) * kTcTwStride;
+#pragma unroll
+        for (int mb = 0; mb < kTcL; mb += 2) {
+          float2 w[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int64_t ex = (((int64_t)(mb + u) * ya) & lvl_mask) << lvl_shift;
+            w[u] = cscale(cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw))), invr);
+          }
+          *reinterpret_cast<float4*>(tw + mb) = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
+        }
+      }
       unsigned char* row = As + b * kTcABytes;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -870,25 +950,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
     const int dw = warp - 5;
     const int set = dw >> 2, lg = warp & 3;
     const int row = lg * 32 + lane;
-    const int64_t tw_mask = (int64_t(1) << a.htw) - 1;
-    const int lvl_shift = a.nmeas - a.logna - 4;
-    const int64_t lvl_mask = (int64_t(1) << (a.logna + 4)) - 1;
     HistAcc32 h32;
     int it = 0;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
       const int b = it & 1;
       const int64_t j = t * kTcRows + row;
-      const int64_t ya = a.rk + (j << a.sh);
       float2 tw[kTcL];
-#pragma unroll
-      for (int mb = 0; mb < kTcL; ++mb) {
-        const int64_t ex = (((int64_t)mb * ya) & lvl_mask) << lvl_shift;
-        tw[mb] = cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
-      }
       float acc[kTcL];
 #pragma unroll
       for (int yb = 0; yb < kTcL; ++yb) acc[yb] = 0.f;
-      float invr = 0.f;
       bool ok = true;
       for (int h = 0; h < 2 && ok; ++h) {
         bool got = mbar_wait(&t_full[h], it & 1);
@@ -899,23 +969,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
           break;
         }
         if (h == 0) {
-          invr = inv[b * kTcRows + row];
+          const float4* tr = reinterpret_cast<const float4*>(twS + (b * kTcRows + row) * kTcTwStride);
+#pragma unroll
+          for (int mb = 0; mb < kTcL; mb += 2) {
+            const float4 w = tr[mb >> 1];
+            tw[mb] = make_float2(w.x, w.y);
+            tw[mb + 1] = make_float2(w.z, w.w);
+          }
           __syncwarp();
-          if (lane == 0) mbar_arrive(&a_empty[b]);  // this warp is done with the stage's scales
+          if (lane == 0) mbar_arrive(&a_empty[b]);  // this warp is done with the stage's twiddles
         }
+        const uint32_t col0 = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * 256 + set * 4 * 32);
+        uint32_t v[32];
+        tmem_ld32_async(col0, v);
+        tmem_wait32(v);
 #pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-          const int il = set * 4 + q;  // column i = 8 h + il
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * 256 + il * 32), v);
+        for (int q = 0; q < 4; ++q) {  // column i = 8 h + 4 set + q
           float2 x[kTcL];
 #pragma unroll
           for (int mb = 0; mb < kTcL; ++mb)
-            x[mb] = cmul(make_float2(__uint_as_float(v[2 * mb]) * invr, __uint_as_float(v[2 * mb + 1]) * invr),
-                         tw[mb]);
+            x[mb] = cmul(make_float2(__uint_as_float(v[2 * mb]), __uint_as_float(v[2 * mb + 1])), tw[mb]);
+          if (q < 3) tmem_ld32_async(col0 + (uint32_t)((q + 1) * 32), v);  // next column while this DFT runs
           dft_k<float2, 4, kTcL>(x);
 #pragma unroll
           for (int yb = 0; yb < kTcL; ++yb) acc[yb] = fmaf(x[yb].x, x[yb].x, fmaf(x[yb].y, x[yb].y, acc[yb]));
+          if (q < 3) tmem_wait32(v);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
