@@ -79,10 +79,10 @@ typedef enum {
                       /* histogram) on the tensor cores when it has >= 128      */
                       /* pencils; otherwise (nmat <= 3, or too few pencils) the  */
                       /* fused complex64 schedule on the CUDA cores              */
-  QPE_C64_TF32X3 = 4  /* as QPE_C64_FP16X2 with tf32 hi/lo splits (~21 bits)    */
-                      /* and three products A_hi B_hi + A_hi B_lo + A_lo B_hi;   */
-                      /* nmat <= 4 runs the fused complex64 schedule on the      */
-                      /* CUDA cores                                              */
+  QPE_C64_TF32X3 = 4  /* as QPE_C64_FP16X2 with tf32 hi/lo splits (~21 bits),   */
+                      /* no scaling, and three products A_hi B_hi + A_hi B_lo +  */
+                      /* A_lo B_hi (nmat = 4: the same fused tensor-core top     */
+                      /* level)                                                  */
 } qpe_precision;
 
 /* Plan flags. */
@@ -160,7 +160,7 @@ typedef enum {
   QPE_INFO_TOP_LEVEL_BITS = 8,  /* fused schedule: r of the top level, i.e.    */
                                 /* its DFT length is 2^r (0 otherwise)         */
   QPE_INFO_TC_TOP_LEVEL = 9     /* 1 when the fused top level runs on the      */
-                                /* tensor cores (QPE_C64_FP16X2, nmat = 4)      */
+                                /* tensor cores (split precision, nmat = 4)     */
 } qpe_info;
 
 /*

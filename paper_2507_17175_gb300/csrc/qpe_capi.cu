@@ -87,10 +87,11 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   }
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
   if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
-  // the fused top level on the tensor cores: FP16x2, d = 16 (a 16-point top
-  // level), at least one tile of 128 pencils per rank, histogram only
-  in.tc_top = in.fused && !batched && prec == QPE_C64_FP16X2 && in.nmat == 4 && !in.keep_state &&
-              !in.levels.empty() && in.levels[0].r == 4 && in.levels[0].logna - in.shard_log >= 7;
+  // the fused top level on the tensor cores: a split precision, d = 16 (a
+  // 16-point top level), at least one tile of 128 pencils per rank, histogram only
+  in.tc_top = in.fused && !batched && is_tc(prec) && in.nmat == 4 && !in.keep_state && !in.levels.empty() &&
+              in.levels[0].r == 4 && in.levels[0].logna - in.shard_log >= 7;
+  in.tc_top_prec = prec;
   if (in.tc_top) in.off_tctab = take(qpe::tc_top_table_bytes());
   in.fft = qpe::make_fft_plan(in.nmeas - (in.shard_plain ? in.shard_log : 0), d, elem_size(prec));
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {

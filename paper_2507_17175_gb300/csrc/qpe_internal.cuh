@@ -260,8 +260,9 @@ struct Instance {
   int shard_log = 0, shard_rank = 0;
   bool shard_plain = false;           // sharded plain schedule: one exchange per run
   size_t off_send = 0, off_recv = 0;  // its all-to-all buffers, [2^shard_log][N / 4^shard_log][d] each
-  // top level of the fused schedule on the tensor cores (QPE_C64_FP16X2, d = 16)
+  // top level of the fused schedule on the tensor cores (FP16x2 / TF32x3, d = 16)
   bool tc_top = false;
+  int tc_top_prec = 0;
   size_t off_tctab = 0;  // its fp16 table operands (both orders)
   int nsm = 0;           // multiprocessors of the bound device
   bool keep_state = false;

@@ -34,6 +34,9 @@
 
 namespace qpe {
 
+using tcg::kTcFP16;
+using tcg::kTcTF32;
+
 __constant__ double2 c_w32_64[32];  // exp(-2 pi i k / 32)
 __constant__ float2 c_w32_32[32];
 
@@ -73,7 +76,9 @@ struct HistAcc32 {
       best = v;
       besty = y;
     }
-    float t1 = v * (float)y - wcomp;  // P y (the finalize divides by N)
+    // P y (the finalize divides by N); y < 2^30 converts through int32 (an
+    // int64 conversion would run on the slow FP64 pipe)
+    float t1 = v * __int2float_rn((int)y) - wcomp;
     float t2 = wsum + t1;
     wcomp = (t2 - wsum) - t1;
     wsum = t2;
@@ -716,7 +721,7 @@ __global__ void seed_psi_kernel(const double2* __restrict__ psi, C* __restrict__
 
 // ------------------------------------------- top level on the tensor cores
 // The top level of the fused schedule for d = 16 (L = 16) under the split
-// precision QPE_C64_FP16X2. The level's contraction
+// precisions QPE_C64_FP16X2 and QPE_C64_TF32X3. The level's contraction
 //   T[y_a][m_b][i] = sum_k M[m_b][i][k] Z[y_a][k]
 // is one real GEMM per tile of 128 pencils y_a:
 //   A (128 x 32): row y_a = the 32 floats (re, im interleaved) of Z[y_a],
@@ -724,21 +729,25 @@ __global__ void seed_psi_kernel(const double2* __restrict__ psi, C* __restrict__
 //                 (c = 0 real part: (Re M, -Im M); c = 1: (Im M, Re M)),
 //   D = A B^T (128 x 512, FP32 in tensor memory): column n of row y_a is the
 //       real (c = 0) or imaginary part of T[y_a][m_b][i],
-// as fp16 hi/lo products in two passes: A_hi B_hi, then [A_hi | A_lo] times
-// [B_lo | B_hi] over K = 64 (both cross products in one pass). Each A row is
+// as split products. FP16x2: two passes, A_hi B_hi, then [A_hi | A_lo] times
+// [B_lo | B_hi] over K = 64 (both cross products in one pass); each A row is
 // scaled by a power of two into fp16's range (largest |entry| in
-// [2^14, 2^15)) and B by 2^14; the drain multiplies by the exact inverse. The
-// 128-byte rows [hi | lo] are the K-major, 128-byte-swizzled layout the MMA
-// reads. B (both orders) stays in shared memory for the whole launch.
+// [2^14, 2^15)) and B by 2^14, and the drain multiplies by the exact inverse;
+// the 128-byte rows [hi | lo] are the K-major, 128-byte-swizzled layout the
+// MMA reads, B in both orders. TF32x3: A_hi, A_lo, B_hi, B_lo are separate
+// 128-byte rows (32 tf32 values) and three products A_hi B_hi + A_hi B_lo +
+// A_lo B_hi; no scaling; one A stage (shared memory). B stays in shared memory
+// for the whole launch.
 //
-// Roles (416 threads, one CTA per SM, persistent over tiles):
-//   warps 0..3   load the tile's Z rows (one row per thread), split and store
+// Roles (384 threads, one CTA per SM, persistent over tiles; 12 warps leave
+// 168 registers per thread):
+//   warps 0..2   load the tile's Z rows (rows p and p + 96), split and store
 //                them into one of two A stages, and store the row's 16
 //                twiddles w_N^(m_b y_a) times the row's inverse scale
-//   warp 4       allocates tensor memory; lane 0 issues the MMAs: columns
+//   warp 3       allocates tensor memory; lane 0 issues the MMAs: columns
 //                [0, 256) (i < 8) into tensor-memory half 0, [256, 512) into
 //                half 1, so the MMAs of one half overlap the drain of the other
-//   warps 5..12  drain: thread (set s, lane group q, lane) owns pencil
+//   warps 4..11  drain: thread (set s, lane group q, lane) owns pencil
 //                y_a = 32 q + lane of the tile and the columns i of set s
 //                (4 per half); for each i it loads the 16 values T[m_b]
 //                (32 floats, one tcgen05.ld, issued while the previous column's
@@ -751,17 +760,25 @@ __global__ void seed_psi_kernel(const double2* __restrict__ psi, C* __restrict__
 constexpr int kTcL = 16, kTcD = 16;   // DFT length and target dimension of this kernel
 constexpr int kTcRows = 128;          // pencils per tile (MMA M)
 constexpr int kTcN = 2 * kTcD * kTcL; // 512 GEMM columns
-constexpr int kTcThreads = 416;
+constexpr int kTcThreads = 384;
+constexpr int kTcProducers = 96;      // threads of warps 0..2
 constexpr int kTcSqStride = 17;       // padded row of the hand-over buffer
 constexpr int kTcTwStride = 18;       // padded twiddle row (complex; 16-byte aligned, no bank conflicts)
-constexpr size_t kTcBBytes = (size_t)kTcN * 128;  // one B order, 64 KiB
-constexpr size_t kTcABytes = (size_t)kTcRows * 128;
-constexpr size_t kTcSmem = 2 * kTcBBytes + 2 * kTcABytes + 2 * (size_t)kTcRows * kTcTwStride * 8 +
-                           2 * (size_t)kTcRows * kTcSqStride * 4 + 1024;
+constexpr size_t kTcBBytes = (size_t)kTcN * 128;  // one B operand (order or part), 64 KiB
+// A stages and the bytes of one (fp16: rows [hi | lo]; tf32: a hi tile and a lo tile)
+template <int KIND>
+__host__ __device__ constexpr int tc_stages() { return KIND == kTcFP16 ? 2 : 1; }
+template <int KIND>
+__host__ __device__ constexpr size_t tc_a_bytes() { return (size_t)kTcRows * 128 * (KIND == kTcFP16 ? 1 : 2); }
+template <int KIND>
+__host__ __device__ constexpr size_t tc_top_smem() {
+  return 2 * kTcBBytes + tc_stages<KIND>() * tc_a_bytes<KIND>() +
+         tc_stages<KIND>() * (size_t)kTcRows * kTcTwStride * 8 + 2 * (size_t)kTcRows * kTcSqStride * 4 + 1024;
+}
 
 struct TcTopArgs {
   const float2* seeds;       // Z of the level below (compact when the level below is sharded)
-  const __half* btab;        // [2][512][64]: rows [hi | lo], then [lo | hi]
+  const uint4* btab;         // 128 KiB: fp16 rows [hi | lo] then [lo | hi], or tf32 rows hi then lo
   const float2* tw_lo;
   const float2* tw_hi;
   double* hist;
@@ -772,9 +789,18 @@ struct TcTopArgs {
   double pscale;
 };
 
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // B rows of the top level's table (tab[k][m_b d + i] = M[m_b][i][k],
-// complex64), scaled by 2^14 and split into fp16 hi / lo.
-__global__ void __launch_bounds__(256) tc_top_table_kernel(const float2* __restrict__ tab, __half* __restrict__ out) {
+// complex64). FP16x2: scaled by 2^14, split into fp16 hi / lo, rows [hi | lo]
+// then [lo | hi] (64 halves each). TF32x3: split into tf32 hi / lo, the hi rows
+// then the lo rows (32 floats each).
+template <int KIND>
+__global__ void __launch_bounds__(256) tc_top_table_kernel(const float2* __restrict__ tab, void* __restrict__ outp) {
   pdl_begin();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kTcN * 32; e += gridDim.x * blockDim.x) {
     const int n = e >> 5, kk = e & 31;
@@ -782,27 +808,38 @@ __global__ void __launch_bounds__(256) tc_top_table_kernel(const float2* __restr
     const int k = kk >> 1, cp = kk & 1;
     const float2 m = tab[k * (kTcL * kTcD) + mb * kTcD + i];
     const float v = c == 0 ? (cp == 0 ? m.x : -m.y) : (cp == 0 ? m.y : m.x);
-    const float vs = v * 16384.0f;  // 2^14, exact
-    const __half hi = __float2half_rn(vs);
-    const __half lo = __float2half_rn(vs - __half2float(hi));
-    out[(size_t)n * 64 + kk] = hi;             // [hi | lo]
-    out[(size_t)n * 64 + 32 + kk] = lo;
-    out[(size_t)(kTcN + n) * 64 + kk] = lo;    // [lo | hi]
-    out[(size_t)(kTcN + n) * 64 + 32 + kk] = hi;
+    if constexpr (KIND == kTcFP16) {
+      __half* out = static_cast<__half*>(outp);
+      const float vs = v * 16384.0f;  // 2^14, exact
+      const __half hi = __float2half_rn(vs);
+      const __half lo = __float2half_rn(vs - __half2float(hi));
+      out[(size_t)n * 64 + kk] = hi;             // [hi | lo]
+      out[(size_t)n * 64 + 32 + kk] = lo;
+      out[(size_t)(kTcN + n) * 64 + kk] = lo;    // [lo | hi]
+      out[(size_t)(kTcN + n) * 64 + 32 + kk] = hi;
+    } else {
+      float* out = static_cast<float*>(outp);
+      const float hi = tf32_rna(v);
+      out[(size_t)n * 32 + kk] = hi;
+      out[(size_t)(kTcN + n) * 32 + kk] = tf32_rna(v - hi);
+    }
   }
   pdl_trigger();
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a) {
   using namespace tcg;
   pdl_begin();
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  unsigned char* Bs = base;                            // B1 then B2, 64 KiB each
-  unsigned char* As = base + 2 * kTcBBytes;            // two A stages, 16 KiB each
-  float2* twS = reinterpret_cast<float2*>(As + 2 * kTcABytes);  // [2][128][18]: scaled twiddles per row
-  float* sq = reinterpret_cast<float*>(twS + 2 * kTcRows * kTcTwStride);  // [2][128][17]
+  constexpr int NST = tc_stages<KIND>();
+  constexpr size_t AB = tc_a_bytes<KIND>();
+  unsigned char* Bs = base;                            // two B operands, 64 KiB each
+  unsigned char* As = base + 2 * kTcBBytes;            // NST A stages
+  float2* twS = reinterpret_cast<float2*>(As + NST * AB);  // [NST][128][18]: scaled twiddles per row
+  float* sq = reinterpret_cast<float*>(twS + NST * kTcRows * kTcTwStride);  // [2][128][17]
   __shared__ uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2], sq_full[2], sq_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
@@ -821,7 +858,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) {
+  if (warp == 3) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(512u)
                  : "memory");
@@ -829,7 +866,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
   }
   // both orders of B into shared memory, swizzled (16-byte chunks)
   {
-    const uint4* src = reinterpret_cast<const uint4*>(a.btab);
+    const uint4* src = a.btab;
     for (int q = threadIdx.x; q < 2 * kTcN * 8; q += kTcThreads) {
       const int which = q / (kTcN * 8), n = (q >> 3) % kTcN, c = q & 7;
       *reinterpret_cast<uint4*>(Bs + which * kTcBBytes + sw128_offset(n, c)) = __ldg(src + q);
@@ -846,17 +883,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
   const int lvl_shift = a.nmeas - a.logna - 4;
   const int64_t lvl_mask = (int64_t(1) << (a.logna + 4)) - 1;
 
-  if (warp < 4) {
+  if (warp < 3) {
     // ---------------------------------------------------------- producer
-    const int p = threadIdx.x;  // tile row
     int it = 0;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
-      const int b = it & 1;
-      if (it >= 2 && !mbar_wait(&a_empty[b], ((it >> 1) - 1) & 1)) {
+      const int b = it % NST;
+      if (it >= NST && !mbar_wait(&a_empty[b], ((it / NST) - 1) & 1)) {
         atomicExch(&fail, 1);
         break;
       }
       if (*vfail) break;
+      for (int p = threadIdx.x; p < kTcRows; p += kTcProducers) {  // tile rows of this thread
       const int64_t j = t * kTcRows + p;
       const float4* src = reinterpret_cast<const float4*>(a.seeds + ((a.seed_rk + (j << a.seed_sh)) << 4));
       float x[32];
@@ -868,14 +905,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
         x[4 * c + 2] = v.z;
         x[4 * c + 3] = v.w;
       }
-      float mx = 0.f;
+      float sc = 1.f, invr = 1.f;
+      if constexpr (KIND == kTcFP16) {
+        float mx = 0.f;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) mx = fmaxf(mx, fabsf(x[c]));
-      // floor(log2(mx)) from the exponent field; zero or tiny rows keep scale 1
-      const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
-      const int e = (ex < -100 || ex > 100) ? 0 : 14 - ex;
-      const float sc = __uint_as_float((uint32_t)(127 + e) << 23);
-      const float invr = __uint_as_float((uint32_t)(127 - e - 14) << 23);  // undoes both operand scales
+        for (int c = 0; c < 32; ++c) mx = fmaxf(mx, fabsf(x[c]));
+        // floor(log2(mx)) from the exponent field; zero or tiny rows keep scale 1
+        const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
+        const int e = (ex < -100 || ex > 100) ? 0 : 14 - ex;
+        sc = __uint_as_float((uint32_t)(127 + e) << 23);
+        invr = __uint_as_float((uint32_t)(127 - e - 14) << 23);  // undoes both operand scales
+      }
       {
         const int64_t ya = a.rk + (j << a.sh);
         float2* tw = twS + (b * kTcRows + p) * kTcTwStride;
@@ -890,39 +930,55 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
           *reinterpret_cast<float4*>(tw + mb) = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
         }
       }
-      unsigned char* row = As + b * kTcABytes;
+      unsigned char* row = As + b * AB;
+      if constexpr (KIND == kTcFP16) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t hw[4], lw[4];
+        for (int c = 0; c < 4; ++c) {
+          uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const float x0 = x[8 * c + 2 * h] * sc, x1 = x[8 * c + 2 * h + 1] * sc;
-          const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-          const __half l0 = __float2half_rn(x0 - __half2float(h0)), l1 = __float2half_rn(x1 - __half2float(h1));
-          hw[h] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-          lw[h] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+          for (int h = 0; h < 4; ++h) {
+            const float x0 = x[8 * c + 2 * h] * sc, x1 = x[8 * c + 2 * h + 1] * sc;
+            const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+            const __half l0 = __float2half_rn(x0 - __half2float(h0)), l1 = __float2half_rn(x1 - __half2float(h1));
+            hw[h] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+            lw[h] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+          }
+          *reinterpret_cast<uint4*>(row + sw128_offset(p, c)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(row + sw128_offset(p, 4 + c)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-        *reinterpret_cast<uint4*>(row + sw128_offset(p, c)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(row + sw128_offset(p, 4 + c)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      } else {  // tf32: the hi tile, then the lo tile 16 KiB on
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float hv[4], lv[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            hv[h] = tf32_rna(x[4 * c + h]);
+            lv[h] = tf32_rna(x[4 * c + h] - hv[h]);
+          }
+          *reinterpret_cast<float4*>(row + sw128_offset(p, c)) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<float4*>(row + kTcRows * 128 + sw128_offset(p, c)) =
+              make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&a_full[b]);
+      }
     }
-  } else if (warp == 4) {
+  } else if (warp == 3) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc<kTcFP16, 256>();
+      const uint32_t idesc = make_idesc<KIND, 256>();
       const uint32_t b1 = smem_u32(Bs), b2 = smem_u32(Bs + kTcBBytes);
       int it = 0;
       for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
-        const int b = it & 1;
-        if (!mbar_wait(&a_full[b], (it >> 1) & 1)) {
+        const int b = it % NST;
+        if (!mbar_wait(&a_full[b], (it / NST) & 1)) {
           atomicExch(&fail, 1);
           break;
         }
         if (*vfail) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t ad = sw128_desc(smem_u32(As + b * kTcABytes));
+        const uint64_t ad = sw128_desc(smem_u32(As + b * AB));
         bool ok = true;
         for (int h = 0; h < 2; ++h) {
           if (it >= 1 && !mbar_wait(&t_empty[h], (it - 1) & 1)) {
@@ -932,10 +988,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint64_t bd1 = sw128_desc(b1 + (uint32_t)h * 32768u), bd2 = sw128_desc(b2 + (uint32_t)h * 32768u);
           const uint32_t d = tmem + (uint32_t)(h * 256);
-          umma_k<kTcFP16>(d, ad, bd1, idesc, 0u);          // A_hi B_hi, K = 0..15
-          umma_k<kTcFP16>(d, ad + 2, bd1 + 2, idesc, 1u);  //            K = 16..31
+          if constexpr (KIND == kTcFP16) {
+            umma_k<kTcFP16>(d, ad, bd1, idesc, 0u);          // A_hi B_hi, K = 0..15
+            umma_k<kTcFP16>(d, ad + 2, bd1 + 2, idesc, 1u);  //            K = 16..31
 #pragma unroll
-          for (int k = 0; k < 4; ++k) umma_k<kTcFP16>(d, ad + 2 * k, bd2 + 2 * k, idesc, 1u);  // cross, K = 64
+            for (int k = 0; k < 4; ++k) umma_k<kTcFP16>(d, ad + 2 * k, bd2 + 2 * k, idesc, 1u);  // cross, K = 64
+          } else {
+            const uint64_t adl = sw128_desc(smem_u32(As + b * AB + kTcRows * 128));  // A_lo tile
+#pragma unroll
+            for (int k = 0; k < 4; ++k) umma_k<kTcTF32>(d, ad + 2 * k, bd1 + 2 * k, idesc, k == 0 ? 0u : 1u);  // hi hi
+#pragma unroll
+            for (int k = 0; k < 4; ++k) umma_k<kTcTF32>(d, ad + 2 * k, bd2 + 2 * k, idesc, 1u);   // hi lo
+#pragma unroll
+            for (int k = 0; k < 4; ++k) umma_k<kTcTF32>(d, adl + 2 * k, bd1 + 2 * k, idesc, 1u);  // lo hi
+          }
           umma_commit(&t_full[h]);
         }
         if (!ok) {
@@ -947,15 +1013,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
     }
   } else {
     // ---------------------------------------------------------- drain
-    const int dw = warp - 5;
+    const int dw = warp - 4;
     const int set = dw >> 2, lg = warp & 3;
     const int row = lg * 32 + lane;
     HistAcc32 h32;
     int it = 0;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
-      const int b = it & 1;
+      const int b = it % NST;   // A / twiddle stage
+      const int bq = it & 1;    // hand-over buffer
       const int64_t j = t * kTcRows + row;
-      float2 tw[kTcL];
+      const float4* tr = reinterpret_cast<const float4*>(twS + (b * kTcRows + row) * kTcTwStride);
       float acc[kTcL];
 #pragma unroll
       for (int yb = 0; yb < kTcL; ++yb) acc[yb] = 0.f;
@@ -968,17 +1035,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
           ok = false;
           break;
         }
-        if (h == 0) {
-          const float4* tr = reinterpret_cast<const float4*>(twS + (b * kTcRows + row) * kTcTwStride);
-#pragma unroll
-          for (int mb = 0; mb < kTcL; mb += 2) {
-            const float4 w = tr[mb >> 1];
-            tw[mb] = make_float2(w.x, w.y);
-            tw[mb + 1] = make_float2(w.z, w.w);
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&a_empty[b]);  // this warp is done with the stage's twiddles
-        }
+        // the stage's twiddles are read from shared memory at every use (no
+        // registers held for them); the stage is released after the last half
         const uint32_t col0 = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * 256 + set * 4 * 32);
         uint32_t v[32];
         tmem_ld32_async(col0, v);
@@ -987,8 +1045,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
         for (int q = 0; q < 4; ++q) {  // column i = 8 h + 4 set + q
           float2 x[kTcL];
 #pragma unroll
-          for (int mb = 0; mb < kTcL; ++mb)
-            x[mb] = cmul(make_float2(__uint_as_float(v[2 * mb]), __uint_as_float(v[2 * mb + 1])), tw[mb]);
+          for (int mb = 0; mb < kTcL; mb += 2) {
+            const float4 w = tr[mb >> 1];
+            x[mb] = cmul(make_float2(__uint_as_float(v[2 * mb]), __uint_as_float(v[2 * mb + 1])), make_float2(w.x, w.y));
+            x[mb + 1] = cmul(make_float2(__uint_as_float(v[2 * mb + 2]), __uint_as_float(v[2 * mb + 3])),
+                             make_float2(w.z, w.w));
+          }
           if (q < 3) tmem_ld32_async(col0 + (uint32_t)((q + 1) * 32), v);  // next column while this DFT runs
           dft_k<float2, 4, kTcL>(x);
 #pragma unroll
@@ -997,29 +1059,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&t_empty[h]);
+        if (lane == 0) {
+          mbar_arrive(&t_empty[h]);
+          if (h == 1) mbar_arrive(&a_empty[b]);  // this warp is done with the stage's twiddles
+        }
       }
       if (!ok || *vfail) {
         atomicExch(&fail, 1);
         break;
       }
-      float* sqb = sq + b * kTcRows * kTcSqStride + row * kTcSqStride;
+      float* sqb = sq + bq * kTcRows * kTcSqStride + row * kTcSqStride;
       if (set == 1) {
-        if (it >= 2 && !mbar_wait(&sq_empty[b], ((it >> 1) - 1) & 1)) {
+        if (it >= 2 && !mbar_wait(&sq_empty[bq], ((it >> 1) - 1) & 1)) {
           atomicExch(&fail, 1);
           break;
         }
 #pragma unroll
         for (int yb = 0; yb < kTcL; ++yb) sqb[yb] = acc[yb];
-        mbar_arrive(&sq_full[b]);
+        mbar_arrive(&sq_full[bq]);
       } else {
-        if (!mbar_wait(&sq_full[b], (it >> 1) & 1)) {
+        if (!mbar_wait(&sq_full[bq], (it >> 1) & 1)) {
           atomicExch(&fail, 1);
           break;
         }
 #pragma unroll
         for (int yb = 0; yb < kTcL; ++yb) acc[yb] += sqb[yb];
-        mbar_arrive(&sq_empty[b]);
+        mbar_arrive(&sq_empty[bq]);
 #pragma unroll
         for (int yb = 0; yb < kTcL; ++yb) {
           const int64_t yl = j + ((int64_t)yb << lna);
@@ -1050,7 +1115,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
     a.parts[blockIdx.x] = r;
     if (fail) atomicExch(a.err, (int)QPE_ERR_TIMEOUT);
   }
-  if (warp == 4)
+  if (warp == 3)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
   pdl_trigger();
 }
@@ -1062,11 +1127,14 @@ size_t tc_top_table_bytes() { return 2 * kTcBBytes; }
 // (one CTA per SM, at most one per tile). Returns launches or -1.
 static int launch_tc_top(const Instance& in, char* ws, const LevelArgs<float2>& la, cudaStream_t s,
                          cudaEvent_t* top_ev, int64_t* grid_out) {
-  __half* btab = reinterpret_cast<__half*>(ws + in.off_tctab);
-  if (launch_k(tc_top_table_kernel, dim3(64), dim3(256), 0, s, la.tab, btab) != cudaSuccess) return -1;
+  void* btab = ws + in.off_tctab;
+  const bool fp16 = in.tc_top_prec == QPE_C64_FP16X2;
+  if ((fp16 ? launch_k(tc_top_table_kernel<kTcFP16>, dim3(64), dim3(256), 0, s, la.tab, btab)
+            : launch_k(tc_top_table_kernel<kTcTF32>, dim3(64), dim3(256), 0, s, la.tab, btab)) != cudaSuccess)
+    return -1;
   TcTopArgs a{};
   a.seeds = la.seeds;
-  a.btab = btab;
+  a.btab = static_cast<const uint4*>(btab);
   a.tw_lo = la.tw_lo;
   a.tw_hi = la.tw_hi;
   a.hist = la.hist;
@@ -1085,7 +1153,11 @@ static int launch_tc_top(const Instance& in, char* ws, const LevelArgs<float2>& 
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid > kReduceBlocks) grid = kReduceBlocks;
   if (top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
-  if (launch_k(level_tc_top_kernel, dim3((unsigned)grid), dim3(kTcThreads), kTcSmem, s, a) != cudaSuccess) return -1;
+  if ((fp16 ? launch_k(level_tc_top_kernel<kTcFP16>, dim3((unsigned)grid), dim3(kTcThreads), tc_top_smem<kTcFP16>(),
+                       s, a)
+            : launch_k(level_tc_top_kernel<kTcTF32>, dim3((unsigned)grid), dim3(kTcThreads), tc_top_smem<kTcTF32>(),
+                       s, a)) != cudaSuccess)
+    return -1;
   if (top_ev && record_event(top_ev[1], s) != cudaSuccess) return -1;
   *grid_out = grid;
   return 2;
@@ -1178,7 +1250,11 @@ cudaError_t configure_level_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_w32_32, w32v, sizeof(w32v));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(level_tc_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  e = cudaFuncSetAttribute(level_tc_top_kernel<kTcFP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_top_smem<kTcFP16>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(level_tc_top_kernel<kTcTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_top_smem<kTcTF32>());
   if (e != cudaSuccess) return e;
   return set_level_attrs();
 }

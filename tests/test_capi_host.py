@@ -128,9 +128,10 @@ def test_plan_batched_validation(q):
     st, ws, h = q.plan_batched_workspace([(3, 8), (8, 10)], q.C64_FP16X2, q.FLAG_SQUARE_TC)
     assert st == q.OK and ws > 0
     q.LIB.qpe_destroy(h)
-    st, ws, h = q.plan_workspace(4, 12, q.C64_FP16X2, 0)
-    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 1
-    q.LIB.qpe_destroy(h)
+    for prec in (q.C64_FP16X2, q.C64_TF32X3):
+        st, ws, h = q.plan_workspace(4, 12, prec, 0)
+        assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 1
+        q.LIB.qpe_destroy(h)
     st, ws, h = q.plan_workspace(3, 8, q.C64_FP16X2, 0)
     assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0
     q.LIB.qpe_destroy(h)

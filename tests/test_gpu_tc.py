@@ -136,26 +136,27 @@ def test_c4_split_precision_l1(q, prec):
 
 
 # ------------------------------------ fused top level on the tensor cores
+@pytest.mark.parametrize("prec", ALL)
 @pytest.mark.parametrize("nmeas", [11, 12, 15, 18, 21])
-def test_fused_tensor_core_top_level_vs_oracle(q, nmeas):
-    """Nmat = 4 under FP16x2: the fused schedule with its top level (16-point
-    DFT, 128-pencil tiles) as fp16 split products on tcgen05, the deep levels
-    in complex64 on the CUDA cores. Whole histogram against the gate-by-gate
+def test_fused_tensor_core_top_level_vs_oracle(q, prec, nmeas):
+    """Nmat = 4 under FP16x2 and TF32x3: the fused schedule with its top level
+    (16-point DFT, 128-pencil tiles) as split products on tcgen05, the deep
+    levels in complex64 on the CUDA cores. Whole histogram against the gate-by-gate
     oracle (max-abs and the L1 bound), the readout, and the same histogram as
     the complex64 CUDA-core plan within the split's accuracy."""
     rng = np.random.default_rng(400 + nmeas)
     inst = W.haar_instance(rng, 4, nmeas, superposition=True)
-    plan = q.Plan(4, nmeas, FP16X2)
+    plan = q.Plan(4, nmeas, prec)
     assert plan.query(q.INFO_TC_TOP_LEVEL) == 1
     plan.load(inst.U, inst.psi)
     plan.run()
     P, am, pa, pm = plan.probs()
     ref = gates.qpe_probabilities(inst.U, inst.psi, nmeas)
     err = np.abs(P - ref)
-    assert err.max() <= PROB_TOL[FP16X2]
+    assert err.max() <= PROB_TOL[prec]
     assert err.sum() <= L1_BOUND
     top2 = np.sort(ref)[-2:]
-    if top2[1] - top2[0] > 10 * PROB_TOL[FP16X2]:
+    if top2[1] - top2[0] > 10 * PROB_TOL[prec]:
         assert am == readout.argmax_lowest(ref)
     assert abs(pm - readout.phase_weighted_mean(ref)) <= 2e-5
     c64 = q.Plan(4, nmeas, q.C64_FP32)
@@ -165,12 +166,13 @@ def test_fused_tensor_core_top_level_vs_oracle(q, nmeas):
     assert np.abs(P - P32).sum() <= L1_BOUND
 
 
-def test_fused_tensor_core_top_level_eigenvector_and_graph(q):
+@pytest.mark.parametrize("prec", ALL)
+def test_fused_tensor_core_top_level_eigenvector_and_graph(q, prec):
     """An eigenvector input (single Fejer kernel, a sharp peak), replayed as a
     CUDA graph twice: identical histograms, closed form within the bound."""
     rng = np.random.default_rng(77)
     inst = W.haar_instance(rng, 4, 16)
-    plan = q.Plan(4, 16, FP16X2, q.FLAG_GRAPH)
+    plan = q.Plan(4, 16, prec, q.FLAG_GRAPH)
     plan.load(inst.U, inst.psi)
     outs = []
     for _ in range(2):
@@ -195,14 +197,15 @@ def test_fused_tensor_core_top_level_falls_back_below_one_tile(q):
     assert np.abs(P - gates.qpe_probabilities(inst.U, inst.psi, 9)).sum() <= L1_BOUND
 
 
-def test_c5_fp16x2_vs_fp64_full_size(q):
-    """The 34-qubit workload under FP16x2 (tensor-core top level) against the
-    all-FP64 path on the same GPU: L1 over all 2^30 bins within 1e-6, the same
-    most probable outcome; and sampled bins against the closed form."""
+def test_c5_split_precisions_vs_fp64_full_size(q):
+    """The 34-qubit workload under FP16x2 and TF32x3 (tensor-core top level)
+    against the all-FP64 path on the same GPU: L1 over all 2^30 bins within
+    1e-6, the same most probable outcome; and sampled bins against the closed
+    form."""
     import torch
     inst = W.c5()
     hs = {}
-    for prec in (q.FP64, FP16X2):
+    for prec in (q.FP64, FP16X2, TF32X3):
         plan = q.Plan(inst.nmat, inst.nmeas, prec)
         plan.load(inst.U, inst.psi)
         plan.run()
@@ -212,12 +215,13 @@ def test_c5_fp16x2_vs_fp64_full_size(q):
         plan.close()
         del plan
         torch.cuda.empty_cache()
-    l1 = float((hs[FP16X2][0] - hs[q.FP64][0]).abs().sum().item())
-    print(f"C5 FP16x2 vs FP64: L1 {l1:.3e}")
-    assert l1 <= L1_BOUND
-    assert hs[FP16X2][1] == hs[q.FP64][1]
     rng = np.random.default_rng(6)
     ys = rng.integers(0, inst.N, 1 << 14)
-    got = hs[FP16X2][0][torch.from_numpy(ys).cuda()].cpu().numpy()
     Q = fejer.probabilities(inst.phases, inst.weights, inst.nmeas, y=ys)
-    assert np.abs(got - Q).max() <= PROB_TOL[FP16X2]
+    for prec in ALL:
+        l1 = float((hs[prec][0] - hs[q.FP64][0]).abs().sum().item())
+        print(f"C5 precision {prec} vs FP64: L1 {l1:.3e}")
+        assert l1 <= L1_BOUND
+        assert hs[prec][1] == hs[q.FP64][1]
+        got = hs[prec][0][torch.from_numpy(ys).cuda()].cpu().numpy()
+        assert np.abs(got - Q).max() <= PROB_TOL[prec]
