@@ -18,20 +18,6 @@ namespace {
 template <typename C>
 __device__ __forceinline__ C ldgc(const C* p) { return __ldg(p); }
 
-// item index with items[i].tile0 <= b < items[i + 1].tile0 (tile0 ascending)
-template <typename T>
-__device__ __forceinline__ int find_item(const T* items, int n, int64_t b) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (items[mid].tile0 <= b)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 }  // namespace
 
 // P_k = P_(k-1)^2 for every listed instance: 8 x 8 output tile per CTA, the

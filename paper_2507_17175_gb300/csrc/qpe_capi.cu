@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -329,6 +330,18 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
   bm.items.clear();
   bm.launches.clear();
   bm.fin.clear();
+  bm.init_items.clear();
+  bm.dbl_items.clear();
+  bm.fft_items.clear();
+  bm.red_items.clear();
+  bm.dbl_rounds.clear();
+  bm.tc_split.clear();
+  bm.tc_gemm.clear();
+  bm.tc_rounds.clear();
+  bm.fft_rounds.clear();
+  bm.fin_plain.clear();
+  bm.ninit = bm.nred = bm.maxn_plain = 0;
+  bm.red_blocks = 0;
   bm.maxn = 0;
   for (const Instance& in : p->inst) bm.maxn = std::max(bm.maxn, in.nmeas);
   bm.sq_begin.assign(bm.maxn + 1, 0);
@@ -515,6 +528,131 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
       }
     }
   }
+  // plain instances: row 0, the doubling rounds, the QFT^-1 passes, the
+  // histogram, the readout, each one grouped launch across the instances
+  {
+    std::vector<int> pl = bm.plain;
+    for (int i : pl) bm.maxn_plain = std::max(bm.maxn_plain, p->inst[i].nmeas);
+    auto build_plain = [&](auto tag) {
+      using C = decltype(tag);
+      for (int i : pl) {
+        const Instance& in = p->inst[i];
+        qpe::InitItem<C> it{};
+        it.S = reinterpret_cast<C*>(ws + in.off_state);
+        it.psi = reinterpret_cast<const double2*>(ws + in.off_psi);
+        it.scale = 1.0 / std::sqrt(std::ldexp(1.0, in.nmeas));
+        it.d = (int)in.d;
+        push_bytes(bm.init_items, &it, sizeof(it));
+        ++bm.ninit;
+      }
+      // level j of an instance runs on the tensor cores once it fills 128-row
+      // tiles and 128-column tiles (2d >= 128), on the CUDA cores otherwise
+      auto on_tc = [&](const Instance& in, int j) {
+        return is_tc(p->prec) && (int64_t(1) << j) >= 128 && in.d >= 64;
+      };
+      for (int j = 0; j < bm.maxn_plain; ++j) {
+        {
+          qpe::TcRound T{};
+          T.j = j;
+          T.item_off = (int)bm.tc_split.size();
+          for (int i : pl) {
+            const Instance& in = p->inst[i];
+            if (in.nmeas <= j || !on_tc(in, j)) continue;
+            qpe::TcSplitItem sp{};
+            qpe::TcGemmItem gm{};
+            if (!qpe::tc_level_items(in, ws, p->prec, j, &sp, &gm)) throw std::runtime_error("tensor map");
+            sp.row0 = sp.tile0 = T.rows;
+            sp.e0 = T.elems;
+            gm.tile0 = T.tiles;
+            T.rows += sp.rows;
+            T.elems += (2 * in.d) * (2 * in.d);
+            T.tiles += qpe::tc_level_tiles(in, j);
+            bm.tc_split.push_back(sp);
+            bm.tc_gemm.push_back(gm);
+          }
+          T.nitems = (int)bm.tc_split.size() - T.item_off;
+          if (T.nitems > 0) bm.tc_rounds.push_back(T);
+        }
+        for (int dclass : {2, 4, 8, 16, 32, 64}) {
+          qpe::DblRound R{};
+          R.j = j;
+          R.dclass = dclass;
+          R.item_off = (int)(bm.dbl_items.size() / sizeof(qpe::DblItem<C>));
+          int64_t tiles = 0;
+          for (int i : pl) {
+            const Instance& in = p->inst[i];
+            if (in.nmeas <= j || on_tc(in, j) || std::min<int64_t>(in.d, 64) != dclass) continue;
+            int BM = 0, BN = 0;
+            qpe::doubling_tile((int)in.d, &BM, &BN);
+            qpe::DblItem<C> it{};
+            it.S = reinterpret_cast<C*>(ws + in.off_state);
+            it.P = reinterpret_cast<const C*>(ws + (c64 ? in.off_pow32 : in.off_pow64)) + (int64_t)j * in.d * in.d;
+            it.M = int64_t(1) << j;
+            it.d = (int)in.d;
+            it.tile0 = tiles;
+            tiles += ((it.M + BM - 1) / BM) * (in.d / BN);
+            push_bytes(bm.dbl_items, &it, sizeof(it));
+          }
+          R.nitems = (int)(bm.dbl_items.size() / sizeof(qpe::DblItem<C>)) - R.item_off;
+          R.tiles = tiles;
+          if (R.nitems > 0) bm.dbl_rounds.push_back(R);
+        }
+      }
+      int maxp = 0;
+      for (int i : pl) maxp = std::max(maxp, p->inst[i].fft.passes);
+      for (int pass = 0; pass < maxp; ++pass) {
+        qpe::FftRound R{};
+        R.item_off = (int)(bm.fft_items.size() / sizeof(qpe::FftItem<C>));
+        int64_t blocks = 0;
+        size_t smem = 0;
+        for (int i : pl) {
+          const Instance& in = p->inst[i];
+          if (in.fft.passes <= pass) continue;
+          qpe::FftItem<C> it{};
+          int64_t nb = 0;
+          size_t sm = 0;
+          it.a = qpe::fft_pass_args(in, pass, &nb, &sm, sizeof(C));
+          it.X = reinterpret_cast<C*>(ws + in.off_state);
+          it.lo = reinterpret_cast<const C*>(ws + (c64 ? in.off_tw_lo32 : in.off_tw_lo64));
+          it.hi = reinterpret_cast<const C*>(ws + (c64 ? in.off_tw_hi32 : in.off_tw_hi64));
+          it.tile0 = blocks;
+          blocks += nb;
+          smem = std::max(smem, sm);
+          push_bytes(bm.fft_items, &it, sizeof(it));
+        }
+        R.nitems = (int)(bm.fft_items.size() / sizeof(qpe::FftItem<C>)) - R.item_off;
+        R.blocks = blocks;
+        R.smem = smem;
+        if (R.nitems > 0) bm.fft_rounds.push_back(R);
+      }
+      for (int i : pl) {
+        const Instance& in = p->inst[i];
+        qpe::RedItem<C> it{};
+        it.X = reinterpret_cast<const C*>(ws + in.off_state);
+        it.hist = reinterpret_cast<double*>(ws + in.off_hist);
+        it.parts = reinterpret_cast<qpe::Partial*>(ws + in.off_partials);
+        it.N = in.N;
+        it.logd = in.nmat;
+        it.n = in.nmeas;
+        it.g = qpe::fft_digits(in.fft);
+        it.nblk = qpe::reduce_blocks(in);
+        it.tile0 = bm.red_blocks;
+        bm.red_blocks += it.nblk;
+        push_bytes(bm.red_items, &it, sizeof(it));
+        ++bm.nred;
+        qpe::FinItem f{};
+        f.parts = it.parts;
+        f.out = reinterpret_cast<qpe::Scalars*>(ws + in.off_scalars);
+        f.count = (int)it.nblk;
+        f.nmeas = in.nmeas;
+        bm.fin_plain.push_back(f);
+      }
+    };
+    if (c64)
+      build_plain(float2{});
+    else
+      build_plain(double2{});
+  }
 }
 
 // Workspace offsets of the uploaded lists, after the instances' regions.
@@ -531,6 +669,13 @@ size_t place_batch_meta(qpe::BatchMeta& bm, size_t off) {
   bm.off_args = take(bm.level_args.size());
   bm.off_items = take(bm.items.size() * sizeof(qpe::GroupItem));
   bm.off_fin = take(bm.fin.size() * sizeof(qpe::FinItem));
+  bm.off_init = take(bm.init_items.size());
+  bm.off_dbl = take(bm.dbl_items.size());
+  bm.off_fft = take(bm.fft_items.size());
+  bm.off_red = take(bm.red_items.size());
+  bm.off_finp = take(bm.fin_plain.size() * sizeof(qpe::FinItem));
+  bm.off_tcsp = take(bm.tc_split.size() * sizeof(qpe::TcSplitItem));
+  bm.off_tcgm = take(bm.tc_gemm.size() * sizeof(qpe::TcGemmItem));
   return off;
 }
 
@@ -546,7 +691,14 @@ qpe_status upload_batch_meta(qpe_plan_t p) {
               {bm.off_seed, bm.seed_items.data(), bm.seed_items.size()},
               {bm.off_args, bm.level_args.data(), bm.level_args.size()},
               {bm.off_items, bm.items.data(), bm.items.size() * sizeof(qpe::GroupItem)},
-              {bm.off_fin, bm.fin.data(), bm.fin.size() * sizeof(qpe::FinItem)}};
+              {bm.off_fin, bm.fin.data(), bm.fin.size() * sizeof(qpe::FinItem)},
+              {bm.off_init, bm.init_items.data(), bm.init_items.size()},
+              {bm.off_dbl, bm.dbl_items.data(), bm.dbl_items.size()},
+              {bm.off_fft, bm.fft_items.data(), bm.fft_items.size()},
+              {bm.off_red, bm.red_items.data(), bm.red_items.size()},
+              {bm.off_finp, bm.fin_plain.data(), bm.fin_plain.size() * sizeof(qpe::FinItem)},
+              {bm.off_tcsp, bm.tc_split.data(), bm.tc_split.size() * sizeof(qpe::TcSplitItem)},
+              {bm.off_tcgm, bm.tc_gemm.data(), bm.tc_gemm.size() * sizeof(qpe::TcGemmItem)}};
   for (const Blk& b : blks) {
     if (!b.n) continue;
     cudaError_t e = cudaMemcpyAsync(p->ws + b.off, b.src, b.n, cudaMemcpyHostToDevice, p->stream);
@@ -672,19 +824,45 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
       in.state_valid = in.keep_state;
     }
   }
-  for (int i : bm.plain) {
-    Instance& in = p->inst[i];
-    in.powers_done = true;
-    int r = c64 ? qpe::launch_sweep<float2>(in, ws, false, p->stream, p->prec)
-                : qpe::launch_sweep<double2>(in, ws, false, p->stream, p->prec);
-    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain sweep");
-    r = c64 ? qpe::launch_fft<float2>(in, ws, p->stream) : qpe::launch_fft<double2>(in, ws, p->stream);
-    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain fft");
-    r = c64 ? qpe::launch_reduce<float2>(in, ws, p->stream) : qpe::launch_reduce<double2>(in, ws, p->stream);
-    if (!chk(r)) return cuda_fail(p, cudaGetLastError(), "plain reduce");
-    in.state_stage = QPE_STAGE_REDUCE;
-    in.state_natural = false;
-    in.state_valid = true;
+  if (!bm.plain.empty()) {
+    // the plain instances step by step, each step one grouped launch
+    auto run_plain = [&](auto tag) -> bool {
+      using C = decltype(tag);
+      if (!chk(qpe::launch_init_grouped<C>(reinterpret_cast<const qpe::InitItem<C>*>(ws + bm.off_init), bm.ninit,
+                                           p->stream)))
+        return false;
+      for (int j = 0; j < bm.maxn_plain; ++j) {
+        for (const qpe::DblRound& R : bm.dbl_rounds)
+          if (R.j == j &&
+              !chk(qpe::launch_doubling_grouped<C>(reinterpret_cast<const qpe::DblItem<C>*>(ws + bm.off_dbl) + R.item_off,
+                                                   R.nitems, R.tiles, R.dclass, p->stream)))
+            return false;
+        for (const qpe::TcRound& T : bm.tc_rounds)
+          if (T.j == j &&
+              !chk(qpe::launch_tc_level_grouped(
+                  p->prec, reinterpret_cast<const qpe::TcSplitItem*>(ws + bm.off_tcsp) + T.item_off,
+                  reinterpret_cast<const qpe::TcGemmItem*>(ws + bm.off_tcgm) + T.item_off, T.nitems, T.rows, T.elems,
+                  T.tiles, p->stream)))
+            return false;
+      }
+      for (const qpe::FftRound& R : bm.fft_rounds)
+        if (!chk(qpe::launch_fft_grouped<C>(reinterpret_cast<const qpe::FftItem<C>*>(ws + bm.off_fft) + R.item_off,
+                                            R.nitems, R.blocks, R.smem, p->stream)))
+          return false;
+      if (!chk(qpe::launch_reduce_grouped<C>(reinterpret_cast<const qpe::RedItem<C>*>(ws + bm.off_red), bm.nred,
+                                             bm.red_blocks, p->stream)))
+        return false;
+      return chk(qpe::launch_finalize_grouped(reinterpret_cast<const qpe::FinItem*>(ws + bm.off_finp),
+                                              (int)bm.fin_plain.size(), p->stream));
+    };
+    if (!(c64 ? run_plain(float2{}) : run_plain(double2{}))) return cuda_fail(p, cudaGetLastError(), "plain instances");
+    for (int i : bm.plain) {
+      Instance& in = p->inst[i];
+      in.powers_done = true;
+      in.state_stage = QPE_STAGE_REDUCE;
+      in.state_natural = false;
+      in.state_valid = true;
+    }
   }
   *launches = n;
   return QPE_OK;
@@ -934,7 +1112,11 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
     if (qpe::launch_twiddles(in, p->ws, p->stream) < 0) return cuda_fail(p, cudaGetLastError(), "twiddle tables");
   }
   if (p->batched) {
-    build_batch_meta(p, p->ws, nsm);
+    try {
+      build_batch_meta(p, p->ws, nsm);
+    } catch (...) {
+      return fail(p, QPE_ERR_CUDA, "batched work lists: tensor map encoding failed");
+    }
     qpe_status st = upload_batch_meta(p);
     if (st != QPE_OK) return st;
     const char* forced = getenv("QPE_SQUARE_TILE");  // 8, 16 or 32: skip the autotuner

@@ -2,6 +2,7 @@
 // layout, and the kernel launchers the C ABI calls. Not part of the ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -121,6 +122,42 @@ struct FftPlan {
   FftPass p[kMaxPasses];
   int logr_list[kMaxPasses];  // digit widths from the top of m downwards
 };
+
+// Arguments of one QFT^-1 pass (fft_pass_kernel): a length-2^logr DFT over
+// the middle axis of the state viewed as [B][R][Q].
+struct FftArgs {
+  int logr;
+  int logw;    // W = 2^logw columns per CTA
+  int logq;    // Q = 2^logq
+  int logd;
+  int n;       // log2 of the transform length
+  int htw;
+  int logb;    // B = 2^logb blocks
+  int last;    // 1: no inter-pass twiddle
+  int tw_sh;   // log2(N / transform length): a shard's local transform reads the N-point tables
+  double scale;
+};
+
+// Digit widths of the passes, top of m first (position -> outcome order).
+struct Digits {
+  int count;
+  int logr[kMaxPasses];
+};
+
+// item index i with items[i].tile0 <= b < items[i + 1].tile0 (tile0 ascending):
+// the grouped kernels map a CTA to the work item it belongs to
+template <typename T>
+__device__ __forceinline__ int find_item(const T* items, int n, int64_t b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].tile0 <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
 
 // Device-side scalars of one instance (readout + error word).
 struct Scalars {
@@ -302,14 +339,104 @@ struct FinItem {
   int count, nmeas;
 };
 
+// Work items of the batched plain schedule (instances run together, one
+// launch per step): row 0 of each state, one doubling level, one QFT^-1 pass,
+// the histogram.
+template <typename C>
+struct InitItem {
+  C* S;
+  const double2* psi;
+  double scale;
+  int d, pad;
+};
+template <typename C>
+struct DblItem {  // rows [M, 2M) = rows [0, M) x P^T
+  C* S;
+  const C* P;
+  int64_t M;
+  int d, pad;
+  int64_t tile0;
+};
+template <typename C>
+struct FftItem {
+  C* X;
+  const C* lo;
+  const C* hi;
+  FftArgs a;
+  int64_t tile0;
+};
+template <typename C>
+struct RedItem {
+  const C* X;
+  double* hist;
+  Partial* parts;
+  int64_t N;
+  int logd, n;
+  Digits g;
+  int64_t tile0, nblk;
+};
+
 struct LevelLaunch {  // one grouped level launch
   int logd, mode;
   int arg_off, item_off, nitems;
   int64_t grid;
 };
 
+// One instance's doubling level on the tensor cores in a grouped launch: its
+// operand tensor maps (A hi / lo rows, B hi / lo embedding; 64-byte aligned in
+// global memory), output and error word.
+struct TcGemmItem {
+  CUtensorMap mAh, mAl, mBh, mBl;
+  float* D;
+  int64_t ldd, M;
+  int K, pad;
+  int* err;
+  const float* row_scale;
+  int64_t tile0;
+};
+// One instance's operand split for the grouped tensor-core level: the rows
+// [0, rows) of its state into hi / lo (warp per row), and U^(2^j)'s embedding.
+struct TcSplitItem {
+  const float* S;
+  void* hi;
+  void* lo;
+  float* inv_scale;
+  const double2* P;
+  void* bhi;
+  void* blo;
+  int64_t rows, row0;  // rows of A, first row in the launch's numbering
+  int64_t e0;          // first embedding element in the launch's numbering
+  int width, d;
+  int64_t tile0;       // = row0 (for find_item over rows)
+};
+struct TcRound {  // one level j across the tensor-core instances
+  int j, item_off, nitems;
+  int64_t rows, elems, tiles;
+};
+
+struct DblRound {  // one grouped doubling launch: level j of the items of one tile class
+  int j, dclass, item_off, nitems;
+  int64_t tiles;
+};
+struct FftRound {  // one grouped QFT^-1 pass launch
+  int item_off, nitems;
+  int64_t blocks;
+  size_t smem;
+};
+
 struct BatchMeta {
   int maxn = 0;
+  // plain instances (Nmat > 6, or QPE_FLAG_PLAIN), run together step by step
+  std::vector<char> init_items, dbl_items, fft_items, red_items;  // typed by the plan's precision
+  std::vector<DblRound> dbl_rounds;
+  std::vector<TcSplitItem> tc_split;  // tensor-core levels (j >= 7, 2d >= 128), grouped per level
+  std::vector<TcGemmItem> tc_gemm;
+  std::vector<TcRound> tc_rounds;
+  std::vector<FftRound> fft_rounds;
+  std::vector<FinItem> fin_plain;
+  int ninit = 0, nred = 0, maxn_plain = 0;
+  int64_t red_blocks = 0;
+  size_t off_init = 0, off_dbl = 0, off_fft = 0, off_red = 0, off_finp = 0, off_tcsp = 0, off_tcgm = 0;
   // squaring: items of step k at [sq_begin[k], sq_begin[k] + sq_count[k])
   std::vector<SqItem> sq;
   std::vector<int> sq_begin, sq_count;
@@ -381,6 +508,12 @@ template <typename C> int launch_sweep(const Instance& in, char* ws, bool gate_m
 int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t s, int pow_off = 0);
 // a bounded wait that runs out after `polls` polls (records QPE_ERR_TIMEOUT)
 int launch_wait_expiry(const Instance& in, char* ws, uint32_t polls, cudaStream_t s);
+// grouped tensor-core level (batched plans): one instance's items, its CTA
+// count, and the two launches (operand splits, GEMM) for all items
+bool tc_level_items(const Instance& in, char* ws, int prec, int j, TcSplitItem* sp, TcGemmItem* gm);
+int64_t tc_level_tiles(const Instance& in, int j);
+int launch_tc_level_grouped(int prec, const TcSplitItem* sp, const TcGemmItem* gm, int nitems, int64_t rows,
+                            int64_t elems, int64_t tiles, cudaStream_t s);
 size_t oz_square_bytes(int nmat);
 int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStream_t s);
 size_t tc_split_bytes(int prec, int nmat, int nmeas);
@@ -410,6 +543,20 @@ std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 bool level_sharded(const Instance& in, int li);
 cudaError_t configure_level_kernels();
 template <typename C> int level_occupancy(int logd, int r);
+
+// The batched plain schedule's grouped launches (one per step across instances).
+template <typename C> int launch_init_grouped(const InitItem<C>* items, int nitems, cudaStream_t s);
+template <typename C>
+int launch_doubling_grouped(const DblItem<C>* items, int nitems, int64_t tiles, int dclass, cudaStream_t s);
+template <typename C>
+int launch_fft_grouped(const FftItem<C>* items, int nitems, int64_t blocks, size_t smem, cudaStream_t s);
+template <typename C> int launch_reduce_grouped(const RedItem<C>* items, int nitems, int64_t blocks, cudaStream_t s);
+// pass i's arguments, CTA count and shared memory; the plain histogram's CTA
+// count; the doubling GEMM's row / column tile for a target dimension d
+FftArgs fft_pass_args(const Instance& in, int i, int64_t* blocks, size_t* smem, size_t esize);
+Digits fft_digits(const FftPlan& f);
+int64_t reduce_blocks(const Instance& in);
+void doubling_tile(int d, int* BM, int* BN);
 
 // Host helpers shared with the ABI layer.
 int64_t fft_position_to_y(const FftPlan& f, int nmeas, int64_t p);

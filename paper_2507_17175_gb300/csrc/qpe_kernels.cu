@@ -223,17 +223,16 @@ struct GateRows {  // gate k: the r-th row with bit k set, in place
 // whole rows, so in-place updates (GateRows) are safe: every read of a row
 // happens before the CTA's epilogue writes it.
 template <typename C, int BM, int BN, int BK, int TM, int TN, typename Rows>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    rows_times_pt_kernel(C* __restrict__ S, const C* __restrict__ P, int64_t M, int d, Rows rows) {
-  pdl_begin();
+__device__ __forceinline__ void rows_times_pt_tile(C* __restrict__ S, const C* __restrict__ P, int64_t M, int d,
+                                                   Rows rows, int64_t bx, int by) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TCOLS = BN / TN;
   __shared__ C As[BK][BM + 1];
   __shared__ C Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tc = tid % TCOLS, tr = tid / TCOLS;
-  const int64_t r0 = (int64_t)blockIdx.x * BM;
-  const int c0 = blockIdx.y * BN;
+  const int64_t r0 = bx * BM;
+  const int c0 = by * BN;
   C acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -277,6 +276,26 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+template <typename C, int BM, int BN, int BK, int TM, int TN, typename Rows>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    rows_times_pt_kernel(C* __restrict__ S, const C* __restrict__ P, int64_t M, int d, Rows rows) {
+  pdl_begin();
+  rows_times_pt_tile<C, BM, BN, BK, TM, TN, Rows>(S, P, M, d, rows, blockIdx.x, blockIdx.y);
+}
+
+// One doubling level of every listed instance (batched plans): CTAs map to
+// (instance, row tile, column tile) through tile0, the item's first CTA.
+template <typename C, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    doubling_grouped_kernel(const DblItem<C>* __restrict__ items, int nitems) {
+  pdl_begin();
+  const DblItem<C> it = items[find_item(items, nitems, blockIdx.x)];
+  const int64_t t = blockIdx.x - it.tile0;
+  const int nby = it.d / BN;
+  rows_times_pt_tile<C, BM, BN, BK, TM, TN, DoublingRows>(it.S, it.P, it.M, it.d, DoublingRows{it.M}, t / nby,
+                                                          (int)(t % nby));
+}
+
 // ------------------------------------------------------------------ fft
 // One decimation-in-frequency pass over the middle axis of X viewed as
 // [B][R][Q] (Q = L * d contiguous elements): for each block and each of the Q
@@ -284,18 +303,6 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // the twiddle omega_(R L)^(b y) with b = column / d the row offset inside the
 // block, stored in place at digit y. Each CTA stages an R x W slab in shared
 // memory and runs log2(R) radix-2 stages on it.
-struct FftArgs {
-  int logr;
-  int logw;    // W = 2^logw columns per CTA
-  int logq;    // Q = 2^logq
-  int logd;
-  int n;       // log2 of the transform length
-  int htw;
-  int logb;    // B = 2^logb blocks
-  int last;    // 1: no inter-pass twiddle
-  int tw_sh;   // log2(N / transform length): a shard's local transform reads the N-point tables
-  double scale;
-};
 
 __device__ __forceinline__ int bitrev(int x, int bits) { return bits ? (__brev(x) >> (32 - bits)) : 0; }
 
@@ -327,16 +334,14 @@ __device__ __forceinline__ void fft_group(C* tile, const C* twp, int W, int w, i
 }
 
 template <typename C>
-__global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const C* __restrict__ tw_lo,
-                                                       const C* __restrict__ tw_hi, FftArgs a) {
-  pdl_begin();
+__device__ __forceinline__ void fft_pass_block(C* __restrict__ X, const C* __restrict__ tw_lo,
+                                               const C* __restrict__ tw_hi, const FftArgs& a, int64_t bid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tile = reinterpret_cast<C*>(smem_raw);
   using R_t = typename real_of<C>::type;
   const int R = 1 << a.logr;
   const int W = 1 << a.logw;
   const int64_t slices_log = a.logq - a.logw;
-  const int64_t bid = blockIdx.x;
   const int64_t blk = bid >> slices_log;
   const int64_t qs = bid & ((int64_t(1) << slices_log) - 1);
   C* base = X + (blk << (a.logr + a.logq)) + (qs << a.logw);
@@ -401,11 +406,22 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const 
   }
 }
 
+template <typename C>
+__global__ void __launch_bounds__(256) fft_pass_kernel(C* __restrict__ X, const C* __restrict__ tw_lo,
+                                                       const C* __restrict__ tw_hi, FftArgs a) {
+  pdl_begin();
+  fft_pass_block<C>(X, tw_lo, tw_hi, a, blockIdx.x);
+}
+
+// One QFT^-1 pass of every listed instance (each item its own pass arguments).
+template <typename C>
+__global__ void __launch_bounds__(256) fft_pass_grouped_kernel(const FftItem<C>* __restrict__ items, int nitems) {
+  pdl_begin();
+  const int i = find_item(items, nitems, blockIdx.x);
+  fft_pass_block<C>(items[i].X, items[i].lo, items[i].hi, items[i].a, blockIdx.x - items[i].tile0);
+}
+
 // --------------------------------------------------------------- reduce
-struct Digits {
-  int count;
-  int logr[kMaxPasses];
-};
 
 // Position p of the in-place DIF output -> outcome y: the pass that ran
 // first (top bits of p) produced the least significant digit of y.
@@ -434,18 +450,17 @@ __device__ __forceinline__ int64_t y_to_pos(const Digits& g, int n, int64_t y) {
 }
 
 template <typename C>
-__global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, double* __restrict__ hist,
-                                                     Partial* __restrict__ parts, int64_t N, int logd, int n,
-                                                     Digits g, double scale) {
-  pdl_begin();
+__device__ __forceinline__ void reduce_block(const C* __restrict__ X, double* __restrict__ hist,
+                                             Partial* __restrict__ part_out, int64_t N, int logd, int n,
+                                             const Digits& g, double scale, int64_t bidx, int64_t nblk) {
   const int d = 1 << logd;
   const int lpr = d < 32 ? d : 32;  // lanes per row
   const int rpw = 32 / lpr;         // rows per warp step
   const int per = d / lpr;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * 8 + warp;
-  const int64_t tw = (int64_t)gridDim.x * 8;
+  const int64_t gw = bidx * 8 + warp;
+  const int64_t tw = nblk * 8;
   double best = -1.0, wsum = 0.0, psum = 0.0;
   int64_t by = INT64_MAX;
   // complex64 rows narrower than a warp (many rows): the per-row readout stays
@@ -546,7 +561,37 @@ __global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, do
       r.wsum += sp[w].wsum;
       r.psum += sp[w].psum;
     }
-    parts[blockIdx.x] = r;
+    *part_out = r;
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) reduce_kernel(const C* __restrict__ X, double* __restrict__ hist,
+                                                     Partial* __restrict__ parts, int64_t N, int logd, int n,
+                                                     Digits g, double scale) {
+  pdl_begin();
+  reduce_block<C>(X, hist, parts + blockIdx.x, N, logd, n, g, scale, blockIdx.x, gridDim.x);
+}
+
+// The histogram and readout partials of every listed instance: item i owns
+// CTAs [tile0, tile0 + nblk) and its own partial slots.
+template <typename C>
+__global__ void __launch_bounds__(256) reduce_grouped_kernel(const RedItem<C>* __restrict__ items, int nitems) {
+  pdl_begin();
+  const int i = find_item(items, nitems, blockIdx.x);
+  const RedItem<C>& it = items[i];
+  const int64_t b = blockIdx.x - it.tile0;
+  reduce_block<C>(it.X, it.hist, it.parts + b, it.N, it.logd, it.n, it.g, 1.0, b, it.nblk);
+}
+
+// Row 0 of every listed instance's state = 2^(-n/2) psi (one CTA each).
+template <typename C>
+__global__ void init_grouped_kernel(const InitItem<C>* __restrict__ items) {
+  pdl_begin();
+  const InitItem<C> it = items[blockIdx.x];
+  for (int i = threadIdx.x; i < it.d; i += blockDim.x) {
+    const double2 v = it.psi[i];
+    it.S[i] = to_c(make_double2(v.x * it.scale, v.y * it.scale), (C*)nullptr);
   }
 }
 
@@ -808,7 +853,7 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, i
       return -1;
     for (int j = 0; j < in.nmeas - sh; ++j) {
       int r;
-      if (tc && (int64_t(1) << j) >= 128)
+      if (tc && in.d >= 32 && (int64_t(1) << j) >= 128)
         r = launch_tc_level(in, ws, prec, j, s, sh);
       else
         r = launch_rows_times_pt<C>(S, P + (j + sh) * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j},
@@ -829,7 +874,7 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, i
       }
     } else if (gate_mode)
       r = launch_rows_times_pt<C>(S, P + j * dd, in.N / 2, (int)in.d, GateRows{j}, s);
-    else if (tc && (int64_t(1) << j) >= 128)
+    else if (tc && in.d >= 32 && (int64_t(1) << j) >= 128)
       r = launch_tc_level(in, ws, prec, j, s);  // tensor cores once a level fills 128-row tiles
     else
       r = launch_rows_times_pt<C>(S, P + j * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j}, s);
@@ -876,33 +921,97 @@ int64_t fft_position_to_y(const FftPlan& f, int nmeas, int64_t p) {
   return y;
 }
 
+FftArgs fft_pass_args(const Instance& in, int i, int64_t* blocks, size_t* smem, size_t esize) {
+  const FftPass& p = in.fft.p[i];
+  FftArgs a;
+  a.logr = p.logr;
+  a.logw = ilog2(p.W);
+  a.logq = ilog2(p.Q);
+  a.logd = in.nmat;
+  a.n = in.nmeas - in.shard_log;  // a sharded plan transforms its N / 2^shard_log local rows
+  a.tw_sh = in.shard_log;
+  a.htw = in.htw;
+  a.logb = ilog2(p.B);
+  a.last = (i == in.fft.passes - 1);
+  a.scale = a.last ? 1.0 / sqrt(ldexp(1.0, in.nmeas)) : 1.0;  // QFT^-1 normalisation 2^(-n/2) in the last pass
+  *blocks = p.B * (p.Q / p.W);
+  *smem = ((size_t)(int64_t(1) << p.logr) * p.W + ((size_t)1 << p.logr) / 2) * esize;
+  return a;
+}
+
 template <typename C>
 int launch_fft(const Instance& in, char* ws, cudaStream_t s) {
   C* X = at<C>(ws, in.off_state);
   const C* lo = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_lo64) : at<C>(ws, in.off_tw_lo32);
   const C* hi = (sizeof(C) == 16) ? at<C>(ws, in.off_tw_hi64) : at<C>(ws, in.off_tw_hi32);
-  const double final_scale = 1.0 / sqrt(ldexp(1.0, in.nmeas));  // QFT^-1 normalisation 2^(-n/2)
   int launches = 0;
   for (int i = 0; i < in.fft.passes; ++i) {
-    const FftPass& p = in.fft.p[i];
-    FftArgs a;
-    a.logr = p.logr;
-    a.logw = ilog2(p.W);
-    a.logq = ilog2(p.Q);
-    a.logd = in.nmat;
-    a.n = in.nmeas - in.shard_log;  // a sharded plan transforms its N / 2^shard_log local rows
-    a.tw_sh = in.shard_log;
-    a.htw = in.htw;
-    a.logb = ilog2(p.B);
-    a.last = (i == in.fft.passes - 1);
-    a.scale = a.last ? final_scale : 1.0;
-    const int64_t blocks = p.B * (p.Q / p.W);
-    const size_t smem = ((size_t)(int64_t(1) << p.logr) * p.W + ((size_t)1 << p.logr) / 2) * sizeof(C);
+    int64_t blocks = 0;
+    size_t smem = 0;
+    const FftArgs a = fft_pass_args(in, i, &blocks, &smem, sizeof(C));
     if (launch_k(fft_pass_kernel<C>, dim3((unsigned)blocks), dim3(256), smem, s, X, lo, hi, a) != cudaSuccess)
       return -1;
     ++launches;
   }
   return launches;
+}
+
+Digits fft_digits(const FftPlan& f) { return digits_of(f); }
+
+int64_t reduce_blocks(const Instance& in) {
+  const int64_t rows_per_block_step = 8 * (32 / (in.d < 32 ? in.d : 32));
+  const int64_t b = std::min<int64_t>(kReduceBlocks, (in.N + rows_per_block_step - 1) / rows_per_block_step);
+  return b < 1 ? 1 : b;
+}
+
+void doubling_tile(int d, int* BM, int* BN) {
+  switch (d) {
+    case 2: *BM = 256; *BN = 2; break;
+    case 4: *BM = 256; *BN = 4; break;
+    case 8: *BM = 256; *BN = 8; break;
+    case 16: *BM = 256; *BN = 16; break;
+    case 32: *BM = 128; *BN = 32; break;
+    default: *BM = 64; *BN = 64; break;
+  }
+}
+
+template <typename C>
+int launch_init_grouped(const InitItem<C>* items, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return 0;
+  return launch_k(init_grouped_kernel<C>, dim3((unsigned)nitems), dim3(256), 0, s, items) == cudaSuccess ? 1 : -1;
+}
+
+// one doubling round for the items of one tile class (d, or 64 for d >= 64)
+template <typename C>
+int launch_doubling_grouped(const DblItem<C>* items, int nitems, int64_t tiles, int dclass, cudaStream_t s) {
+  if (nitems <= 0) return 0;
+  cudaError_t e;
+  switch (dclass) {
+    case 2: e = launch_k(doubling_grouped_kernel<C, 256, 2, 2, 2, 1>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+    case 4: e = launch_k(doubling_grouped_kernel<C, 256, 4, 4, 4, 1>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+    case 8: e = launch_k(doubling_grouped_kernel<C, 256, 8, 8, 4, 2>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+    case 16: e = launch_k(doubling_grouped_kernel<C, 256, 16, 8, 4, 4>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+    case 32: e = launch_k(doubling_grouped_kernel<C, 128, 32, 8, 4, 4>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+    default: e = launch_k(doubling_grouped_kernel<C, 64, 64, 8, 4, 4>, dim3((unsigned)tiles), dim3(256), 0, s, items, nitems); break;
+  }
+  return e == cudaSuccess ? 1 : -1;
+}
+
+template <typename C>
+int launch_fft_grouped(const FftItem<C>* items, int nitems, int64_t blocks, size_t smem, cudaStream_t s) {
+  if (nitems <= 0) return 0;
+  return launch_k(fft_pass_grouped_kernel<C>, dim3((unsigned)blocks), dim3(256), smem, s, items, nitems) ==
+                 cudaSuccess
+             ? 1
+             : -1;
+}
+
+template <typename C>
+int launch_reduce_grouped(const RedItem<C>* items, int nitems, int64_t blocks, cudaStream_t s) {
+  if (nitems <= 0) return 0;
+  return launch_k(reduce_grouped_kernel<C>, dim3((unsigned)blocks), dim3(256), 0, s, items, nitems) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 template <typename C>
@@ -980,6 +1089,14 @@ template int launch_sweep<double2>(const Instance&, char*, bool, cudaStream_t, i
 template int launch_fft<float2>(const Instance&, char*, cudaStream_t);
 template int launch_fft<double2>(const Instance&, char*, cudaStream_t);
 template int launch_reduce<float2>(const Instance&, char*, cudaStream_t);
+#define QPE_GROUPED_INST(C)                                                                             \
+  template int launch_init_grouped<C>(const InitItem<C>*, int, cudaStream_t);                          \
+  template int launch_doubling_grouped<C>(const DblItem<C>*, int, int64_t, int, cudaStream_t);         \
+  template int launch_fft_grouped<C>(const FftItem<C>*, int, int64_t, size_t, cudaStream_t);           \
+  template int launch_reduce_grouped<C>(const RedItem<C>*, int, int64_t, cudaStream_t);
+QPE_GROUPED_INST(float2)
+QPE_GROUPED_INST(double2)
+#undef QPE_GROUPED_INST
 template int launch_shard_pack<float2>(const Instance&, char*, cudaStream_t);
 template int launch_shard_pack<double2>(const Instance&, char*, cudaStream_t);
 template int launch_shard_combine<float2>(const Instance&, char*, cudaStream_t, int*);

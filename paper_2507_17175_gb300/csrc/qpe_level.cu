@@ -1016,6 +1016,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
     const int dw = warp - 4;
     const int set = dw >> 2, lg = warp & 3;
     const int row = lg * 32 + lane;
+    const float pscale = (float)a.pscale;  // 1/N^2, a power of two
     HistAcc32 h32;
     int it = 0;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
@@ -1088,7 +1089,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) level_tc_top_kernel(TcTopArgs a
 #pragma unroll
         for (int yb = 0; yb < kTcL; ++yb) {
           const int64_t yl = j + ((int64_t)yb << lna);
-          const float pv = acc[yb] * (float)a.pscale;  // pscale = 1/N^2, a power of two
+          const float pv = acc[yb] * pscale;
           a.hist[yl] = widen_nonneg(pv);
           h32.add(pv, a.rk + (yl << a.sh));
         }

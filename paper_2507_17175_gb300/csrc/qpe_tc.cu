@@ -79,12 +79,11 @@ constexpr int kMS = 2;   // hi.hi drains per K-block (every 2 MMA instructions)
 constexpr int kTcDrainWarps = 8;  // 4 lane quarters x 2 column halves
 
 template <int KIND, int BN>
-__global__ void __launch_bounds__(64 + 32 * kTcDrainWarps, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
-                   const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
-                   float* __restrict__ D, int64_t ldd, int64_t M, int K, int* __restrict__ err,
-                   const float* __restrict__ row_scale) {
-  pdl_begin();
+__device__ __forceinline__ void tc_gemm_tile(const CUtensorMap* mapAhi, const CUtensorMap* mapAlo,
+                                             const CUtensorMap* mapBhi, const CUtensorMap* mapBlo,
+                                             float* __restrict__ D, int64_t ldd, int64_t M, int K,
+                                             int* __restrict__ err, const float* __restrict__ row_scale,
+                                             int64_t bid) {
   constexpr int ESZ = KIND == kTcTF32 ? 4 : 2;
   constexpr int BK = 128 / ESZ;       // K elements per 128-byte swizzle row
   constexpr int A_BYTES = kBM * 128;  // 16 KiB
@@ -105,7 +104,6 @@ __global__ void __launch_bounds__(64 + 32 * kTcDrainWarps, 1)
   const int n_tiles = (int)(ldd / BN);
   int64_t m_tile, n_tile;
   {
-    const int64_t bid = blockIdx.x;
     const int64_t per_group = (int64_t)kGroupM * n_tiles;
     const int64_t g = bid / per_group;
     const int64_t first = g * kGroupM;
@@ -156,10 +154,10 @@ __global__ void __launch_bounds__(64 + 32 * kTcDrainWarps, 1)
         if (*((volatile int*)&fail)) break;
         unsigned char* sa = ring + st * STAGE_BYTES;
         mbar_expect_tx(&full_bar[st], STAGE_BYTES);
-        tma_load_2d(sa, &mapAhi, &full_bar[st], kb * BK, (int)m0);
-        tma_load_2d(sa + A_BYTES, &mapAlo, &full_bar[st], kb * BK, (int)m0);
-        tma_load_2d(sa + 2 * A_BYTES, &mapBhi, &full_bar[st], kb * BK, n0);
-        tma_load_2d(sa + 2 * A_BYTES + B_BYTES, &mapBlo, &full_bar[st], kb * BK, n0);
+        tma_load_2d(sa, mapAhi, &full_bar[st], kb * BK, (int)m0);
+        tma_load_2d(sa + A_BYTES, mapAlo, &full_bar[st], kb * BK, (int)m0);
+        tma_load_2d(sa + 2 * A_BYTES, mapBhi, &full_bar[st], kb * BK, n0);
+        tma_load_2d(sa + 2 * A_BYTES + B_BYTES, mapBlo, &full_bar[st], kb * BK, n0);
       }
     }
   } else if (warp == 1) {
@@ -290,6 +288,44 @@ __global__ void __launch_bounds__(64 + 32 * kTcDrainWarps, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(4 * BN))
                  : "memory");
   }
+}
+
+template <int KIND, int BN>
+__global__ void __launch_bounds__(64 + 32 * kTcDrainWarps, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
+                   const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
+                   float* __restrict__ D, int64_t ldd, int64_t M, int K, int* __restrict__ err,
+                   const float* __restrict__ row_scale) {
+  pdl_begin();
+  tc_gemm_tile<KIND, BN>(&mapAhi, &mapAlo, &mapBhi, &mapBlo, D, ldd, M, K, err, row_scale, blockIdx.x);
+  pdl_trigger();
+}
+
+// Acquire a tensor map that the host wrote into global memory before the
+// launch, for the TMA (tensor-map) proxy.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
+               : "memory");
+}
+
+// One doubling level on the tensor cores for every listed instance (batched
+// plans): item i owns CTAs [tile0, tile0 + tiles) of the launch; its four
+// operand tensor maps live in the item (global memory, written at bind).
+template <int KIND, int BN>
+__global__ void __launch_bounds__(64 + 32 * kTcDrainWarps, 1)
+    tc_gemm_grouped_kernel(const TcGemmItem* __restrict__ items, int nitems) {
+  pdl_begin();
+  const int i = find_item(items, nitems, blockIdx.x);
+  const TcGemmItem* it = items + i;
+  if (threadIdx.x == 0) {
+    tensormap_acquire(&it->mAh);
+    tensormap_acquire(&it->mAl);
+    tensormap_acquire(&it->mBh);
+    tensormap_acquire(&it->mBl);
+  }
+  __syncthreads();
+  tc_gemm_tile<KIND, BN>(&it->mAh, &it->mAl, &it->mBh, &it->mBl, it->D, it->ldd, it->M, it->K, it->err,
+                         it->row_scale, blockIdx.x - it->tile0);
   pdl_trigger();
 }
 
@@ -316,13 +352,11 @@ __global__ void split_rows_tf32_kernel(const float* __restrict__ src, float* __r
 // A rows -> fp16 hi / lo after scaling each row by 2^e so that its largest
 // |entry| lies in [2^14, 2^15); inv_scale[row] = 2^-(e + 14) undoes both
 // operand scales. One warp per row (width floats, a multiple of 4).
-__global__ void split_rows_fp16_kernel(const float* __restrict__ src, __half* __restrict__ hi,
-                                       __half* __restrict__ lo, float* __restrict__ inv_scale, int64_t rows,
-                                       int width) {
-  pdl_begin();
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+// one row (width floats) by one warp
+__device__ __forceinline__ void split_row_fp16(const float* __restrict__ src, __half* __restrict__ hi,
+                                               __half* __restrict__ lo, float* __restrict__ inv_scale, int64_t r,
+                                               int width, int lane) {
+  {
     const float* row = src + r * width;
     float mx = 0.f;
     for (int c = lane * 4; c < width; c += 128) {
@@ -346,33 +380,91 @@ __global__ void split_rows_fp16_kernel(const float* __restrict__ src, __half* __
       }
     }
   }
+}
+
+__global__ void split_rows_fp16_kernel(const float* __restrict__ src, __half* __restrict__ hi,
+                                       __half* __restrict__ lo, float* __restrict__ inv_scale, int64_t rows,
+                                       int width) {
+  pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps)
+    split_row_fp16(src, hi, lo, inv_scale, r, width, lane);
   pdl_trigger();
 }
 
 // P (d x d complex128) -> real embedding B (2d x 2d, n-major) split hi / lo
+// element e of P's real embedding (2d x 2d, n-major) split into hi / lo
+template <int KIND>
+__device__ __forceinline__ void embed_split_elem(const double2* __restrict__ P, void* __restrict__ hi,
+                                                 void* __restrict__ lo, int d, int64_t e) {
+  const int64_t n2 = 2 * (int64_t)d;
+  const int64_t n = e / n2, kk = e - n * n2;
+  const int64_t i = n >> 1, k = kk >> 1;
+  const double2 p = P[i * d + k];
+  const int c = (int)(n & 1), cp = (int)(kk & 1);
+  // [[re, -im], [im, re]]
+  const double v = c == 0 ? (cp == 0 ? p.x : -p.y) : (cp == 0 ? p.y : p.x);
+  if constexpr (KIND == kTcTF32) {
+    const float h = tf32_round((float)v);
+    reinterpret_cast<float*>(hi)[e] = h;
+    reinterpret_cast<float*>(lo)[e] = tf32_round((float)(v - (double)h));
+  } else {
+    static_assert(KIND == kTcFP16, "gate GEMM operands are tf32 or fp16");
+    const double vs = v * 16384.0;  // 2^14, exact
+    const __half h = __float2half_rn((float)vs);
+    reinterpret_cast<__half*>(hi)[e] = h;
+    reinterpret_cast<__half*>(lo)[e] = __float2half_rn((float)(vs - (double)__half2float(h)));
+  }
+}
+
 template <int KIND>
 __global__ void embed_split_kernel(const double2* __restrict__ P, void* __restrict__ hi, void* __restrict__ lo,
                                    int d) {
   pdl_begin();
   const int64_t n2 = 2 * (int64_t)d;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2 * n2; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = e / n2, kk = e - n * n2;
-    const int64_t i = n >> 1, k = kk >> 1;
-    const double2 p = P[i * d + k];
-    const int c = (int)(n & 1), cp = (int)(kk & 1);
-    // [[re, -im], [im, re]]
-    const double v = c == 0 ? (cp == 0 ? p.x : -p.y) : (cp == 0 ? p.y : p.x);
-    if constexpr (KIND == kTcTF32) {
-      const float h = tf32_round((float)v);
-      reinterpret_cast<float*>(hi)[e] = h;
-      reinterpret_cast<float*>(lo)[e] = tf32_round((float)(v - (double)h));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2 * n2; e += (int64_t)gridDim.x * blockDim.x)
+    embed_split_elem<KIND>(P, hi, lo, d, e);
+  pdl_trigger();
+}
+
+// The operand splits of one tensor-core level for every listed instance:
+// warps take the A rows of all items (row0 numbering), threads the embedding
+// elements of all items (e0 numbering).
+template <int KIND>
+__global__ void split_grouped_kernel(const TcSplitItem* __restrict__ items, int nitems, int64_t rows, int64_t elems) {
+  pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const TcSplitItem& it = items[find_item(items, nitems, r)];
+    const int64_t lr = r - it.row0;
+    if constexpr (KIND == kTcFP16) {
+      split_row_fp16(it.S, static_cast<__half*>(it.hi), static_cast<__half*>(it.lo), it.inv_scale, lr, it.width,
+                     lane);
     } else {
-      static_assert(KIND == kTcFP16, "gate GEMM operands are tf32 or fp16");
-      const double vs = v * 16384.0;  // 2^14, exact
-      const __half h = __float2half_rn((float)vs);
-      reinterpret_cast<__half*>(hi)[e] = h;
-      reinterpret_cast<__half*>(lo)[e] = __float2half_rn((float)(vs - (double)__half2float(h)));
+      const float* row = it.S + lr * it.width;
+      float* h = static_cast<float*>(it.hi) + lr * it.width;
+      float* l = static_cast<float*>(it.lo) + lr * it.width;
+      for (int c = lane; c < it.width; c += 32) {
+        const float x = row[c];
+        const float hv = tf32_round(x);
+        h[c] = hv;
+        l[c] = tf32_round(x - hv);
+      }
     }
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < elems; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo_i = 0, hi_i = nitems - 1;  // item with e0 <= e
+    while (lo_i < hi_i) {
+      const int mid = (lo_i + hi_i + 1) >> 1;
+      if (items[mid].e0 <= e)
+        lo_i = mid;
+      else
+        hi_i = mid - 1;
+    }
+    const TcSplitItem& it = items[lo_i];
+    embed_split_elem<KIND>(it.P, it.bhi, it.blo, it.d, e - it.e0);
   }
   pdl_trigger();
 }
@@ -748,6 +840,12 @@ cudaError_t configure_tc_kernels() {
   QPE_TC_ATTR(kTcFP16, 64)
   QPE_TC_ATTR(kTcFP16, 128)
 #undef QPE_TC_ATTR
+  e = cudaFuncSetAttribute(tc_gemm_grouped_kernel<kTcTF32, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem<kTcTF32, 128>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tc_gemm_grouped_kernel<kTcFP16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem<kTcFP16, 128>());
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(oz_square_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem<64>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(oz_square_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -867,6 +965,65 @@ int launch_tc_level(const Instance& in, char* ws, int prec, int j, cudaStream_t 
 #undef QPE_TC_LAUNCH
   if (e != cudaSuccess) return -1;
   return launches + 1;
+}
+
+// ------------------------------------------------ grouped tensor-core level
+// Fills the operand buffers, tensor maps and numbering of instance `in`'s
+// level j for a grouped launch (tensor maps only when ws is a bound workspace).
+bool tc_level_items(const Instance& in, char* ws, int prec, int j, TcSplitItem* sp, TcGemmItem* gm) {
+  const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : kTcFP16;
+  const size_t esz = kind == kTcTF32 ? 4 : 2;
+  const int64_t half = int64_t(1) << j;
+  const int64_t d2 = 2 * in.d;
+  char* Ahi = ws + in.off_tcsplit;
+  char* Alo = Ahi + (size_t)(int64_t(1) << (in.nmeas - 1)) * d2 * esz;
+  char* Bhi = Alo + (size_t)(int64_t(1) << (in.nmeas - 1)) * d2 * esz;
+  char* Blo = Bhi + (size_t)d2 * d2 * esz;
+  float* inv_scale = reinterpret_cast<float*>(Blo + (size_t)d2 * d2 * esz);
+  float* S = reinterpret_cast<float*>(ws + in.off_state);
+  sp->S = S;
+  sp->hi = Ahi;
+  sp->lo = Alo;
+  sp->inv_scale = inv_scale;
+  sp->P = reinterpret_cast<const double2*>(ws + in.off_pow64) + (int64_t)j * in.d * in.d;
+  sp->bhi = Bhi;
+  sp->blo = Blo;
+  sp->rows = half;
+  sp->width = (int)d2;
+  sp->d = (int)in.d;
+  gm->D = S + half * d2;
+  gm->ldd = d2;
+  gm->M = half;
+  gm->K = (int)d2;
+  gm->err = reinterpret_cast<int*>(ws + in.off_err);
+  gm->row_scale = inv_scale;
+  if (!ws) return true;
+  return make_map(&gm->mAh, Ahi, kind, half, d2, kBM) && make_map(&gm->mAl, Alo, kind, half, d2, kBM) &&
+         make_map(&gm->mBh, Bhi, kind, d2, d2, 128) && make_map(&gm->mBl, Blo, kind, d2, d2, 128);
+}
+
+int64_t tc_level_tiles(const Instance& in, int j) {
+  const int64_t half = int64_t(1) << j;
+  return ((half + kBM - 1) / kBM) * (2 * in.d / 128);
+}
+
+// split + embed of every item, then the GEMM of every item (BN = 128: every
+// grouped instance has 2d >= 128)
+int launch_tc_level_grouped(int prec, const TcSplitItem* sp, const TcGemmItem* gm, int nitems, int64_t rows,
+                            int64_t elems, int64_t tiles, cudaStream_t s) {
+  if (nitems <= 0) return 0;
+  const int kind = prec == QPE_C64_TF32X3 ? kTcTF32 : kTcFP16;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((elems + 255) / 256, 152 * 16));
+  cudaError_t e = kind == kTcTF32 ? launch_k(split_grouped_kernel<kTcTF32>, dim3(blocks), dim3(256), 0, s, sp, nitems,
+                                             rows, elems)
+                                  : launch_k(split_grouped_kernel<kTcFP16>, dim3(blocks), dim3(256), 0, s, sp, nitems,
+                                             rows, elems);
+  if (e != cudaSuccess) return -1;
+  e = kind == kTcTF32 ? launch_k(tc_gemm_grouped_kernel<kTcTF32, 128>, dim3((unsigned)tiles),
+                                 dim3(64 + 32 * kTcDrainWarps), tc_smem<kTcTF32, 128>(), s, gm, nitems)
+                      : launch_k(tc_gemm_grouped_kernel<kTcFP16, 128>, dim3((unsigned)tiles),
+                                 dim3(64 + 32 * kTcDrainWarps), tc_smem<kTcFP16, 128>(), s, gm, nitems);
+  return e == cudaSuccess ? 2 : -1;
 }
 
 // ------------------------------------------- expiry of a bounded wait
