@@ -177,19 +177,24 @@ qpe_status qpe_plan(const qpe_plan_desc* desc, size_t* workspace_bytes, qpe_plan
 
 /*
  * qpe_plan_batched: one plan for `count` independent problems of uneven
- * nmat/nmeas (descs[i]; all with the same prec and flags; GATE_SWEEP and
- * TIMING are not available here, QPE_ERR_UNSUPPORTED). Instances are
- * addressed by index 0..count-1 in qpe_load / qpe_probs / qpe_state. A run
- * groups the work across instances: one launch per U^(2^k) squaring step for
- * every instance that needs it, and for nmat <= 6 grouped table, level and
- * readout launches whose CTAs walk a work list of (instance, level, column
- * group, pencil range) items built at qpe_bind; nmat > 6 instances run the
- * plain schedule one after another in the same stream (and graph). Under the
- * split precisions (QPE_C64_FP16X2 / TF32X3) instances with
- * nmat <= 6 keep the fused complex64 schedule and the plain instances run
- * their gate GEMMs on the tensor cores, so any nmat is accepted; with
- * QPE_FLAG_SQUARE_TC the instances with d >= 256 square on the tensor cores.
- * Only whole runs (qpe_run) are supported. Host only, like qpe_plan.
+ * nmat/nmeas (descs[i]; all with the same prec and flags; GATE_SWEEP is not
+ * available here, QPE_ERR_UNSUPPORTED; TIMING gives the coarse split of
+ * qpe_stage_times). Instances are addressed by index 0..count-1 in qpe_load /
+ * qpe_probs / qpe_state. A run groups the work across instances: every launch
+ * covers one step for every instance that needs it, its CTAs mapped to
+ * (instance, tile) through work lists built at qpe_bind and kept in the
+ * workspace. Steps: each U^(2^k) squaring (FP64 units; with
+ * QPE_FLAG_SQUARE_TC the instances with d >= 256 on the tensor cores, their
+ * digit-slice tensor maps in the work list); for nmat <= 6 the fused tables,
+ * levels and readouts; for the plain instances (nmat > 6, or QPE_FLAG_PLAIN)
+ * row 0, each doubling level (CUDA cores, one launch per tile class; under
+ * the split precisions the levels of >= 128 rows and 2d >= 128 on the tensor
+ * cores, per-item tensor maps), each QFT^-1 pass, the histograms and the
+ * readouts. The number of launches depends on the largest nmeas and the tile
+ * classes present, not on the number of instances. Under the split
+ * precisions (QPE_C64_FP16X2 / TF32X3) instances with nmat <= 6 keep the
+ * fused complex64 schedule. Only whole runs (qpe_run) are supported. Host
+ * only, like qpe_plan.
  */
 qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* workspace_bytes, qpe_plan_t* out);
 
@@ -320,8 +325,11 @@ int64_t qpe_query(qpe_plan_t plan, int32_t key);
 /*
  * qpe_stage_times: milliseconds each stage of the last qpe_run took on the
  * bound stream (ms[0..3] = POWERS, SWEEP, FFT, REDUCE), from CUDA events the
- * library records around its own launches. Needs QPE_FLAG_TIMING and a
- * single-instance plan (QPE_ERR_STATE otherwise). Synchronises the stream.
+ * library records around its own launches. Needs QPE_FLAG_TIMING (QPE_ERR_STATE
+ * otherwise). Batched plans split a run into every squaring step; the fused
+ * instances' levels and the plain instances' doubling levels; the plain
+ * instances' QFT^-1 passes; their histograms and every readout.
+ * Synchronises the stream.
  */
 qpe_status qpe_stage_times(qpe_plan_t plan, double* ms);
 

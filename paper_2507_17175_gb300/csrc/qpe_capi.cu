@@ -335,6 +335,8 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
   bm.fft_items.clear();
   bm.red_items.clear();
   bm.dbl_rounds.clear();
+  bm.oz_items.clear();
+  bm.oz_steps.clear();
   bm.tc_split.clear();
   bm.tc_gemm.clear();
   bm.tc_rounds.clear();
@@ -372,6 +374,24 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
       bm.sq.push_back(it);
     }
     bm.sq_count[k] = (int)bm.sq.size() - bm.sq_begin[k];
+    // the tensor-core squarings of this step, one grouped launch set
+    qpe::OzStep O{};
+    O.k = k;
+    O.item_off = (int)bm.oz_items.size();
+    for (Instance& in : p->inst) {
+      if (in.nmeas <= k || !in.oz_square) continue;
+      qpe::OzItem oz{};
+      if (!qpe::oz_square_item(in, ws, k, c64, &oz)) throw std::runtime_error("tensor map");
+      oz.sb0 = O.sblocks;
+      oz.e0 = O.elems;
+      oz.tile0 = O.tiles;
+      O.sblocks += 2 * in.d;
+      O.elems += in.d * in.d;
+      O.tiles += qpe::oz_square_tiles(in);
+      bm.oz_items.push_back(oz);
+    }
+    O.nitems = (int)bm.oz_items.size() - O.item_off;
+    if (O.nitems > 0) bm.oz_steps.push_back(O);
     bm.sq_tiles[k] = tiles;
     bm.sq_tiles16[k] = tiles16;
     bm.sq_tiles32[k] = tiles32;
@@ -674,6 +694,7 @@ size_t place_batch_meta(qpe::BatchMeta& bm, size_t off) {
   bm.off_fft = take(bm.fft_items.size());
   bm.off_red = take(bm.red_items.size());
   bm.off_finp = take(bm.fin_plain.size() * sizeof(qpe::FinItem));
+  bm.off_oz = take(bm.oz_items.size() * sizeof(qpe::OzItem));
   bm.off_tcsp = take(bm.tc_split.size() * sizeof(qpe::TcSplitItem));
   bm.off_tcgm = take(bm.tc_gemm.size() * sizeof(qpe::TcGemmItem));
   return off;
@@ -697,6 +718,7 @@ qpe_status upload_batch_meta(qpe_plan_t p) {
               {bm.off_fft, bm.fft_items.data(), bm.fft_items.size()},
               {bm.off_red, bm.red_items.data(), bm.red_items.size()},
               {bm.off_finp, bm.fin_plain.data(), bm.fin_plain.size() * sizeof(qpe::FinItem)},
+              {bm.off_oz, bm.oz_items.data(), bm.oz_items.size() * sizeof(qpe::OzItem)},
               {bm.off_tcsp, bm.tc_split.data(), bm.tc_split.size() * sizeof(qpe::TcSplitItem)},
               {bm.off_tcgm, bm.tc_gemm.data(), bm.tc_gemm.size() * sizeof(qpe::TcGemmItem)}};
   for (const Blk& b : blks) {
@@ -762,6 +784,13 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
   };
   for (Instance& in : p->inst)
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
+  // QPE_FLAG_TIMING: events at the start, after the squarings, after the gates
+  // (fused levels whole, plain doubling levels), after the plain QFT^-1 passes
+  // and at the end (plain histograms and every readout)
+  const bool timing = (p->flags & QPE_FLAG_TIMING) && p->ev[0];
+  p->timed_run = timing;
+  auto mark = [&](int i) { return !timing || record_event(p->ev[i], p->stream) == cudaSuccess; };
+  if (!mark(0)) return cuda_fail(p, cudaGetLastError(), "cudaEventRecord");
   // error words of the instances whose kernels can set them, cleared per run
   for (Instance& in : p->inst)
     if (in.oz_square || (is_tc(p->prec) && !in.fused)) {
@@ -780,13 +809,16 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
                                         bm.sq_count[k], square_tiles(bm, k, p->sq_variant), p->sq_variant,
                                         p->stream)))
       return cuda_fail(p, cudaGetLastError(), "grouped squaring");
-    for (Instance& in : p->inst)
-      if (in.oz_square && in.nmeas > k && !chk(qpe::launch_square_oz(in, ws, k, c64, p->stream)))
+    for (const qpe::OzStep& O : bm.oz_steps)
+      if (O.k == k && !chk(qpe::launch_square_oz_grouped(reinterpret_cast<const qpe::OzItem*>(ws + bm.off_oz) +
+                                                             O.item_off,
+                                                         O.nitems, O.sblocks, O.elems, O.tiles, p->stream)))
         return cuda_fail(p, cudaGetLastError(), "tensor-core squaring");
   }
   if (!chk(qpe::launch_convert_grouped(reinterpret_cast<const qpe::SqItem*>(ws + bm.off_conv), (int)bm.conv.size(),
                                        bm.conv_tiles, p->stream)))
     return cuda_fail(p, cudaGetLastError(), "grouped conversion");
+  if (!mark(1)) return cuda_fail(p, cudaGetLastError(), "cudaEventRecord");
   if (!bm.fused.empty()) {
     int r;
     if (c64)
@@ -845,10 +877,12 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
                   T.tiles, p->stream)))
             return false;
       }
+      if (!mark(2)) return false;
       for (const qpe::FftRound& R : bm.fft_rounds)
         if (!chk(qpe::launch_fft_grouped<C>(reinterpret_cast<const qpe::FftItem<C>*>(ws + bm.off_fft) + R.item_off,
                                             R.nitems, R.blocks, R.smem, p->stream)))
           return false;
+      if (!mark(3)) return false;
       if (!chk(qpe::launch_reduce_grouped<C>(reinterpret_cast<const qpe::RedItem<C>*>(ws + bm.off_red), bm.nred,
                                              bm.red_blocks, p->stream)))
         return false;
@@ -863,7 +897,10 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
       in.state_natural = false;
       in.state_valid = true;
     }
+  } else if (!mark(2) || !mark(3)) {
+    return cuda_fail(p, cudaGetLastError(), "cudaEventRecord");
   }
+  if (!mark(4)) return cuda_fail(p, cudaGetLastError(), "cudaEventRecord");
   *launches = n;
   return QPE_OK;
 }
@@ -1035,7 +1072,7 @@ qpe_status qpe_plan_batched(const qpe_plan_desc* descs, int32_t count, size_t* w
     if (st != QPE_OK) return st;
     if (descs[i].prec != descs[0].prec || descs[i].flags != descs[0].flags) return QPE_ERR_ARG;
   }
-  if (descs[0].flags & (QPE_FLAG_GATE_SWEEP | QPE_FLAG_TIMING)) return QPE_ERR_UNSUPPORTED;
+  if (descs[0].flags & QPE_FLAG_GATE_SWEEP) return QPE_ERR_UNSUPPORTED;
   qpe_plan_s* p = new (std::nothrow) qpe_plan_s();
   if (!p) return QPE_ERR_ARG;
   p->prec = descs[0].prec;
@@ -1341,8 +1378,8 @@ int64_t qpe_query(qpe_plan_t p, int32_t key) {
 
 qpe_status qpe_stage_times(qpe_plan_t p, double* ms) {
   if (!p || !ms) return fail(p, QPE_ERR_ARG, "null pointer");
-  if (!(p->flags & QPE_FLAG_TIMING) || p->inst.size() != 1 || !p->ev[0])
-    return fail(p, QPE_ERR_STATE, "plan was not created with QPE_FLAG_TIMING (single instance) and bound");
+  if (!(p->flags & QPE_FLAG_TIMING) || !p->ev[0])
+    return fail(p, QPE_ERR_STATE, "plan was not created with QPE_FLAG_TIMING and bound");
   if (!p->timed_run) return fail(p, QPE_ERR_STATE, "no whole qpe_run has been timed yet");
   cudaError_t e = cudaEventSynchronize(p->ev[4]);
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventSynchronize");

@@ -414,6 +414,32 @@ struct TcRound {  // one level j across the tensor-core instances
   int64_t rows, elems, tiles;
 };
 
+// The digit-product GEMM of the tensor-core squaring (P_(k+1) = P_k^2).
+struct OzArgs {
+  const int* tau;  // row scales of E
+  const int* sig;  // column scales of B
+  double2* C;      // P_(k+1), complex128 d x d
+  float2* C32;     // its complex64 copy, or null
+  int d;
+  int* err;
+};
+// One instance's squaring step in a grouped launch: the digit slices' tensor
+// maps, P_k, the slice buffers, and the item's first scale block, first slice
+// element and first GEMM CTA in the launches' numbering.
+struct OzItem {
+  CUtensorMap mA, mB;
+  OzArgs a;
+  const double2* P;
+  void* A;
+  void* B;
+  float2* A32;
+  int64_t sb0, e0, tile0;
+};
+struct OzStep {  // squaring step k across the tensor-core instances
+  int k, item_off, nitems;
+  int64_t sblocks, elems, tiles;
+};
+
 struct DblRound {  // one grouped doubling launch: level j of the items of one tile class
   int j, dclass, item_off, nitems;
   int64_t tiles;
@@ -429,6 +455,8 @@ struct BatchMeta {
   // plain instances (Nmat > 6, or QPE_FLAG_PLAIN), run together step by step
   std::vector<char> init_items, dbl_items, fft_items, red_items;  // typed by the plan's precision
   std::vector<DblRound> dbl_rounds;
+  std::vector<OzItem> oz_items;  // tensor-core squarings, grouped per step
+  std::vector<OzStep> oz_steps;
   std::vector<TcSplitItem> tc_split;  // tensor-core levels (j >= 7, 2d >= 128), grouped per level
   std::vector<TcGemmItem> tc_gemm;
   std::vector<TcRound> tc_rounds;
@@ -436,7 +464,7 @@ struct BatchMeta {
   std::vector<FinItem> fin_plain;
   int ninit = 0, nred = 0, maxn_plain = 0;
   int64_t red_blocks = 0;
-  size_t off_init = 0, off_dbl = 0, off_fft = 0, off_red = 0, off_finp = 0, off_tcsp = 0, off_tcgm = 0;
+  size_t off_init = 0, off_dbl = 0, off_fft = 0, off_red = 0, off_finp = 0, off_tcsp = 0, off_tcgm = 0, off_oz = 0;
   // squaring: items of step k at [sq_begin[k], sq_begin[k] + sq_count[k])
   std::vector<SqItem> sq;
   std::vector<int> sq_begin, sq_count;
@@ -515,6 +543,12 @@ int64_t tc_level_tiles(const Instance& in, int j);
 int launch_tc_level_grouped(int prec, const TcSplitItem* sp, const TcGemmItem* gm, int nitems, int64_t rows,
                             int64_t elems, int64_t tiles, cudaStream_t s);
 size_t oz_square_bytes(int nmat);
+// grouped tensor-core squaring (batched plans): one instance's item, its GEMM
+// CTAs, and the three launches (scales, slices, GEMM) for all items of a step
+bool oz_square_item(const Instance& in, char* ws, int k, bool want_c64, OzItem* it);
+int64_t oz_square_tiles(const Instance& in);
+int launch_square_oz_grouped(const OzItem* items, int nitems, int64_t sblocks, int64_t elems, int64_t tiles,
+                             cudaStream_t s);
 int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStream_t s);
 size_t tc_split_bytes(int prec, int nmat, int nmeas);
 cudaError_t configure_tc_kernels();

@@ -1080,7 +1080,12 @@ cudaError_t configure_kernels() {
   // tile (<= 64 KiB) + the pass's twiddles (<= 256 entries)
   e = cudaFuncSetAttribute(fft_pass_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 4096);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fft_pass_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(fft_pass_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 4096);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fft_pass_grouped_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           64 * 1024 + 4096);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fft_pass_grouped_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               64 * 1024 + 4096);
 }
 

@@ -504,10 +504,8 @@ __device__ __forceinline__ int oz_exponent(double mx) {
 
 // tau[i]: scale of rows i and i + d of E (from row i of P); sig[j]: of column
 // j of [Re P ; Im P]. A non-finite entry sets the error word.
-__global__ void __launch_bounds__(256) oz_scale_kernel(const double2* __restrict__ P, int d, int* __restrict__ tau,
-                                                       int* __restrict__ sig, int* __restrict__ err) {
-  pdl_begin();
-  const int b = blockIdx.x;
+__device__ __forceinline__ void oz_scale_block(const double2* __restrict__ P, int d, int* __restrict__ tau,
+                                               int* __restrict__ sig, int* __restrict__ err, int b) {
   double mx = 0.0;
   bool finite = true;
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
@@ -528,6 +526,12 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const double2* __restrict
     else
       sig[b - d] = e;
   }
+}
+
+__global__ void __launch_bounds__(256) oz_scale_kernel(const double2* __restrict__ P, int d, int* __restrict__ tau,
+                                                       int* __restrict__ sig, int* __restrict__ err) {
+  pdl_begin();
+  oz_scale_block(P, d, tau, sig, err, blockIdx.x);
   pdl_trigger();
 }
 
@@ -547,12 +551,10 @@ __device__ __forceinline__ void oz_digits(double x, int t, __nv_bfloat16* out, i
 
 // digits of E (rows 2d, K = 2d) per slice: A[(s 2d + m) 2d + kk]; also the
 // complex64 copy of P when A32 is given
-__global__ void __launch_bounds__(256) oz_slice_a_kernel(const double2* __restrict__ P, int d,
-                                                         const int* __restrict__ tau, __nv_bfloat16* __restrict__ A,
-                                                         float2* __restrict__ A32) {
-  pdl_begin();
-  const int64_t dd = (int64_t)d * d, d2 = 2 * (int64_t)d, stride = d2 * d2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dd; e += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void oz_slice_a_elem(const double2* __restrict__ P, int d, const int* __restrict__ tau,
+                                                __nv_bfloat16* __restrict__ A, float2* __restrict__ A32, int64_t e) {
+  const int64_t d2 = 2 * (int64_t)d, stride = d2 * d2;
+  {
     const int64_t i = e / d, j = e - i * d;
     const double2 p = P[e];
     if (A32) A32[e] = make_float2((float)p.x, (float)p.y);
@@ -562,32 +564,40 @@ __global__ void __launch_bounds__(256) oz_slice_a_kernel(const double2* __restri
     oz_digits(-p.y, t, A + i * d2 + j + d, stride);        // E[i][j+d]   = -Im
     oz_digits(p.y, t, A + (i + d) * d2 + j, stride);       // E[i+d][j]   = Im
   }
+}
+
+__global__ void __launch_bounds__(256) oz_slice_a_kernel(const double2* __restrict__ P, int d,
+                                                         const int* __restrict__ tau, __nv_bfloat16* __restrict__ A,
+                                                         float2* __restrict__ A32) {
+  pdl_begin();
+  const int64_t dd = (int64_t)d * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dd; e += (int64_t)gridDim.x * blockDim.x)
+    oz_slice_a_elem(P, d, tau, A, A32, e);
   pdl_trigger();
 }
 
 // digits of B (rows d, K = 2d): B[(s d + n) 2d + kk] = digits of E[kk][n]
-__global__ void __launch_bounds__(256) oz_slice_b_kernel(const double2* __restrict__ P, int d,
-                                                         const int* __restrict__ sig, __nv_bfloat16* __restrict__ B) {
-  pdl_begin();
-  const int64_t dd = (int64_t)d * d, d2 = 2 * (int64_t)d, stride = (int64_t)d * d2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dd; e += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void oz_slice_b_elem(const double2* __restrict__ P, int d, const int* __restrict__ sig,
+                                                __nv_bfloat16* __restrict__ B, int64_t e) {
+  const int64_t d2 = 2 * (int64_t)d, stride = (int64_t)d * d2;
+  {
     const int64_t n = e / d, kk = e - n * d;  // consecutive threads: consecutive kk (contiguous writes)
     const double2 p = P[kk * d + n];
     const int t = sig[n];
     oz_digits(p.x, t, B + n * d2 + kk, stride);      // E[kk][n]   = Re P[kk][n]
     oz_digits(p.y, t, B + n * d2 + kk + d, stride);  // E[kk+d][n] = Im P[kk][n]
   }
+}
+
+__global__ void __launch_bounds__(256) oz_slice_b_kernel(const double2* __restrict__ P, int d,
+                                                         const int* __restrict__ sig, __nv_bfloat16* __restrict__ B) {
+  pdl_begin();
+  const int64_t dd = (int64_t)d * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < dd; e += (int64_t)gridDim.x * blockDim.x)
+    oz_slice_b_elem(P, d, sig, B, e);
   pdl_trigger();
 }
 
-struct OzArgs {
-  const int* tau;
-  const int* sig;
-  double2* C;    // P_(k+1), complex128 d x d
-  float2* C32;   // its complex64 copy, or null
-  int d;
-  int* err;
-};
 
 // One CTA per 128 x BN tile of out (rows of E, columns n < d); roles as in
 // tc_gemm_kernel: warp 0 lane 0 TMA producer, warp 1 lane 0 MMA issuer, warps
@@ -596,9 +606,8 @@ struct OzArgs {
 // each weight a drain thread folds its row's int32 sums into FP64 values kept
 // in its own row of the output (read back only by the same thread).
 template <int BN>
-__global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                           const __grid_constant__ CUtensorMap mapB, OzArgs a) {
-  pdl_begin();
+__device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CUtensorMap* mapB, const OzArgs& a,
+                                               int bid) {
   constexpr int kOzBN = BN;
   constexpr int A_BYTES = kBM * 128;
   constexpr int B_BYTES = kOzBN * 128;
@@ -615,7 +624,6 @@ __global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant
   const int m_tiles = d2 / kBM, n_tiles = d / kOzBN;
   int m_tile, n_tile;
   {
-    const int bid = blockIdx.x;
     const int per_group = kGroupM * n_tiles;
     const int g = bid / per_group;
     const int first = g * kGroupM;
@@ -669,8 +677,8 @@ __global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant
             }
             unsigned char* sa = ring + st * STAGE_BYTES;
             mbar_expect_tx(&full_bar[st], STAGE_BYTES);
-            tma_load_2d(sa, &mapA, &full_bar[st], kb * 64, (s - 1) * d2 + m0);
-            tma_load_2d(sa + A_BYTES, &mapB, &full_bar[st], kb * 64, (u - s - 1) * d + n0);
+            tma_load_2d(sa, mapA, &full_bar[st], kb * 64, (s - 1) * d2 + m0);
+            tma_load_2d(sa + A_BYTES, mapB, &full_bar[st], kb * 64, (u - s - 1) * d + n0);
           }
     }
   } else if (warp == 1) {
@@ -782,8 +790,66 @@ __global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * kOzBN))
                  : "memory");
   }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB, OzArgs a) {
+  pdl_begin();
+  oz_square_tile<BN>(&mapA, &mapB, a, blockIdx.x);
   pdl_trigger();
 }
+
+// One squaring step of every listed instance (batched plans): scales, digit
+// slices, then the digit-product GEMM with per-item tensor maps.
+__global__ void __launch_bounds__(256) oz_scale_grouped_kernel(const OzItem* __restrict__ items, int nitems) {
+  pdl_begin();
+  int lo = 0, hi = nitems - 1;  // item whose scale blocks [sb0, sb0 + 2d) hold this CTA
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].sb0 <= (int64_t)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const OzItem& it = items[lo];
+  oz_scale_block(it.P, it.a.d, const_cast<int*>(it.a.tau), const_cast<int*>(it.a.sig), it.a.err,
+                 (int)(blockIdx.x - it.sb0));
+  pdl_trigger();
+}
+
+__global__ void __launch_bounds__(256) oz_slice_grouped_kernel(const OzItem* __restrict__ items, int nitems,
+                                                               int64_t elems) {
+  pdl_begin();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < elems; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nitems - 1;  // item whose elements [e0, e0 + d^2) hold e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].e0 <= e)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const OzItem& it = items[lo];
+    const int64_t le = e - it.e0;
+    oz_slice_a_elem(it.P, it.a.d, it.a.tau, static_cast<__nv_bfloat16*>(it.A), it.A32, le);
+    oz_slice_b_elem(it.P, it.a.d, it.a.sig, static_cast<__nv_bfloat16*>(it.B), le);
+  }
+  pdl_trigger();
+}
+
+__global__ void __launch_bounds__(192, 1) oz_square_grouped_kernel(const OzItem* __restrict__ items, int nitems) {
+  pdl_begin();
+  const OzItem* it = items + find_item(items, nitems, blockIdx.x);
+  if (threadIdx.x == 0) {
+    tensormap_acquire(&it->mA);
+    tensormap_acquire(&it->mB);
+  }
+  __syncthreads();
+  oz_square_tile<64>(&it->mA, &it->mB, it->a, (int)(blockIdx.x - it->tile0));
+  pdl_trigger();
+}
+
 
 // ------------------------------------------------------------ host side
 namespace {
@@ -847,6 +913,8 @@ cudaError_t configure_tc_kernels() {
                            (int)tc_smem<kTcFP16, 128>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(oz_square_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem<64>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(oz_square_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem<64>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(oz_square_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)oz_smem<128>());
@@ -1024,6 +1092,40 @@ int launch_tc_level_grouped(int prec, const TcSplitItem* sp, const TcGemmItem* g
                       : launch_k(tc_gemm_grouped_kernel<kTcFP16, 128>, dim3((unsigned)tiles),
                                  dim3(64 + 32 * kTcDrainWarps), tc_smem<kTcFP16, 128>(), s, gm, nitems);
   return e == cudaSuccess ? 2 : -1;
+}
+
+// One instance's squaring step k for a grouped launch (tensor maps only when
+// ws is a bound workspace); its scale blocks, slice elements and GEMM CTAs.
+bool oz_square_item(const Instance& in, char* ws, int k, bool want_c64, OzItem* it) {
+  const int d = (int)in.d;
+  const int64_t dd = in.d * in.d;
+  it->P = reinterpret_cast<const double2*>(ws + in.off_pow64) + (k - 1) * dd;
+  float2* P32 = want_c64 ? reinterpret_cast<float2*>(ws + in.off_pow32) : nullptr;
+  char* base = ws + in.off_ozsq;
+  int* tau = reinterpret_cast<int*>(base);
+  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(base + ((2 * (size_t)d * sizeof(int) + 255) & ~size_t(255)));
+  __nv_bfloat16* B = A + (size_t)kOzS * 4 * dd;
+  it->A = A;
+  it->B = B;
+  it->A32 = (P32 && k == 1) ? P32 : nullptr;
+  it->a = OzArgs{tau, tau + d, reinterpret_cast<double2*>(ws + in.off_pow64) + k * dd, P32 ? P32 + k * dd : nullptr, d,
+                 reinterpret_cast<int*>(ws + in.off_err)};
+  if (!ws) return true;
+  return make_map(&it->mA, A, kTcBF16, (int64_t)kOzS * 2 * d, 2 * (int64_t)d, kBM) &&
+         make_map(&it->mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, 64);
+}
+
+int64_t oz_square_tiles(const Instance& in) { return (2 * in.d / kBM) * (in.d / 64); }
+
+int launch_square_oz_grouped(const OzItem* items, int nitems, int64_t sblocks, int64_t elems, int64_t tiles,
+                             cudaStream_t s) {
+  if (nitems <= 0) return 0;
+  const unsigned eb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((elems + 255) / 256, 152 * 16));
+  cudaError_t e = launch_k(oz_scale_grouped_kernel, dim3((unsigned)sblocks), dim3(256), 0, s, items, nitems);
+  if (e == cudaSuccess) e = launch_k(oz_slice_grouped_kernel, dim3(eb), dim3(256), 0, s, items, nitems, elems);
+  if (e == cudaSuccess)
+    e = launch_k(oz_square_grouped_kernel, dim3((unsigned)tiles), dim3(192), oz_smem<64>(), s, items, nitems);
+  return e == cudaSuccess ? 3 : -1;
 }
 
 // ------------------------------------------- expiry of a bounded wait

@@ -35,7 +35,8 @@ def main(argv=None):
             "tf32x3": qpe.C64_TF32X3}[args.prec]
     shapes = [(i.nmat, i.nmeas) for i in insts]
     stream = torch.cuda.Stream()
-    flags = qpe.FLAG_GRAPH | (qpe.FLAG_AUTOTUNE if args.autotune else 0) | (qpe.FLAG_SQUARE_TC if args.square_tc else 0)
+    flags = (qpe.FLAG_GRAPH | qpe.FLAG_TIMING | (qpe.FLAG_AUTOTUNE if args.autotune else 0) |
+             (qpe.FLAG_SQUARE_TC if args.square_tc else 0))
     bp = qpe.BatchedPlan(shapes, prec, flags, stream=stream)
     dev_inputs = [(torch.from_numpy(i.U).cuda(), torch.from_numpy(i.psi).cuda()) for i in insts]
     for k, (U, psi) in enumerate(dev_inputs):
@@ -57,6 +58,10 @@ def main(argv=None):
            "square_tc": bool(args.square_tc),
            "batched_ms": min(times), "batched_runs_per_s": 1e3 / min(times),
            "launches_per_run": bp.query(qpe.INFO_LAST_LAUNCHES),
+           "stage_ms": dict(zip(["squarings", "gates (fused levels whole, plain doubling levels)",
+                                 "plain QFT^-1 passes", "plain histograms + every readout"],
+                                [round(x, 3) for x in bp.stage_times()])),
+           "plain_instances": sum(1 for a, _ in shapes if a > 6),
            "square_tile": bp.query(qpe.INFO_SQUARE_TILE),
            "workspace_gib": bp.ws_bytes / 2 ** 30}
     del bp

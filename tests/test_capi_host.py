@@ -122,7 +122,9 @@ def test_plan_batched_validation(q):
     assert q.plan_batched_workspace([], q.C64_FP32)[0] == q.ERR_ARG
     assert q.plan_batched_workspace([(0, 4)], q.C64_FP32)[0] == q.ERR_ARG
     assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_GATE_SWEEP)[0] == q.ERR_UNSUPPORTED
-    assert q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_TIMING)[0] == q.ERR_UNSUPPORTED
+    st, ws, h = q.plan_batched_workspace([(2, 4)], q.C64_FP32, q.FLAG_TIMING)  # coarse stage split
+    assert st == q.OK
+    q.LIB.qpe_destroy(h)
     # split precisions: any nmat in a batched plan (nmat <= 6 runs fused in complex64); single plans with
     # nmat <= 4 run fused (FP16x2 at nmat = 4 with the top level on the tensor cores), not gate by gate
     st, ws, h = q.plan_batched_workspace([(3, 8), (8, 10)], q.C64_FP16X2, q.FLAG_SQUARE_TC)
