@@ -474,21 +474,17 @@ __global__ void split_grouped_kernel(const TcSplitItem* __restrict__ items, int 
 // Over reals, with E = [[Re P, -Im P], [Im P, Re P]] (2d x 2d), the first d
 // columns of E^2 are [Re P^2 ; Im P^2]; so out = E (2d x 2d) times
 // B^T, B[n][kk] = E[kk][n] (n < d, K-major). Every entry of row m of E is
-// written as x = 2^(tau_m - 55) sum_{s=1..7} a_s 2^(8 (7 - s)) with balanced
+// written as x = 2^(tau_m - 55) sum_{s=0..6} a_s 2^(8 (6 - s)) with balanced
 // integer digits |a_s| <= 128 (round to nearest at 2^(tau_m - 55), |x| <
-// 2^tau_m), and every entry of column n of B likewise with sigma_n. Digits are
-// exact in bf16 and the product of two is an exact integer below 2^14, so
-// tcgen05 MMAs with FP32 accumulation sum them exactly as long as a partial
-// sum stays below 2^24: the digit pairs (s, t) of one weight u = s + t (at
-// most 7 pairs) go into one tensor-memory accumulator per 64-element K-block
-// (at most 7 * 64 * 2^14 < 2^23), which the drain warps convert to integers
-// and add into int32 registers (at most 128 K-blocks: < 2^30). The pairs with
-// u <= 8 are formed (28 bf16 products); the rest lie below 2^-53 of
-// 2^(tau + sigma) K. At the end of each weight the integer sums are folded in
-// FP64, val += acc_u 2^(-8 u), and out = val 2^(tau_m + sigma_n + 2).
+// 2^tau_m), and every entry of column n of B likewise (digits b_t) with
+// sigma_n. Digits are exact in bf16 and the product of two is an exact integer
+// of at most 2^14, so tcgen05 MMAs with FP32 accumulation sum them exactly as
+// long as every partial sum stays below 2^24. A digit pair (s, t) has weight
+// w = s + t: out = 2^(tau_m + sigma_n + 2) sum_w acc_w 2^(-8 w - 16), acc_w
+// the integer sum of the pairs of weight w over K. The pairs with w <= 6 are
+// formed (28 bf16 products); the rest lie below 2^-53 of 2^(tau + sigma) K.
 constexpr int kOzS = 7;       // digits per operand entry
 constexpr int kOzBeta = 8;    // bits per digit
-constexpr int kOzStages = 6;  // TMA ring stages (A 16 KiB + B BN x 128 B each)
 
 __device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023
   return __longlong_as_double((long long)(1023 + e) << 52);
@@ -599,23 +595,152 @@ __global__ void __launch_bounds__(256) oz_slice_b_kernel(const double2* __restri
 }
 
 
-// One CTA per 128 x BN tile of out (rows of E, columns n < d); roles as in
-// tc_gemm_kernel: warp 0 lane 0 TMA producer, warp 1 lane 0 MMA issuer, warps
-// 2..5 drain (one tile row per thread). Stages run weight by weight
-// (u = 2 .. 8), K-block by K-block, digit pair by digit pair. At the end of
-// each weight a drain thread folds its row's int32 sums into FP64 values kept
-// in its own row of the output (read back only by the same thread).
-template <int BN>
+// One CTA per 128 x 64 tile of out (rows m0.. of E, columns n0.. < d).
+// K-block by K-block (64 elements of K), every digit tile is loaded once: the
+// seven B digit tiles of the K-block (resident, two buffers) and the seven A
+// digit tiles one after another through a ring; A digit s meets B digits
+// t = 0 .. 6 - s, and pair (s, t) goes into the tensor-memory accumulator of
+// weight w = s + t (64 columns each, 448 in all). Weight w is complete for the
+// K-block once A digit w has been used, so the weights finish in order and
+// the drain of one overlaps the MMAs of the next.
+// An accumulator holds (w + 1) pairs per K-block, each at most 64 * 2^14, so
+// it stays an exact FP32 integer (below 2^24) over a window of win_w
+// K-blocks, (w + 1) * win_w < 16; the drain reads it once per window.
+// Drain warps 2 .. 9 (two per tensor-memory lane quarter, 32 columns each)
+// convert the window sums to integers and add them into two int64 sums per
+// column, hi = sum_(w <= 2) acc_w 2^(8 (2 - w)) and lo = sum_(w >= 3) acc_w
+// 2^(8 (6 - w)) (below 2^44 and 2^54 for K <= 8192); at the end
+// val = hi 2^-32 + lo 2^-64 and out = val 2^(tau_m + sigma_n + 2).
+// Warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs.
+constexpr int kOzBN = 64;
+constexpr int kOzAStages = 6;
+constexpr int kOzThreads = 320;
+constexpr int kOzA = kBM * 128;              // one A digit tile, 16 KiB
+constexpr int kOzB = kOzBN * 128;            // one B digit tile, 8 KiB
+constexpr int kOzBSet = kOzS * kOzB;         // the seven B digit tiles of a K-block
+// Window of weight w's accumulator in K-blocks (8, 4, 4, 2, 2, 2, 2) and its
+// phase: window j of weight w covers the K-blocks kb with
+// (kb + off_w) >> log2(win_w) = j (the first one shorter when off_w > 0). The
+// phases spread the drains over the K-blocks (two or three at each boundary)
+// instead of all seven at once.
+template <int W>
+__host__ __device__ constexpr int oz_log_win() { return W == 0 ? 3 : (W <= 2 ? 2 : 1); }
+template <int W>
+__host__ __device__ constexpr int oz_win() { return 1 << oz_log_win<W>(); }
+template <int W>
+__host__ __device__ constexpr int oz_off() { return W == 0 ? 2 : (W == 1 ? 1 : (W == 2 ? 3 : (W & 1) ^ 1)); }
+static_assert((0 + 1) * oz_win<0>() < 16 && (2 + 1) * oz_win<2>() < 16 && (6 + 1) * oz_win<6>() < 16,
+              "window sums must stay below 2^24");
+
+template <int W>
+__device__ __forceinline__ int oz_window(int kb) { return (kb + oz_off<W>()) >> oz_log_win<W>(); }
+template <int W>
+__device__ __forceinline__ bool oz_window_start(int kb) {
+  return kb == 0 || ((kb + oz_off<W>()) & (oz_win<W>() - 1)) == 0;
+}
+template <int W>
+__device__ __forceinline__ bool oz_window_end(int kb, int kblocks) {
+  return ((kb + 1 + oz_off<W>()) & (oz_win<W>() - 1)) == 0 || kb + 1 == kblocks;
+}
+
+// The MMAs of A digit S against B digits T .. 6 - S (one K-block): pair
+// (S, T) into the accumulator of weight S + T, four K = 16 steps. The first
+// pair of a window (S = 0) overwrites the accumulator, after waiting for the
+// drain of the window before. False if that wait runs out.
+template <int S, int T>
+__device__ __forceinline__ bool oz_mma_pairs(uint32_t tmem, uint64_t ad, uint64_t bd0, uint32_t idesc, int kb,
+                                             uint64_t* acc_empty) {
+  if constexpr (S + T < kOzS) {
+    constexpr int w = S + T;
+    bool fresh = false;
+    if constexpr (S == 0) {
+      fresh = oz_window_start<w>(kb);
+      if (fresh && kb > 0) {
+        if (!mbar_wait(&acc_empty[w], (oz_window<w>(kb) - 1) & 1)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+    }
+    const uint64_t bd = bd0 + (uint64_t)(T * (kOzB >> 4));
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      umma_k<kTcBF16>(tmem + (uint32_t)(w * kOzBN), ad + 2 * k, bd + 2 * k, idesc, (fresh && k == 0) ? 0u : 1u);
+    return oz_mma_pairs<S, T + 1>(tmem, ad, bd0, idesc, kb, acc_empty);
+  }
+  return true;
+}
+
+// A digits S .. 6 of one K-block: wait for the digit's ring stage, its pairs,
+// release the stage, and signal weight S complete at the end of its window.
+template <int S>
+__device__ __forceinline__ bool oz_mma_digits(uint32_t tmem, uint64_t a_desc0, uint64_t bd0, uint32_t idesc, int kb,
+                                              int kblocks, int& stage, uint32_t& phase, uint64_t* a_full,
+                                              uint64_t* a_empty, uint64_t* acc_full, uint64_t* acc_empty) {
+  if constexpr (S < kOzS) {
+    if (!mbar_wait(&a_full[stage], phase)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint64_t ad = a_desc0 + (uint64_t)(stage * (kOzA >> 4));
+    if (!oz_mma_pairs<S, 0>(tmem, ad, bd0, idesc, kb, acc_empty)) return false;
+    umma_commit(&a_empty[stage]);
+    if (oz_window_end<S>(kb, kblocks)) umma_commit(&acc_full[S]);  // weight S is complete
+    if (++stage == kOzAStages) {
+      stage = 0;
+      phase ^= 1u;
+    }
+    return oz_mma_digits<S + 1>(tmem, a_desc0, bd0, idesc, kb, kblocks, stage, phase, a_full, a_empty, acc_full,
+                                acc_empty);
+  }
+  return true;
+}
+
+// Drain of weight W at the end of its window: 32 columns of this warp's lane
+// quarter into the int64 sums (weights 0-2 into hi, 3-6 into lo, shifted by
+// their place). False if the wait runs out or another role failed.
+template <int W>
+__device__ __forceinline__ bool oz_drain_weight(uint32_t taddr, int kb, uint64_t* acc_full, uint64_t* acc_empty,
+                                                const int* fail, int lane, long long (&hi)[32],
+                                                long long (&lo)[32]) {
+  bool got = mbar_wait(&acc_full[W], oz_window<W>(kb) & 1);
+  got = __all_sync(0xffffffffu, got && !*((volatile const int*)fail)) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!got) return false;
+  uint32_t v[32];
+  tmem_ld32(taddr + (uint32_t)(W * kOzBN), v);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&acc_empty[W]);
+  constexpr int sh = 8 * ((W <= 2 ? 2 : 6) - W);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const long long x = (long long)__float2int_rn(__uint_as_float(v[i])) << sh;
+    if constexpr (W <= 2)
+      hi[i] += x;
+    else
+      lo[i] += x;
+  }
+  return true;
+}
+
+template <int W>
+__device__ __forceinline__ bool oz_drain_kblock(uint32_t taddr, int kb, int kblocks, uint64_t* acc_full,
+                                                uint64_t* acc_empty, const int* fail, int lane, long long (&hi)[32],
+                                                long long (&lo)[32]) {
+  if constexpr (W < kOzS) {
+    if (oz_window_end<W>(kb, kblocks) && !oz_drain_weight<W>(taddr, kb, acc_full, acc_empty, fail, lane, hi, lo))
+      return false;
+    return oz_drain_kblock<W + 1>(taddr, kb, kblocks, acc_full, acc_empty, fail, lane, hi, lo);
+  }
+  return true;
+}
+
 __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CUtensorMap* mapB, const OzArgs& a,
                                                int bid) {
-  constexpr int kOzBN = BN;
-  constexpr int A_BYTES = kBM * 128;
-  constexpr int B_BYTES = kOzBN * 128;
-  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
-  unsigned char* ring =
+  unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full_bar[kOzStages], empty_bar[kOzStages], acc_full[2], acc_empty[2];
+  unsigned char* bset = base;                 // 2 x kOzBSet
+  unsigned char* aring = base + 2 * kOzBSet;  // kOzAStages x kOzA
+  __shared__ uint64_t a_full[kOzAStages], a_empty[kOzAStages], b_full[2], b_empty[2];
+  __shared__ uint64_t acc_full[kOzS], acc_empty[kOzS], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
 
@@ -636,20 +761,25 @@ __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CU
   const int kblocks = d2 / 64;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kOzStages; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+    for (int s = 0; s < kOzAStages; ++s) {
+      mbar_init(&a_full[s], 1);
+      mbar_init(&a_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&b_full[b], 1);
+      mbar_init(&b_empty[b], 1);
     }
+    for (int w = 0; w < kOzS; ++w) {
+      mbar_init(&acc_full[w], 1);
+      mbar_init(&acc_empty[w], 8);
+    }
+    mbar_init(&mma_done, 1);
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"((uint32_t)(2 * kOzBN))
+                 "r"(512u)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -658,124 +788,87 @@ __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CU
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
+  int a_issued = 0, b_issued = 0;  // producer: loads issued (to wait for them after a failure)
   if (warp == 0) {
     if (lane == 0) {
       int it = 0;
-      bool go = true;
-      for (int u = 2; u <= kOzS + 1 && go; ++u)
-        for (int kb = 0; kb < kblocks && go; ++kb)
-          for (int s = 1; s < u; ++s, ++it) {
-            const int st = it % kOzStages;
-            if (it >= kOzStages && !mbar_wait(&empty_bar[st], ((it / kOzStages) - 1) & 1)) {
-              atomicExch(&fail, 1);
-              go = false;
-              break;
-            }
-            if (*((volatile int*)&fail)) {
-              go = false;
-              break;
-            }
-            unsigned char* sa = ring + st * STAGE_BYTES;
-            mbar_expect_tx(&full_bar[st], STAGE_BYTES);
-            tma_load_2d(sa, mapA, &full_bar[st], kb * 64, (s - 1) * d2 + m0);
-            tma_load_2d(sa + A_BYTES, mapB, &full_bar[st], kb * 64, (u - s - 1) * d + n0);
-          }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = make_idesc<kTcBF16, kOzBN>();
-      int it = 0, g = 0;
-      bool go = true;
-      for (int u = 2; u <= kOzS + 1 && go; ++u)
-        for (int kb = 0; kb < kblocks && go; ++kb, ++g) {
-          const int b = g & 1;
-          if (g >= 2 && !mbar_wait(&acc_empty[b], ((g >> 1) - 1) & 1)) {
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int bb = kb & 1;
+        if (kb >= 2 && !mbar_wait(&b_empty[bb], ((kb >> 1) - 1) & 1)) {
+          atomicExch(&fail, 1);
+          break;
+        }
+        if (*((volatile int*)&fail)) break;
+        mbar_expect_tx(&b_full[bb], kOzBSet);
+        for (int t = 0; t < kOzS; ++t)
+          tma_load_2d(bset + bb * kOzBSet + t * kOzB, mapB, &b_full[bb], kb * 64, t * d + n0);
+        ++b_issued;
+        bool go = true;
+        for (int s = 0; s < kOzS; ++s, ++it) {
+          const int st = it % kOzAStages;
+          if (it >= kOzAStages && !mbar_wait(&a_empty[st], ((it / kOzAStages) - 1) & 1)) {
             atomicExch(&fail, 1);
             go = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          for (int s = 1; s < u; ++s, ++it) {
-            const int st = it % kOzStages;
-            if (!mbar_wait(&full_bar[st], (it / kOzStages) & 1)) {
-              atomicExch(&fail, 1);
-              go = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(ring + st * STAGE_BYTES);
-            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              umma_k<kTcBF16>(tmem + (uint32_t)(b * kOzBN), ad + 2 * k, bd + 2 * k, idesc,
-                              (s == 1 && k == 0) ? 0u : 1u);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&empty_bar[st]))
-                         : "memory");
+          if (*((volatile int*)&fail)) {
+            go = false;
+            break;
           }
-          if (!go) break;
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&acc_full[b]))
-                       : "memory");
+          mbar_expect_tx(&a_full[st], kOzA);
+          tma_load_2d(aring + st * kOzA, mapA, &a_full[st], kb * 64, s * d2 + m0);
+          ++a_issued;
         }
+        if (!go) break;
+      }
     }
-  } else {
-    const int lg = warp & 3;
-    const int row = lg * 32 + lane;  // tile row of this thread
-    int acc[kOzBN];
-    bool ok = true;
-    int g = 0;
-    for (int u = 2; u <= kOzS + 1 && ok; ++u) {
-      for (int kb = 0; kb < kblocks && ok; ++kb, ++g) {
-        const int b = g & 1;
-        bool got = mbar_wait(&acc_full[b], (g >> 1) & 1);
-        got = __all_sync(0xffffffffu, got && !*((volatile int*)&fail)) != 0;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!got) {
-          ok = false;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc<kTcBF16, kOzBN>();
+      const uint64_t a_desc0 = sw128_desc(smem_u32(aring)), b_desc0 = sw128_desc(smem_u32(bset));
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int bb = kb & 1;
+        if (!mbar_wait(&b_full[bb], (kb >> 1) & 1)) {
+          atomicExch(&fail, 1);
           break;
         }
-#pragma unroll
-        for (int q = 0; q < kOzBN / 32; ++q) {
-          uint32_t v[32];
-          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * kOzBN + q * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-              "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-              "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int x = __float2int_rn(__uint_as_float(v[i]));  // an exact integer below 2^23
-            acc[q * 32 + i] = kb == 0 ? x : acc[q * 32 + i] + x;
-          }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t bd0 = b_desc0 + (uint64_t)(bb * (kOzBSet >> 4));
+        if (!oz_mma_digits<0>(tmem, a_desc0, bd0, idesc, kb, kblocks, stage, phase, a_full, a_empty, acc_full,
+                              acc_empty)) {
+          atomicExch(&fail, 1);
+          break;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+        umma_commit(&b_empty[bb]);
       }
-      if (!ok) break;
-      const double w = pow2d(-kOzBeta * u);
-      const int gm = m0 + row;  // row of E: real part of P row gm, or imaginary part of row gm - d
-      double* vr = reinterpret_cast<double*>(a.C + (int64_t)(gm < d ? gm : gm - d) * d + n0) + (gm < d ? 0 : 1);
-#pragma unroll
-      for (int n = 0; n < kOzBN; ++n) vr[2 * n] = (u == 2 ? 0.0 : vr[2 * n]) + (double)acc[n] * w;
+      // every MMA issued has finished before tensor memory is released
+      umma_commit(&mma_done);
+      if (!mbar_wait(&mma_done, 0)) atomicExch(&fail, 1);
     }
+  } else {
+    const int q = warp & 3;          // tensor-memory lane quarter
+    const int h = (warp - 2) >> 2;   // column half
+    const int row = q * 32 + lane;   // tile row of this thread
+    long long hi[32], lo[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0;
+    bool ok = true;
+    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 32);
+    for (int kb = 0; kb < kblocks && ok; ++kb)
+      ok = oz_drain_kblock<0>(taddr, kb, kblocks, acc_full, acc_empty, &fail, lane, hi, lo);
     if (ok) {
-      const int gm = m0 + row;
+      const int gm = m0 + row;  // row of E: real part of P row gm, or imaginary part of row gm - d
       const int i = gm < d ? gm : gm - d;
       const int t = a.tau[i];
-      double* vr = reinterpret_cast<double*>(a.C + (int64_t)i * d + n0) + (gm < d ? 0 : 1);
-      for (int n = 0; n < kOzBN; ++n) {
-        const int col = n0 + n;
+      double* vr = reinterpret_cast<double*>(a.C + (int64_t)i * d + n0 + h * 32) + (gm < d ? 0 : 1);
+#pragma unroll
+      for (int n = 0; n < 32; ++n) {
+        const int col = n0 + h * 32 + n;
+        const double val = fma((double)lo[n], 0x1p-64, (double)hi[n] * 0x1p-32);
         const int e = t + a.sig[col] + 2;
-        const double c = vr[2 * n] == 0.0 ? 0.0 : vr[2 * n] * pow2d(e < -1022 ? -1022 : e);
+        const double c = val == 0.0 ? 0.0 : val * pow2d(e < -1022 ? -1022 : e);
         vr[2 * n] = c;
         if (a.C32) reinterpret_cast<float*>(a.C32 + (int64_t)i * d + col)[gm < d ? 0 : 1] = (float)c;
       }
@@ -783,20 +876,26 @@ __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CU
       atomicExch(&fail, 1);
     }
   }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && fail) {
+    // copies still in flight land before the CTA's shared memory is released
+    const int na = a_issued < kOzAStages ? a_issued : kOzAStages;
+    for (int j = a_issued - na; j < a_issued; ++j) mbar_wait(&a_full[j % kOzAStages], (j / kOzAStages) & 1);
+    const int nb = b_issued < 2 ? b_issued : 2;
+    for (int j = b_issued - nb; j < b_issued; ++j) mbar_wait(&b_full[j & 1], (j >> 1) & 1);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (fail && threadIdx.x == 0) atomicExch(a.err, (int)QPE_ERR_TIMEOUT);
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * kOzBN))
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
   }
 }
 
-template <int BN>
-__global__ void __launch_bounds__(192, 1) oz_square_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                           const __grid_constant__ CUtensorMap mapB, OzArgs a) {
+__global__ void __launch_bounds__(kOzThreads, 1) oz_square_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                                  const __grid_constant__ CUtensorMap mapB, OzArgs a) {
   pdl_begin();
-  oz_square_tile<BN>(&mapA, &mapB, a, blockIdx.x);
+  oz_square_tile(&mapA, &mapB, a, blockIdx.x);
   pdl_trigger();
 }
 
@@ -838,7 +937,7 @@ __global__ void __launch_bounds__(256) oz_slice_grouped_kernel(const OzItem* __r
   pdl_trigger();
 }
 
-__global__ void __launch_bounds__(192, 1) oz_square_grouped_kernel(const OzItem* __restrict__ items, int nitems) {
+__global__ void __launch_bounds__(kOzThreads, 1) oz_square_grouped_kernel(const OzItem* __restrict__ items, int nitems) {
   pdl_begin();
   const OzItem* it = items + find_item(items, nitems, blockIdx.x);
   if (threadIdx.x == 0) {
@@ -846,7 +945,7 @@ __global__ void __launch_bounds__(192, 1) oz_square_grouped_kernel(const OzItem*
     tensormap_acquire(&it->mB);
   }
   __syncthreads();
-  oz_square_tile<64>(&it->mA, &it->mB, it->a, (int)(blockIdx.x - it->tile0));
+  oz_square_tile(&it->mA, &it->mB, it->a, (int)(blockIdx.x - it->tile0));
   pdl_trigger();
 }
 
@@ -891,8 +990,8 @@ size_t tc_smem() {
   return (size_t)tc_stages<BN>() * 2 * (kBM * 128 + BN * 128) + 1024;
 }
 
-template <int BN>
-size_t oz_smem() { return (size_t)kOzStages * (kBM * 128 + BN * 128) + 1024; }
+// two sets of B digit tiles, the A ring, 1 KiB for the alignment
+size_t oz_smem() { return (size_t)2 * kOzBSet + (size_t)kOzAStages * kOzA + 1024; }
 
 }  // namespace
 
@@ -912,12 +1011,9 @@ cudaError_t configure_tc_kernels() {
   e = cudaFuncSetAttribute(tc_gemm_grouped_kernel<kTcFP16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem<kTcFP16, 128>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(oz_square_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem<64>());
+  e = cudaFuncSetAttribute(oz_square_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(oz_square_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem<64>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(oz_square_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)oz_smem<128>());
+  return cudaFuncSetAttribute(oz_square_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
 }
 
 // Workspace of the tensor-core squaring: row / column scales and the digit
@@ -948,17 +1044,13 @@ int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStr
                  (P32 && k == 1) ? P32 : (float2*)nullptr);
   if (e == cudaSuccess) e = launch_k(oz_slice_b_kernel, dim3(eb), dim3(256), 0, s, P, d, (const int*)sig, B);
   if (e != cudaSuccess) return -1;
-  // 128-column tiles halve the operand bytes per MMA; below d = 2048 they
-  // would leave SMs idle (fewer than 256 tiles), so 64 there
-  const int BN = d >= 2048 ? 128 : 64;
   CUtensorMap mA, mB;
   if (!make_map(&mA, A, kTcBF16, (int64_t)kOzS * 2 * d, 2 * (int64_t)d, kBM) ||
-      !make_map(&mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, BN))
+      !make_map(&mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, kOzBN))
     return -1;
   OzArgs a{tau, sig, C, P32 ? P32 + k * dd : nullptr, d, err};
-  const unsigned grid = (unsigned)((2 * d / kBM) * (d / BN));
-  e = BN == 128 ? launch_k(oz_square_kernel<128>, dim3(grid), dim3(192), oz_smem<128>(), s, mA, mB, a)
-                : launch_k(oz_square_kernel<64>, dim3(grid), dim3(192), oz_smem<64>(), s, mA, mB, a);
+  const unsigned grid = (unsigned)((2 * d / kBM) * (d / kOzBN));
+  e = launch_k(oz_square_kernel, dim3(grid), dim3(kOzThreads), oz_smem(), s, mA, mB, a);
   return e == cudaSuccess ? 4 : -1;
 }
 
@@ -1112,10 +1204,10 @@ bool oz_square_item(const Instance& in, char* ws, int k, bool want_c64, OzItem* 
                  reinterpret_cast<int*>(ws + in.off_err)};
   if (!ws) return true;
   return make_map(&it->mA, A, kTcBF16, (int64_t)kOzS * 2 * d, 2 * (int64_t)d, kBM) &&
-         make_map(&it->mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, 64);
+         make_map(&it->mB, B, kTcBF16, (int64_t)kOzS * d, 2 * (int64_t)d, kOzBN);
 }
 
-int64_t oz_square_tiles(const Instance& in) { return (2 * in.d / kBM) * (in.d / 64); }
+int64_t oz_square_tiles(const Instance& in) { return (2 * in.d / kBM) * (in.d / kOzBN); }
 
 int launch_square_oz_grouped(const OzItem* items, int nitems, int64_t sblocks, int64_t elems, int64_t tiles,
                              cudaStream_t s) {
@@ -1124,7 +1216,7 @@ int launch_square_oz_grouped(const OzItem* items, int nitems, int64_t sblocks, i
   cudaError_t e = launch_k(oz_scale_grouped_kernel, dim3((unsigned)sblocks), dim3(256), 0, s, items, nitems);
   if (e == cudaSuccess) e = launch_k(oz_slice_grouped_kernel, dim3(eb), dim3(256), 0, s, items, nitems, elems);
   if (e == cudaSuccess)
-    e = launch_k(oz_square_grouped_kernel, dim3((unsigned)tiles), dim3(192), oz_smem<64>(), s, items, nitems);
+    e = launch_k(oz_square_grouped_kernel, dim3((unsigned)tiles), dim3(kOzThreads), oz_smem(), s, items, nitems);
   return e == cudaSuccess ? 3 : -1;
 }
 

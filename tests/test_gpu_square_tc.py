@@ -68,6 +68,29 @@ def test_signed_permutation_is_exact(q):
         ref = ref @ ref
 
 
+@pytest.mark.parametrize("nmat", [8, 10, 12])
+def test_extreme_digits_accumulate_exactly(q, nmat):
+    """Every entry c = -(127 2^48 + 128 sum_(j<6) 2^(8j)) 2^-55 (in [0.5, 1), so
+    its row and column scale is 2^0), whose balanced base-256 digits are -127
+    then six times -128: the digit products are +2^14 (16256 or 16129 with a
+    leading digit) and the integer sums of the accumulation windows reach the
+    largest value the windows allow (up to 14 * 2^20, against 2^24). The square
+    of c J (J all ones) is c^2 d J; the formed digit pairs miss it only by the
+    pairs dropped below 2^-53. One unit lost in a window sum of weight w moves
+    the result by 2^(-8 w - 14 - nmat) of itself: above the tolerance of 4 ulps
+    for the weights w <= 3 (window sums up to 12 * 2^20); the lower weights
+    lie below FP64 resolution."""
+    from fractions import Fraction
+    d = 1 << nmat
+    c = -(127 * Fraction(2) ** 48 + 128 * sum(Fraction(2) ** (8 * j) for j in range(6))) / Fraction(2) ** 55
+    assert float(c) == c and 0.5 <= -c < 1  # exact in FP64
+    U = np.full((d, d), float(c), dtype=np.complex128)
+    tc = powers(q, U, 2, q.FLAG_SQUARE_TC)
+    exact = float(c * c * d)
+    assert np.all(tc[1].imag == 0.0)
+    assert np.abs(tc[1].real - exact).max() <= 4 * U64 * abs(exact)
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
 def test_end_to_end_against_oracle(q, prec, tol):
     rng = np.random.default_rng(11)
