@@ -122,6 +122,16 @@ typedef enum {
                                   /* 28 exact bf16 digit products accumulated  */
                                   /* in integers (the Ozaki scheme); single-   */
                                   /* instance plans                            */
+#define QPE_FLAG_LEVEL_TC 0x200u /* QPE_FP64, nmat = 4, fused schedule with   */
+                                 /* an 8-point top level: that level's        */
+                                 /* contraction on the tcgen05 tensor cores   */
+                                 /* with FP64-grade accuracy (7 balanced      */
+                                 /* 8-bit digits per operand, per-pencil and  */
+                                 /* table power-of-two scales, 28 exact bf16  */
+                                 /* digit products folded in integers; the    */
+                                 /* twiddles, DFT, |X|^2 and readout in FP64);*/
+                                 /* ignored where those conditions do not     */
+                                 /* hold (QPE_INFO_TC_TOP_LEVEL tells)        */
 #define QPE_FLAG_CHECK_UNITARY 0x40u /* the POWERS stage first forms U^dagger */
                                      /* U in FP64; if any entry of            */
                                      /* U^dagger U - I exceeds 1e-8 in        */

@@ -88,12 +88,15 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   }
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
   if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
-  // the fused top level on the tensor cores: a split precision, d = 16 (a
-  // 16-point top level), at least one tile of 128 pencils per rank, histogram only
-  in.tc_top = in.fused && !batched && is_tc(prec) && in.nmat == 4 && !in.keep_state && !in.levels.empty() &&
-              in.levels[0].r == 4 && in.levels[0].logna - in.shard_log >= 7;
+  // the fused top level on the tensor cores, d = 16, at least one tile of 128
+  // pencils per rank, histogram only: a split precision with a 16-point top
+  // level, or FP64 (QPE_FLAG_LEVEL_TC) with an 8-point one
+  const bool tc_top_ok = in.fused && !batched && in.nmat == 4 && !in.keep_state && !in.levels.empty() &&
+                         in.levels[0].logna - in.shard_log >= 7;
+  const bool fp64_top = prec == QPE_FP64 && (flags & QPE_FLAG_LEVEL_TC) && tc_top_ok && in.levels[0].r == 3;
+  in.tc_top = (tc_top_ok && is_tc(prec) && in.levels[0].r == 4) || fp64_top;
   in.tc_top_prec = prec;
-  if (in.tc_top) in.off_tctab = take(qpe::tc_top_table_bytes());
+  if (in.tc_top) in.off_tctab = take(fp64_top ? qpe::oz_top_table_bytes() : qpe::tc_top_table_bytes());
   in.fft = qpe::make_fft_plan(in.nmeas - (in.shard_plain ? in.shard_log : 0), d, elem_size(prec));
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a
@@ -119,7 +122,8 @@ qpe_status check_desc(const qpe_plan_desc* desc, bool batched = false) {
   if (desc->nmeas < 1 || desc->nmeas > kMaxNmeas) return QPE_ERR_ARG;
   if (desc->prec < QPE_FP64 || desc->prec > QPE_C64_TF32X3) return QPE_ERR_ARG;
   if (desc->flags & ~(QPE_FLAG_GATE_SWEEP | QPE_FLAG_GRAPH | QPE_FLAG_TIMING | QPE_FLAG_PLAIN | QPE_FLAG_KEEP_STATE |
-                      QPE_FLAG_REPEAT_U | QPE_FLAG_CHECK_UNITARY | QPE_FLAG_AUTOTUNE | QPE_FLAG_SQUARE_TC))
+                      QPE_FLAG_REPEAT_U | QPE_FLAG_CHECK_UNITARY | QPE_FLAG_AUTOTUNE | QPE_FLAG_SQUARE_TC |
+                      QPE_FLAG_LEVEL_TC))
     return QPE_ERR_ARG;
   if ((desc->flags & QPE_FLAG_REPEAT_U) && (!(desc->flags & QPE_FLAG_GATE_SWEEP) || desc->nmeas > 14))
     return QPE_ERR_UNSUPPORTED;
@@ -1109,6 +1113,7 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
   cudaError_t e = qpe::configure_kernels();
   if (e == cudaSuccess) e = qpe::configure_batched_kernels();
   if (e == cudaSuccess && (is_tc(p->prec) || (p->flags & QPE_FLAG_SQUARE_TC))) e = qpe::configure_tc_kernels();
+  if (e == cudaSuccess && (p->flags & QPE_FLAG_LEVEL_TC)) e = qpe::configure_oz_top_kernel();
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute");
   {
     const char* v = getenv("QPE_PDL");

@@ -570,6 +570,11 @@ inline void finalize_readout(const Instance& in, char* ws, int count, cudaStream
 }
 size_t level_smem_bytes(int logd, int mode, size_t esize);
 size_t tc_top_table_bytes();
+// the FP64 top level on the tensor cores (d = 16, 8-point top level)
+size_t oz_top_table_bytes();
+cudaError_t configure_oz_top_kernel();
+int launch_oz_top(const Instance& in, char* ws, const LevelArgs<double2>& la, cudaStream_t s, cudaEvent_t* top_ev,
+                  int64_t* grid_out);
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 // a level of a sharded plan computes only this rank's outcomes when it has at

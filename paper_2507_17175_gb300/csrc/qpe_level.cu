@@ -1352,16 +1352,18 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s,
       a.hist = reinterpret_cast<double*>(ws + in.off_hist);
       a.parts = reinterpret_cast<Partial*>(ws + in.off_partials);
       if (grid > kReduceBlocks) grid = kReduceBlocks;
-      if constexpr (sizeof(C) == 8) {
-        if (in.tc_top) {
-          const int r = launch_tc_top(in, ws, a, s, top_ev, &grid);
-          if (r < 0) return -1;
-          launches += r;
-          finalize_readout(in, ws, (int)grid, s);
-          if (cudaPeekAtLastError() != cudaSuccess) return -1;
-          ++launches;
-          break;
-        }
+      if (in.tc_top) {
+        int r;
+        if constexpr (sizeof(C) == 8)
+          r = launch_tc_top(in, ws, a, s, top_ev, &grid);
+        else
+          r = launch_oz_top(in, ws, a, s, top_ev, &grid);
+        if (r < 0) return -1;
+        launches += r;
+        finalize_readout(in, ws, (int)grid, s);
+        if (cudaPeekAtLastError() != cudaSuccess) return -1;
+        ++launches;
+        break;
       }
       if (top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
       if (keep_state) {

@@ -1,0 +1,561 @@
+// FP64 top level of the fused schedule on the tcgen05 tensor cores, d = 16
+// and an 8-point top level (QPE_FLAG_LEVEL_TC with QPE_FP64), with the
+// accuracy of FP64 arithmetic.
+//
+// The level (the last step of the recursion of the fused schedule) takes, for
+// every pencil y_a, the level below's Z[y_a] (16 complex values) and forms
+// T[m_b][i] = sum_k M[m_b][i][k] Z[y_a][k] for m_b < 8 (M[m_b] the level's
+// table), X[y_a + N_a y_b][i] = sum_(m_b) w_8^(m_b y_b) (w_N^(m_b y_a)
+// T[m_b][i]) and the histogram bin sum_i |X|^2 / N^2.
+//
+// The contraction is one real product per tile of 128 pencils: A = the Z rows
+// (K = 32 reals, re / im interleaved), B = the table's real embedding with
+// rows n = 16 i + 2 m_b + c (c: re / im of T). Both are split into 7 balanced
+// 8-bit digits (the Ozaki scheme): A per pencil at its own power-of-two scale
+// 2^tau, B at one scale 2^sigma, x = 2^(tau - 55) sum_(s<7) a_s 2^(8 (6 - s)),
+// |a_s| <= 128 (exact in bf16). The 28 digit pairs (s, t) of weight
+// w = s + t <= 6 are formed; a pair's products are integers of at most 2^14,
+// so a weight's accumulator (w + 1 pairs over K = 32) stays below 2^22 and is
+// exact in FP32. With acc_w the weight sums,
+//   T = 2^(tau + sigma - 30) (hi + 2^-32 lo),
+//   hi = sum_(w<=2) acc_w 2^(8 (2 - w)),  lo = sum_(w>=3) acc_w 2^(8 (6 - w)),
+// integers below 2^36 and 2^46, turned into FP64 exactly by the magic-number
+// construction and combined with one rounding. The omitted pairs and the
+// digit rounding lie at 2^-53 of |Z| |M| K, the error bound of an FP64 dot
+// product. Twiddles, the 8-point DFT, |X|^2 and the readout run in FP64; the
+// scale 2^(2 (tau + sigma - 30)) goes into the histogram's 1 / N^2.
+//
+// Roles (384 threads, one CTA per SM, persistent over the tiles):
+//   warps 0-2   producers: Z rows -> digit tiles (shared memory, 128-byte
+//               swizzled K-major, two digits per 128-byte row), the pencils'
+//               twiddles w_N^(m_b y_a) and scales (two buffers);
+//   warp 3      tensor memory, and lane 0 issues the MMAs: per chunk of two
+//               columns i (32 table rows), 28 pairs x 2 K-steps of
+//               M = 128, N = 32 into seven weight accumulators (224 columns;
+//               two chunk buffers);
+//   warps 4-11  drain: two warps per tensor-memory lane quarter, one column i
+//               each (16 table rows) per chunk; weights -> integers -> FP64,
+//               twiddle, DFT, |X|^2; the two warps' sums meet through tensor
+//               memory columns 448-463.
+// Every wait is a bounded mbarrier wait; an expired wait sets QPE_ERR_TIMEOUT.
+#include "qpe_internal.cuh"
+#include "qpe_tcgen05.cuh"
+
+#include <cuda_bf16.h>
+
+namespace qpe {
+using namespace tcg;
+
+namespace {
+
+constexpr int kOtL = 8, kOtD = 16, kOtS = 7;
+constexpr int kOtRows = 128;                   // pencils per tile (MMA M)
+constexpr int kOtN = 2 * kOtD * kOtL;          // 256 table rows
+constexpr int kOtChunks = kOtD / 2;            // two columns i per chunk
+constexpr int kOtThreads = 384;
+constexpr int kOtProducers = 96;
+constexpr uint32_t kOtSlabA = kOtRows * 128;   // digits [2q | 2q+1] of 128 pencils, 16 KiB
+constexpr uint32_t kOtSlabB = kOtN * 128;      // 32 KiB
+constexpr uint32_t kOtBufCols = kOtS * 32;     // one chunk's seven weight accumulators
+constexpr uint32_t kOtSqCol = 2 * kOtBufCols;  // column 448: the hand-over of the two halves
+constexpr size_t kOtBBytes = 4 * (size_t)kOtSlabB;
+constexpr size_t kOtABytes = 4 * (size_t)kOtSlabA;
+constexpr size_t kOtTwBytes = (size_t)kOtRows * (kOtL - 1) * sizeof(double2);
+constexpr size_t kOtSmem = kOtBBytes + kOtABytes + 2 * kOtTwBytes + 2 * kOtRows * sizeof(int) + 1024;
+static_assert(kOtSmem <= 227 * 1024, "shared memory of the FP64 top level");
+
+// 2^52 + 2^51: an integer v with |v| < 2^51 becomes the double 2^52 + 2^51 + v
+// when added to these bits; kOtMagicC = (2^52 + 2^51) (1 + 2^-32) undoes both
+// offsets in hi + 2^-32 lo.
+constexpr long long kOtMagic = 0x4338000000000000LL;
+constexpr double kOtMagicC = 6755399441055744.0 + 1572864.0;
+
+__device__ __forceinline__ double ot_pow2(int e) {  // 2^e, -1022 <= e <= 1023
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// the largest exponent field among the values, as the scale exponent t with
+// |x| < 2^t; zero or subnormal only: 0 (their digits are zero)
+__device__ __forceinline__ int ot_scale_exp(int emax) {
+  if (emax == 0) return 0;
+  const int t = emax - 1022;
+  return t < -960 ? -960 : t;
+}
+
+// balanced base-256 digits of round(x 2^(55 - t)), most significant first
+__device__ __forceinline__ void ot_digits(double x, double sc, int (&dg)[kOtS]) {
+  long long F = __double2ll_rn(x * sc);  // |F| <= 2^55
+#pragma unroll
+  for (int s = kOtS - 1; s >= 1; --s) {
+    int r = (int)(F & 255);
+    if (r >= 128) r -= 256;
+    dg[s] = r;
+    F = (F - r) >> 8;
+  }
+  dg[0] = (int)F;
+}
+
+// bf16 bits of a small integer (|v| <= 256: exact in the upper half of the float)
+__device__ __forceinline__ uint32_t ot_bf16(int v) { return __float_as_uint((float)v) >> 16; }
+
+__device__ __forceinline__ double2 ot_cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// 8-point DFT X[k] = sum_n x[n] exp(-2 pi i n k / 8), natural order in and out
+// (radix-2 decimation in frequency; the factors -i and (+-1 - i) / sqrt 2 by
+// additions)
+__device__ __forceinline__ void ot_dft8(double2 (&x)[8]) {
+  constexpr double c = 0.70710678118654752440;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const double2 u = x[p], v = x[p + 4];
+    x[p] = make_double2(u.x + v.x, u.y + v.y);
+    const double2 d = make_double2(u.x - v.x, u.y - v.y);
+    if (p == 0) x[4] = d;
+    if (p == 1) x[5] = make_double2(c * (d.x + d.y), c * (d.y - d.x));
+    if (p == 2) x[6] = make_double2(d.y, -d.x);
+    if (p == 3) x[7] = make_double2(c * (d.y - d.x), -c * (d.x + d.y));
+  }
+#pragma unroll
+  for (int g = 0; g < 8; g += 4) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const double2 u = x[g + p], v = x[g + p + 2];
+      x[g + p] = make_double2(u.x + v.x, u.y + v.y);
+      const double2 d = make_double2(u.x - v.x, u.y - v.y);
+      x[g + p + 2] = p == 0 ? d : make_double2(d.y, -d.x);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < 8; g += 2) {
+    const double2 u = x[g], v = x[g + 1];
+    x[g] = make_double2(u.x + v.x, u.y + v.y);
+    x[g + 1] = make_double2(u.x - v.x, u.y - v.y);
+  }
+  double2 t = x[1];
+  x[1] = x[4];
+  x[4] = t;
+  t = x[3];
+  x[3] = x[6];
+  x[6] = t;
+}
+
+// The MMAs of one chunk: pair (S, T) into weight S + T, two K = 16 steps of
+// the 32-wide digit (digit s sits in half s & 1 of slab s >> 1).
+template <int S, int T>
+__device__ __forceinline__ void ot_pairs(uint32_t d0, uint64_t a0, uint64_t b0, uint32_t idesc) {
+  if constexpr (S < kOtS) {
+    if constexpr (S + T < kOtS) {
+      const uint64_t ad = a0 + (uint64_t)((S >> 1) * (kOtSlabA >> 4) + (S & 1) * 4);
+      const uint64_t bd = b0 + (uint64_t)((T >> 1) * (kOtSlabB >> 4) + (T & 1) * 4);
+      const uint32_t d = d0 + (uint32_t)((S + T) * 32);
+      umma_k<kTcBF16>(d, ad, bd, idesc, S == 0 ? 0u : 1u);
+      umma_k<kTcBF16>(d, ad + 2, bd + 2, idesc, 1u);
+      ot_pairs<S, T + 1>(d0, a0, b0, idesc);
+    } else {
+      ot_pairs<S + 1, 0>(d0, a0, b0, idesc);
+    }
+  }
+}
+
+// The table's digits: rows n = 16 i + 2 m_b + c, K index k2 = 2 k + c'
+// (value Re M, -Im M, Im M, Re M for (c, c') = (0,0), (0,1), (1,0), (1,1)),
+// stored [slab q][row n][64 bf16] with digit 2q in the first 32 and 2q + 1 in
+// the second; sigma (|M| < 2^sigma) after the digits. One CTA.
+__global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __restrict__ tab,
+                                                           unsigned short* __restrict__ out, int* __restrict__ sigma) {
+  pdl_begin();
+  __shared__ int emax_s;
+  if (threadIdx.x == 0) emax_s = 0;
+  __syncthreads();
+  int em = 0;
+  for (int e = threadIdx.x; e < kOtD * kOtL * kOtD; e += blockDim.x) {
+    const double2 m = tab[e];
+    em = max(em, (int)((__double_as_longlong(m.x) >> 52) & 0x7ff));
+    em = max(em, (int)((__double_as_longlong(m.y) >> 52) & 0x7ff));
+  }
+  atomicMax(&emax_s, em);
+  __syncthreads();
+  const int sg = ot_scale_exp(emax_s);
+  const double sc = ot_pow2(55 - sg);
+  for (int e = threadIdx.x; e < kOtN * 32; e += blockDim.x) {
+    const int n = e >> 5, k2 = e & 31;
+    const int i = n >> 4, mb = (n >> 1) & 7, c = n & 1;
+    const int k = k2 >> 1, cp = k2 & 1;
+    const double2 m = tab[k * (kOtL * kOtD) + mb * kOtD + i];
+    const double v = c == 0 ? (cp == 0 ? m.x : -m.y) : (cp == 0 ? m.y : m.x);
+    int dg[kOtS];
+    ot_digits(v, sc, dg);
+#pragma unroll
+    for (int s = 0; s < kOtS; ++s)
+      out[((size_t)(s >> 1) * kOtN + n) * 64 + (s & 1) * 32 + k2] = (unsigned short)ot_bf16(dg[s]);
+  }
+  if (threadIdx.x == 0) *sigma = sg;
+  pdl_trigger();
+}
+
+struct OzTopArgs {
+  const double2* seeds;  // Z of the level below (compact when that level is sharded)
+  const uint4* btab;     // the table's digit slabs (128 KiB)
+  const int* sigma;
+  const double2* tw_lo;
+  const double2* tw_hi;
+  double* hist;
+  Partial* parts;
+  int* err;
+  int64_t ntiles;  // local pencils / 128
+  int nmeas, logna, htw, sh, rk, seed_sh, seed_rk;
+  double pscale;   // 1 / N^2
+};
+
+__global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a) {
+  pdl_begin();
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  unsigned char* Bs = base;
+  unsigned char* As = base + kOtBBytes;
+  double2* twS = reinterpret_cast<double2*>(As + kOtABytes);  // [2][128][7]
+  int* tauS = reinterpret_cast<int*>(twS + 2 * kOtRows * (kOtL - 1));  // [2][128]
+  __shared__ uint64_t a_full, a_empty, tw_empty[2], t_full[2], t_empty[2], sq_full, sq_empty, mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ Partial sp[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&a_full, kOtRows);
+    mbar_init(&a_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tw_empty[b], 8);
+      mbar_init(&t_full[b], 1);
+      mbar_init(&t_empty[b], 8);
+    }
+    mbar_init(&sq_full, 4);
+    mbar_init(&sq_empty, 4);
+    mbar_init(&mma_done, 1);
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 3) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // the table's digit slabs into shared memory, swizzled (16-byte chunks)
+  for (int q = threadIdx.x; q < (int)(kOtBBytes / 16); q += kOtThreads) {
+    const int slab = q / (kOtN * 8), n = (q >> 3) % kOtN, c = q & 7;
+    *reinterpret_cast<uint4*>(Bs + slab * kOtSlabB + sw128_offset(n, c)) = __ldg(a.btab + q);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* vfail = &fail;
+  const int lna = a.logna - a.sh;
+  const int64_t tw_mask = (int64_t(1) << a.htw) - 1;
+  const int lvl_shift = a.nmeas - a.logna - 3;
+  const int64_t lvl_mask = (int64_t(1) << (a.logna + 3)) - 1;
+
+  if (warp < 3) {
+    // ------------------------------------------------------------ producers
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+      const int tb = it & 1;
+      if (it >= 1 && !mbar_wait(&a_empty, (it - 1) & 1)) {
+        atomicExch(&fail, 1);
+        break;
+      }
+      if (it >= 2 && !mbar_wait(&tw_empty[tb], ((it >> 1) - 1) & 1)) {
+        atomicExch(&fail, 1);
+        break;
+      }
+      if (*vfail) break;
+      for (int p = threadIdx.x; p < kOtRows; p += kOtProducers) {
+        const int64_t j = t * kOtRows + p;
+        const double2* src = a.seeds + ((a.seed_rk + (j << a.seed_sh)) << 4);
+        double2 z[kOtD];
+        int emax = 0;
+#pragma unroll
+        for (int k = 0; k < kOtD; ++k) {
+          z[k] = __ldg(src + k);
+          emax = max(emax, (int)((__double_as_longlong(z[k].x) >> 52) & 0x7ff));
+          emax = max(emax, (int)((__double_as_longlong(z[k].y) >> 52) & 0x7ff));
+        }
+        const int tau = ot_scale_exp(emax);
+        const double sc = ot_pow2(55 - tau);
+        // digit s of reals 8 g .. 8 g + 7 -> chunk (s & 1) 4 + g of slab s >> 1
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          int dg[8][kOtS];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            ot_digits(z[4 * g + u].x, sc, dg[2 * u]);
+            ot_digits(z[4 * g + u].y, sc, dg[2 * u + 1]);
+          }
+#pragma unroll
+          for (int s = 0; s < kOtS; ++s) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) w[h] = ot_bf16(dg[2 * h][s]) | (ot_bf16(dg[2 * h + 1][s]) << 16);
+            *reinterpret_cast<uint4*>(As + (s >> 1) * kOtSlabA + sw128_offset(p, (s & 1) * 4 + g)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+        const int64_t ya = a.rk + (j << a.sh);
+        double2* tw = twS + (tb * kOtRows + p) * (kOtL - 1);
+#pragma unroll
+        for (int m = 1; m < kOtL; ++m) {
+          const int64_t ex = (((int64_t)m * ya) & lvl_mask) << lvl_shift;
+          tw[m - 1] = ot_cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
+        }
+        tauS[tb * kOtRows + p] = tau;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&a_full);
+      }
+    }
+  } else if (warp == 3) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc<kTcBF16, 32>();
+      const uint64_t a0 = sw128_desc(smem_u32(As)), b00 = sw128_desc(smem_u32(Bs));
+      int it = 0;
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+        if (!mbar_wait(&a_full, it & 1) || *vfail) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < kOtChunks; ++c, ++g) {
+          const int buf = g & 1;
+          if (g >= 2 && !mbar_wait(&t_empty[buf], ((g >> 1) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          ot_pairs<0, 0>(tmem + (uint32_t)buf * kOtBufCols, a0, b00 + (uint64_t)(c * (32 * 128 >> 4)), idesc);
+          umma_commit(&t_full[buf]);
+        }
+        if (!ok) break;
+        umma_commit(&a_empty);
+      }
+      if (!ok) atomicExch(&fail, 1);
+      // every MMA issued has finished before tensor memory is released
+      umma_commit(&mma_done);
+      if (!mbar_wait(&mma_done, 0)) atomicExch(&fail, 1);
+    }
+  } else {
+    // ------------------------------------------------------------ drain
+    const int h = (warp - 4) >> 2;  // column i = 2 c + h of chunk c
+    const int q = warp & 3;         // tensor-memory lane quarter
+    const int row = q * 32 + lane;  // pencil of this thread within the tile
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    double best = -1.0, wsum = 0.0, psum = 0.0;
+    int64_t besty = INT64_MAX;
+    int it = 0;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+      const int tb = it & 1;
+      bool got = mbar_wait(&a_full, it & 1);  // this tile's twiddles and scales are written
+      if (!__all_sync(0xffffffffu, got && !*vfail)) {
+        ok = false;
+        break;
+      }
+      const double2* tw = twS + (tb * kOtRows + row) * (kOtL - 1);
+      const int tau = tauS[tb * kOtRows + row];
+      double acc[kOtL];
+#pragma unroll
+      for (int y = 0; y < kOtL; ++y) acc[y] = 0.0;
+      for (int c = 0; c < kOtChunks; ++c, ++g) {
+        const int buf = g & 1;
+        got = mbar_wait(&t_full[buf], (g >> 1) & 1);
+        got = __all_sync(0xffffffffu, got && !*vfail) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!got) {
+          ok = false;
+          break;
+        }
+        // weights -> integer groups: g0 = acc_0, g1 = 2^8 acc_1 + acc_2,
+        // g2 = 2^8 acc_3 + acc_4, g3 = 2^8 acc_5 + acc_6 (all below 2^31)
+        const uint32_t col = lane_base + (uint32_t)buf * kOtBufCols + (uint32_t)(h * 16);
+        int g0[16], g1[16], g2[16], g3[16];
+        uint32_t v[16];
+        tmem_ld16(col, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) g0[e] = __float2int_rn(__uint_as_float(v[e]));
+        tmem_ld16(col + 32, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) g1[e] = __float2int_rn(__uint_as_float(v[e])) << 8;
+        tmem_ld16(col + 64, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) g1[e] += __float2int_rn(__uint_as_float(v[e]));
+        tmem_ld16(col + 96, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) g2[e] = __float2int_rn(__uint_as_float(v[e])) << 8;
+        tmem_ld16(col + 128, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) g2[e] += __float2int_rn(__uint_as_float(v[e]));
+        tmem_ld16(col + 160, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) g3[e] = __float2int_rn(__uint_as_float(v[e])) << 8;
+        tmem_ld16(col + 192, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) g3[e] += __float2int_rn(__uint_as_float(v[e]));
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&t_empty[buf]);
+        // T[m_b] (columns 2 m_b + c of this half) in units of 2^(tau + sigma - 30)
+        double2 x[kOtL];
+#pragma unroll
+        for (int m = 0; m < kOtL; ++m) {
+          double re, im;
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int e = 2 * m + cc;
+            const long long hi = ((long long)g0[e] << 16) + g1[e];
+            const long long lo = ((long long)g2[e] << 16) + g3[e];
+            const double val =
+                fma(__longlong_as_double(lo + kOtMagic), 0x1p-32, __longlong_as_double(hi + kOtMagic) - kOtMagicC);
+            if (cc == 0)
+              re = val;
+            else
+              im = val;
+          }
+          x[m] = make_double2(re, im);
+        }
+#pragma unroll
+        for (int m = 1; m < kOtL; ++m) x[m] = ot_cmul(x[m], tw[m - 1]);
+        ot_dft8(x);
+#pragma unroll
+        for (int y = 0; y < kOtL; ++y) acc[y] = fma(x[y].x, x[y].x, fma(x[y].y, x[y].y, acc[y]));
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tw_empty[tb]);  // done with this tile's twiddles and scales
+      if (!ok) break;
+      // the two halves' sums meet in tensor memory (columns 448 .. 463)
+      const uint32_t sqc = lane_base + kOtSqCol;
+      if (h == 1) {
+        got = it < 1 || mbar_wait(&sq_empty, (it - 1) & 1);
+        if (!__all_sync(0xffffffffu, got && !*vfail)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t w[16];
+#pragma unroll
+        for (int y = 0; y < kOtL; ++y) {
+          w[2 * y] = (uint32_t)__double2loint(acc[y]);
+          w[2 * y + 1] = (uint32_t)__double2hiint(acc[y]);
+        }
+        tmem_st16(sqc, w);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sq_full);
+      } else {
+        got = mbar_wait(&sq_full, it & 1);
+        if (!__all_sync(0xffffffffu, got && !*vfail)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t w[16];
+        tmem_ld16(sqc, w);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sq_empty);
+        // |T|^2 carried 2^(2 (tau + sigma - 30)); with 1 / N^2, in two exact
+        // power-of-two steps
+        const int ex = 2 * (tau + *a.sigma - 30);
+        const int e1 = ex / 2, e2 = ex - e1;
+        const double f = a.pscale * ot_pow2(e1) * ot_pow2(e2);
+        const int64_t j = t * kOtRows + row;
+#pragma unroll
+        for (int y = 0; y < kOtL; ++y) {
+          const double s = acc[y] + __hiloint2double((int)w[2 * y + 1], (int)w[2 * y]);
+          const double pv = s * f;
+          const int64_t yl = j + ((int64_t)y << lna);
+          a.hist[yl] = pv;
+          const int64_t yy = a.rk + (yl << a.sh);
+          better(best, besty, pv, yy);
+          wsum = fma(pv, (double)yy, wsum);
+          psum += pv;
+        }
+      }
+    }
+    if (!ok) atomicExch(&fail, 1);
+    if (h == 0) {  // readout partial of this CTA: the four h = 0 warps
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int64_t oy = __shfl_xor_sync(0xffffffffu, besty, off);
+        better(best, besty, ob, oy);
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+        psum += __shfl_xor_sync(0xffffffffu, psum, off);
+      }
+      if (lane == 0) sp[q] = Partial{best, besty, wsum, psum};
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial r = sp[0];
+    for (int w = 1; w < 4; ++w) merge_partial(r, sp[w]);
+    a.parts[blockIdx.x] = r;
+    if (fail) atomicExch(a.err, (int)QPE_ERR_TIMEOUT);
+  }
+  if (warp == 3)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  pdl_trigger();
+}
+
+}  // namespace
+
+size_t oz_top_table_bytes() { return kOtBBytes + 256; }
+
+cudaError_t configure_oz_top_kernel() {
+  return cudaFuncSetAttribute(level_oz_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOtSmem);
+}
+
+// The table's digits, then the persistent kernel (one CTA per SM, at most one
+// per tile). Returns the launches or -1; *grid_out = the readout partials.
+int launch_oz_top(const Instance& in, char* ws, const LevelArgs<double2>& la, cudaStream_t s, cudaEvent_t* top_ev,
+                  int64_t* grid_out) {
+  char* btab = ws + in.off_tctab;
+  int* sigma = reinterpret_cast<int*>(btab + kOtBBytes);
+  if (launch_k(oz_top_table_kernel, dim3(1), dim3(256), 0, s, la.tab, reinterpret_cast<unsigned short*>(btab),
+               sigma) != cudaSuccess)
+    return -1;
+  OzTopArgs a{};
+  a.seeds = la.seeds;
+  a.btab = reinterpret_cast<const uint4*>(btab);
+  a.sigma = sigma;
+  a.tw_lo = la.tw_lo;
+  a.tw_hi = la.tw_hi;
+  a.hist = la.hist;
+  a.parts = la.parts;
+  a.err = reinterpret_cast<int*>(ws + in.off_err);
+  a.ntiles = (int64_t(1) << (la.logna - la.sh)) / kOtRows;
+  a.nmeas = la.nmeas;
+  a.logna = la.logna;
+  a.htw = la.htw;
+  a.sh = la.sh;
+  a.rk = la.rk;
+  a.seed_sh = la.seed_sh;
+  a.seed_rk = la.seed_rk;
+  a.pscale = la.pscale;
+  int64_t grid = in.nsm > 0 ? in.nsm : 1;
+  if (grid > a.ntiles) grid = a.ntiles;
+  if (grid > kReduceBlocks) grid = kReduceBlocks;
+  if (top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
+  if (launch_k(level_oz_top_kernel, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a) != cudaSuccess) return -1;
+  if (top_ev && record_event(top_ev[1], s) != cudaSuccess) return -1;
+  *grid_out = grid;
+  return 2;
+}
+
+}  // namespace qpe

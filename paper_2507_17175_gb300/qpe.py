@@ -41,6 +41,7 @@ FLAG_REPEAT_U = 0x20
 FLAG_CHECK_UNITARY = 0x40
 FLAG_AUTOTUNE = 0x80
 FLAG_SQUARE_TC = 0x100
+FLAG_LEVEL_TC = 0x200
 STAGE_POWERS, STAGE_SWEEP, STAGE_FFT, STAGE_REDUCE = 1, 2, 3, 4
 INFO_WORKSPACE_BYTES, INFO_STATE_BYTES, INFO_FFT_PASSES, INFO_LAST_LAUNCHES, INFO_INSTANCES = 1, 2, 3, 4, 5
 INFO_SQUARE_TILE = 6

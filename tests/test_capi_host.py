@@ -62,8 +62,9 @@ def test_plan_sizes_workspace(q):
     (2, 31, 0, 0, "ERR_ARG"),
     (2, 4, 7, 0, "ERR_ARG"),
     (2, 4, -1, 0, "ERR_ARG"),
-    (2, 4, 0, 0x200, "ERR_ARG"),
+    (2, 4, 0, 0x400, "ERR_ARG"),
     (9, 8, 1, 0x100, "OK"),   # QPE_FLAG_SQUARE_TC
+    (2, 4, 0, 0x200, "OK"),   # QPE_FLAG_LEVEL_TC (ignored outside its shape)
     (2, 4, 0, 0x80, "OK"),    # QPE_FLAG_AUTOTUNE
     (2, 4, 2, 0, "ERR_UNSUPPORTED"),
     (7, 4, 1, 1, "ERR_UNSUPPORTED"),
@@ -138,6 +139,31 @@ def test_plan_batched_validation(q):
     assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0
     q.LIB.qpe_destroy(h)
     assert q.plan_workspace(3, 8, q.C64_FP16X2, q.FLAG_GATE_SWEEP)[0] == q.ERR_UNSUPPORTED
+
+
+def test_fp64_level_tc_plans(q):
+    """QPE_FLAG_LEVEL_TC puts the FP64 top level on the tensor cores only for
+    nmat = 4 with at least one 128-pencil tile (per rank) and no kept state;
+    the table's digit slabs add 128 KiB to the workspace."""
+    st, ws0, h = q.plan_workspace(4, 12, q.FP64, 0)
+    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0
+    q.LIB.qpe_destroy(h)
+    st, ws1, h = q.plan_workspace(4, 12, q.FP64, q.FLAG_LEVEL_TC)
+    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 1
+    assert q.LIB.qpe_query(h, q.INFO_TOP_LEVEL_BITS) == 3
+    q.LIB.qpe_destroy(h)
+    assert ws1 - ws0 >= 128 * 1024
+    for nmat, nmeas, prec, flags in [(4, 9, 0, 0), (3, 12, 0, 0), (5, 12, 0, 0), (4, 12, 1, 0), (4, 12, 0, 0x10)]:
+        st, _, h = q.plan_workspace(nmat, nmeas, prec, flags | q.FLAG_LEVEL_TC)
+        assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0, (nmat, nmeas, prec, flags)
+        q.LIB.qpe_destroy(h)
+    # sharded: each rank needs a whole tile of its own pencils
+    st, _, h = q.plan_shard_workspace(4, 14, q.FP64, q.FLAG_LEVEL_TC, 1, 4)
+    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 1
+    q.LIB.qpe_destroy(h)
+    st, _, h = q.plan_shard_workspace(4, 12, q.FP64, q.FLAG_LEVEL_TC, 1, 8)
+    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0
+    q.LIB.qpe_destroy(h)
 
 
 def test_bf16x3_is_refused_everywhere(q):

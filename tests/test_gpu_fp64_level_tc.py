@@ -1,0 +1,143 @@
+"""QPE_FLAG_LEVEL_TC: the FP64 fused schedule's top level (d = 16, 8-point top
+level) with its contraction on the tcgen05 tensor cores by exact digit
+products (7 balanced 8-bit digits per operand, the Ozaki scheme) and the
+twiddles, DFT, |X|^2 and readout in FP64.
+
+Pins: the oracle's histogram and readout within the FP64 tolerance; the
+CUDA-core FP64 plan on the same input within a few units of rounding; the
+analytic family's exact phases (delta peaks); sharded plans equal the
+unsharded one bit for bit; the full 34-qubit workload against the closed form.
+"""
+import numpy as np
+import pytest
+
+from oracle import fejer, gates, readout
+from paper_2507_17175_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+U64 = np.finfo(np.float64).eps / 2
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2507_17175_gb300 import qpe
+    return qpe
+
+
+def _run(q, inst, flags):
+    plan = q.Plan(inst.nmat, inst.nmeas, q.FP64, flags)
+    plan.load(inst.U, inst.psi)
+    plan.run()
+    out = plan.probs()
+    on_tc = plan.query(q.INFO_TC_TOP_LEVEL)
+    plan.close()
+    return out, on_tc
+
+
+@pytest.mark.parametrize("nmeas", [10, 11, 12, 13, 15, 17])
+def test_against_oracle_and_cuda_cores(q, nmeas):
+    rng = np.random.default_rng(40 + nmeas)
+    inst = W.haar_instance(rng, 4, nmeas, superposition=True)
+    ref = gates.qpe_probabilities(inst.U, inst.psi, nmeas)
+    (P, am, pa, pm), on_tc = _run(q, inst, q.FLAG_LEVEL_TC)
+    assert on_tc == 1
+    assert np.abs(P - ref).max() <= 1e-10
+    top2 = np.sort(ref)[-2:]
+    if top2[1] - top2[0] > 1e-9:
+        assert am == readout.argmax_lowest(ref)
+    assert abs(pm - readout.phase_weighted_mean(ref)) <= 1e-9
+    assert abs(P.sum() - ref.sum()) <= 1e-10
+    # the CUDA-core FP64 path: both are FP64-accurate, so they agree to a few
+    # units of rounding of the largest bin
+    (P1, am1, _, pm1), on_tc1 = _run(q, inst, 0)
+    assert on_tc1 == 0
+    assert np.abs(P - P1).max() <= 64 * U64 * max(P1.max(), 1e-300) * np.sqrt(1 << nmeas)
+    assert am == am1 and abs(pm - pm1) <= 1e-12
+
+
+def test_flag_ignored_outside_its_shape(q):
+    """Other target sizes, too few pencils for one tile, or complex64: the
+    flag changes nothing (the CUDA-core schedule runs, same histogram)."""
+    for nmat, nmeas, prec in [(3, 12, 0), (5, 12, 0), (4, 8, 0), (4, 12, 1)]:
+        rng = np.random.default_rng(nmat * 100 + nmeas)
+        inst = W.haar_instance(rng, nmat, nmeas, superposition=True)
+        plans = []
+        for flags in (0, q.FLAG_LEVEL_TC):
+            plan = q.Plan(nmat, nmeas, prec, flags)
+            plan.load(inst.U, inst.psi)
+            plan.run()
+            plans.append((plan.probs(), plan.query(q.INFO_TC_TOP_LEVEL)))
+            plan.close()
+        assert plans[1][1] == 0
+        assert np.array_equal(plans[0][0][0], plans[1][0][0])
+
+
+@pytest.mark.parametrize("j", [0, 5, 15])
+def test_analytic_family_exact_phases(q, j):
+    """phi_j = j / 16 and psi = x_j: the distribution is a delta at
+    y = j 2^(Nmeas - 4) (Sec. 3)."""
+    nmeas = 12
+    inst = W.analytic_instance(4, nmeas, j)
+    (P, am, pa, pm), on_tc = _run(q, inst, q.FLAG_LEVEL_TC)
+    assert on_tc == 1
+    y0 = j << (nmeas - 4)
+    assert am == y0
+    assert abs(P[y0] - 1.0) <= 1e-10
+    P[y0] = 0.0
+    assert np.abs(P).max() <= 1e-10
+
+
+@pytest.mark.parametrize("world,nmeas", [(2, 12), (4, 14), (8, 13)])
+def test_shards_equal_unsharded(q, world, nmeas):
+    rng = np.random.default_rng(7 * world + nmeas)
+    inst = W.haar_instance(rng, 4, nmeas, superposition=True)
+    (Pf, amf, paf, pmf), _ = _run(q, inst, q.FLAG_LEVEL_TC)
+    parts, reads = [], []
+    for r in range(world):
+        sp = q.ShardedPlan(4, nmeas, q.FP64, q.FLAG_LEVEL_TC, r, world)
+        assert sp.query(q.INFO_TC_TOP_LEVEL) == 1
+        sp.load(inst.U, inst.psi)
+        sp.run()
+        parts.append(sp.probs()[0].copy())
+        reads.append(sp.shard_readout())
+        sp.close()
+    assert np.array_equal(q.interleave_shards(parts), Pf)
+    am, pa, pm, tot = q.merge_shard_readouts(reads)
+    assert am == amf and pa == paf and abs(pm - pmf) <= 1e-12
+
+
+def test_c5_full_size_against_closed_form(q):
+    """Nmat = 4, Nmeas = 30 (34 qubits), the benchmark's FP64 workload with the
+    flag: sampled bins and the peaks against the Fejer closed form, to the
+    input's FP64 floor (as the CUDA-core FP64 path is held to)."""
+    import torch
+    inst = W.c5(30)
+    plan = q.Plan(inst.nmat, inst.nmeas, q.FP64, q.FLAG_LEVEL_TC)
+    assert plan.query(q.INFO_TC_TOP_LEVEL) == 1
+    plan.load(inst.U, inst.psi)
+    plan.run()
+    out = torch.empty(inst.N, dtype=torch.float64, device="cuda")
+    _, am, pa, pm = plan.probs(out)
+    N = inst.N
+    rng = np.random.default_rng(5)
+    y0 = np.floor(N * inst.phases).astype(np.int64)
+    ys = np.concatenate([rng.integers(0, N, 1 << 16), y0 % N, (y0 + 1) % N])
+    got = out[torch.from_numpy(ys).cuda()].cpu().numpy()
+    Q = fejer.probabilities(inst.phases, inst.weights, inst.nmeas, y=ys)
+    tol = max(1e-10, 2 * N * U64 * np.sqrt(inst.d))
+    assert np.abs(got - Q).max() <= tol
+    cand = np.unique(np.concatenate([(y0 + k) % N for k in (-1, 0, 1, 2)]))
+    Qc = fejer.probabilities(inst.phases, inst.weights, inst.nmeas, y=cand)
+    order = np.argsort(Qc)
+    if Qc[order[-1]] - Qc[order[-2]] > 10 * tol:
+        assert am == cand[order[-1]]
+    assert abs(float(out.sum().item()) - 1.0) <= 1e-8
+    del out
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
