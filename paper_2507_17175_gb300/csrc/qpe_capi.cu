@@ -88,15 +88,21 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   }
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
   if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
-  // the fused top level on the tensor cores, d = 16, at least one tile of 128
-  // pencils per rank, histogram only: a split precision with a 16-point top
-  // level, or FP64 (QPE_FLAG_LEVEL_TC) with an 8-point one
-  const bool tc_top_ok = in.fused && !batched && in.nmat == 4 && !in.keep_state && !in.levels.empty() &&
-                         in.levels[0].logna - in.shard_log >= 7;
-  const bool fp64_top = prec == QPE_FP64 && (flags & QPE_FLAG_LEVEL_TC) && tc_top_ok && in.levels[0].r == 3;
-  in.tc_top = (tc_top_ok && is_tc(prec) && in.levels[0].r == 4) || fp64_top;
+  // the fused top level on the tensor cores, d = 16, histogram only: a split
+  // precision with a 16-point top level and at least one tile of 128 pencils
+  // per rank, or FP64 (QPE_FLAG_LEVEL_TC) with an 8-point one of at least 128
+  // pencils in all (a rank with fewer runs one partial tile, so that sharded
+  // and unsharded plans take the same arithmetic)
+  const bool tc_top_ok = in.fused && !batched && in.nmat == 4 && !in.keep_state && !in.levels.empty();
+  const bool fp64_top = prec == QPE_FP64 && (flags & QPE_FLAG_LEVEL_TC) && tc_top_ok && in.levels[0].r == 3 &&
+                        in.levels[0].logna >= 7;
+  in.tc_top = (tc_top_ok && is_tc(prec) && in.levels[0].r == 4 && in.levels[0].logna - in.shard_log >= 7) ||
+              fp64_top;
   in.tc_top_prec = prec;
-  if (in.tc_top) in.off_tctab = take(fp64_top ? qpe::oz_top_table_bytes() : qpe::tc_top_table_bytes());
+  // FP64: the lower 8-point levels too (each one that fills 128-pencil tiles)
+  in.oz_levels = prec == QPE_FP64 && (flags & QPE_FLAG_LEVEL_TC) && in.fused && !batched && in.nmat == 4;
+  if (in.tc_top || in.oz_levels)
+    in.off_tctab = take(in.oz_levels ? qpe::oz_top_table_bytes() : qpe::tc_top_table_bytes());
   in.fft = qpe::make_fft_plan(in.nmeas - (in.shard_plain ? in.shard_log : 0), d, elem_size(prec));
   if (in.nmat <= QPE_MAX_FUSED_NMAT) {
     // level buffers for the fused schedule (also allotted to plain plans so a

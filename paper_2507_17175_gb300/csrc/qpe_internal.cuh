@@ -297,10 +297,12 @@ struct Instance {
   int shard_log = 0, shard_rank = 0;
   bool shard_plain = false;           // sharded plain schedule: one exchange per run
   size_t off_send = 0, off_recv = 0;  // its all-to-all buffers, [2^shard_log][N / 4^shard_log][d] each
-  // top level of the fused schedule on the tensor cores (FP16x2 / TF32x3, d = 16)
+  // top level of the fused schedule on the tensor cores (FP16x2 / TF32x3, or
+  // FP64 with QPE_FLAG_LEVEL_TC; d = 16)
   bool tc_top = false;
   int tc_top_prec = 0;
-  size_t off_tctab = 0;  // its fp16 table operands (both orders)
+  bool oz_levels = false;  // FP64: every 8-point level with a 128-pencil tile per rank on the tensor cores
+  size_t off_tctab = 0;    // the table operands (fp16 / tf32 splits, or the FP64 table's digit slabs)
   int nsm = 0;           // multiprocessors of the bound device
   bool keep_state = false;
   bool loaded = false;
@@ -573,8 +575,8 @@ size_t tc_top_table_bytes();
 // the FP64 top level on the tensor cores (d = 16, 8-point top level)
 size_t oz_top_table_bytes();
 cudaError_t configure_oz_top_kernel();
-int launch_oz_top(const Instance& in, char* ws, const LevelArgs<double2>& la, cudaStream_t s, cudaEvent_t* top_ev,
-                  int64_t* grid_out);
+int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, bool top, cudaStream_t s,
+                    cudaEvent_t* top_ev, int64_t* grid_out);
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 // a level of a sharded plan computes only this rank's outcomes when it has at

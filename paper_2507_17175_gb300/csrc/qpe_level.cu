@@ -1343,7 +1343,17 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s,
       if (per > iters) per = iters;
       C* out = reinterpret_cast<C*>(ws + in.off_zbuf[li & 1]);
       a.xout = out;
-      launch_level2<C, 0>(in.nmat, (unsigned)(per * ncg), level_smem_bytes(in.nmat, 0, esize), s, a);
+      bool on_tc = false;
+      if constexpr (sizeof(C) == 16) {
+        // FP64 with QPE_FLAG_LEVEL_TC: an 8-point level of at least 128 pencils
+        // in all (the same levels with or without sharding)
+        if (in.oz_levels && L.r == 3 && L.logna >= 7) {
+          if (launch_oz_level(in, ws, a, false, s, nullptr, nullptr) < 0) return -1;
+          ++launches;  // the table's digits; the level kernel is counted below
+          on_tc = true;
+        }
+      }
+      if (!on_tc) launch_level2<C, 0>(in.nmat, (unsigned)(per * ncg), level_smem_bytes(in.nmat, 0, esize), s, a);
       cur_seed = out;
     } else {
       const size_t smem = level_smem_bytes(in.nmat, 1, esize);
@@ -1357,7 +1367,7 @@ int launch_levels(const Instance& in, char* ws, bool keep_state, cudaStream_t s,
         if constexpr (sizeof(C) == 8)
           r = launch_tc_top(in, ws, a, s, top_ev, &grid);
         else
-          r = launch_oz_top(in, ws, a, s, top_ev, &grid);
+          r = launch_oz_level(in, ws, a, true, s, top_ev, &grid);
         if (r < 0) return -1;
         launches += r;
         finalize_readout(in, ws, (int)grid, s);

@@ -1,12 +1,13 @@
-// FP64 top level of the fused schedule on the tcgen05 tensor cores, d = 16
-// and an 8-point top level (QPE_FLAG_LEVEL_TC with QPE_FP64), with the
-// accuracy of FP64 arithmetic.
+// FP64 levels of the fused schedule on the tcgen05 tensor cores, d = 16 and
+// 8-point levels (QPE_FLAG_LEVEL_TC with QPE_FP64), with the accuracy of FP64
+// arithmetic.
 //
-// The level (the last step of the recursion of the fused schedule) takes, for
-// every pencil y_a, the level below's Z[y_a] (16 complex values) and forms
-// T[m_b][i] = sum_k M[m_b][i][k] Z[y_a][k] for m_b < 8 (M[m_b] the level's
-// table), X[y_a + N_a y_b][i] = sum_(m_b) w_8^(m_b y_b) (w_N^(m_b y_a)
-// T[m_b][i]) and the histogram bin sum_i |X|^2 / N^2.
+// A level takes, for every pencil y_a, the level below's Z[y_a] (16 complex
+// values) and forms T[m_b][i] = sum_k M[m_b][i][k] Z[y_a][k] for m_b < 8
+// (M[m_b] the level's table) and X[y_a + N_a y_b][i] = sum_(m_b)
+// w_8^(m_b y_b) (w_N'^(m_b y_a) T[m_b][i]). The top level (MODE 1) keeps only
+// the histogram bin sum_i |X|^2 / N^2 and the readout; a lower level (MODE 0)
+// writes X, the next level's Z.
 //
 // The contraction is one real product per tile of 128 pencils: A = the Z rows
 // (K = 32 reals, re / im interleaved), B = the table's real embedding with
@@ -23,7 +24,8 @@
 // construction and combined with one rounding. The omitted pairs and the
 // digit rounding lie at 2^-53 of |Z| |M| K, the error bound of an FP64 dot
 // product. Twiddles, the 8-point DFT, |X|^2 and the readout run in FP64; the
-// scale 2^(2 (tau + sigma - 30)) goes into the histogram's 1 / N^2.
+// scale 2^(2 (tau + sigma - 30)) goes into the histogram's 1 / N^2 (MODE 1),
+// or 2^(tau + sigma - 30) into the twiddles and the m_b = 0 term (MODE 0).
 //
 // Roles (384 threads, one CTA per SM, persistent over the tiles):
 //   warps 0-2   producers: Z rows -> digit tiles (shared memory, 128-byte
@@ -35,8 +37,8 @@
 //               two chunk buffers);
 //   warps 4-11  drain: two warps per tensor-memory lane quarter, one column i
 //               each (16 table rows) per chunk; weights -> integers -> FP64,
-//               twiddle, DFT, |X|^2; the two warps' sums meet through tensor
-//               memory columns 448-463.
+//               twiddle, DFT, then |X|^2 (the two warps' sums meet through
+//               tensor memory columns 448-463) or the store of X.
 // Every wait is a bounded mbarrier wait; an expired wait sets QPE_ERR_TIMEOUT.
 #include "qpe_internal.cuh"
 #include "qpe_tcgen05.cuh"
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __rest
 
 struct OzTopArgs {
   const double2* seeds;  // Z of the level below (compact when that level is sharded)
+  double2* xout;         // MODE 0: X of this level
   const uint4* btab;     // the table's digit slabs (128 KiB)
   const int* sigma;
   const double2* tw_lo;
@@ -204,12 +207,14 @@ struct OzTopArgs {
   double* hist;
   Partial* parts;
   int* err;
-  int64_t ntiles;  // local pencils / 128
+  int64_t npencils;  // local pencils (a power of two)
+  int64_t ntiles;    // tiles of 128 pencils (one partial tile below 128 pencils)
   int nmeas, logna, htw, sh, rk, seed_sh, seed_rk;
   double pscale;   // 1 / N^2
 };
 
-__global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a) {
+template <int MODE>
+__global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
   pdl_begin();
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* base =
@@ -258,6 +263,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a
   const int lna = a.logna - a.sh;
   const int64_t tw_mask = (int64_t(1) << a.htw) - 1;
   const int lvl_shift = a.nmeas - a.logna - 3;
+  const int sigma = *a.sigma;
   const int64_t lvl_mask = (int64_t(1) << (a.logna + 3)) - 1;
 
   if (warp < 3) {
@@ -276,43 +282,47 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a
       if (*vfail) break;
       for (int p = threadIdx.x; p < kOtRows; p += kOtProducers) {
         const int64_t j = t * kOtRows + p;
-        const double2* src = a.seeds + ((a.seed_rk + (j << a.seed_sh)) << 4);
+        const bool have = j < a.npencils;  // rows past a partial tile's pencils: zero digits
+        const double2* src = a.seeds + (have ? ((a.seed_rk + (j << a.seed_sh)) << 4) : 0);
         double2 z[kOtD];
         int emax = 0;
 #pragma unroll
         for (int k = 0; k < kOtD; ++k) {
-          z[k] = __ldg(src + k);
+          z[k] = have ? __ldg(src + k) : make_double2(0.0, 0.0);
           emax = max(emax, (int)((__double_as_longlong(z[k].x) >> 52) & 0x7ff));
           emax = max(emax, (int)((__double_as_longlong(z[k].y) >> 52) & 0x7ff));
         }
         const int tau = ot_scale_exp(emax);
         const double sc = ot_pow2(55 - tau);
-        // digit s of reals 8 g .. 8 g + 7 -> chunk (s & 1) 4 + g of slab s >> 1
+        // digit s of reals 4 g .. 4 g + 3 (two complex values) -> the half g & 1
+        // of chunk (s & 1) 4 + (g >> 1) of slab s >> 1
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          int dg[8][kOtS];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            ot_digits(z[4 * g + u].x, sc, dg[2 * u]);
-            ot_digits(z[4 * g + u].y, sc, dg[2 * u + 1]);
-          }
+        for (int g = 0; g < 8; ++g) {
+          int dg[4][kOtS];
+          ot_digits(z[2 * g].x, sc, dg[0]);
+          ot_digits(z[2 * g].y, sc, dg[1]);
+          ot_digits(z[2 * g + 1].x, sc, dg[2]);
+          ot_digits(z[2 * g + 1].y, sc, dg[3]);
 #pragma unroll
           for (int s = 0; s < kOtS; ++s) {
-            uint32_t w[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) w[h] = ot_bf16(dg[2 * h][s]) | (ot_bf16(dg[2 * h + 1][s]) << 16);
-            *reinterpret_cast<uint4*>(As + (s >> 1) * kOtSlabA + sw128_offset(p, (s & 1) * 4 + g)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
+            const uint32_t w0 = ot_bf16(dg[0][s]) | (ot_bf16(dg[1][s]) << 16);
+            const uint32_t w1 = ot_bf16(dg[2][s]) | (ot_bf16(dg[3][s]) << 16);
+            *reinterpret_cast<uint2*>(As + (s >> 1) * kOtSlabA + sw128_offset(p, (s & 1) * 4 + (g >> 1)) +
+                                      (g & 1) * 8) = make_uint2(w0, w1);
           }
         }
         const int64_t ya = a.rk + (j << a.sh);
         double2* tw = twS + (tb * kOtRows + p) * (kOtL - 1);
+        // MODE 0: the output scale 2^(tau + sigma - 30) rides on the twiddles
+        const int es = tau + sigma - 30;
+        const double tsc = MODE == 0 ? ot_pow2(es) : 1.0;
 #pragma unroll
         for (int m = 1; m < kOtL; ++m) {
           const int64_t ex = (((int64_t)m * ya) & lvl_mask) << lvl_shift;
-          tw[m - 1] = ot_cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
+          const double2 w = ot_cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
+          tw[m - 1] = MODE == 0 ? make_double2(w.x * tsc, w.y * tsc) : w;
         }
-        tauS[tb * kOtRows + p] = tau;
+        tauS[tb * kOtRows + p] = es;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&a_full);
       }
@@ -368,7 +378,9 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a
         break;
       }
       const double2* tw = twS + (tb * kOtRows + row) * (kOtL - 1);
-      const int tau = tauS[tb * kOtRows + row];
+      const int es = tauS[tb * kOtRows + row];  // this pencil's scale exponent tau + sigma - 30
+      const double sc0 = MODE == 0 ? ot_pow2(es) : 1.0;
+      const int64_t jt = t * kOtRows + row;     // local pencil index
       double acc[kOtL];
 #pragma unroll
       for (int y = 0; y < kOtL; ++y) acc[y] = 0.0;
@@ -431,13 +443,23 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a
         }
 #pragma unroll
         for (int m = 1; m < kOtL; ++m) x[m] = ot_cmul(x[m], tw[m - 1]);
+        if (MODE == 0) x[0] = make_double2(x[0].x * sc0, x[0].y * sc0);
         ot_dft8(x);
+        if (MODE == 0) {
+          const int i = 2 * c + h;
+          if (jt < a.npencils) {
 #pragma unroll
-        for (int y = 0; y < kOtL; ++y) acc[y] = fma(x[y].x, x[y].x, fma(x[y].y, x[y].y, acc[y]));
+            for (int y = 0; y < kOtL; ++y) a.xout[((jt + ((int64_t)y << lna)) << 4) + i] = x[y];
+          }
+        } else {
+#pragma unroll
+          for (int y = 0; y < kOtL; ++y) acc[y] = fma(x[y].x, x[y].x, fma(x[y].y, x[y].y, acc[y]));
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&tw_empty[tb]);  // done with this tile's twiddles and scales
       if (!ok) break;
+      if (MODE == 0) continue;
       // the two halves' sums meet in tensor memory (columns 448 .. 463)
       const uint32_t sqc = lane_base + kOtSqCol;
       if (h == 1) {
@@ -471,25 +493,25 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a
         if (lane == 0) mbar_arrive(&sq_empty);
         // |T|^2 carried 2^(2 (tau + sigma - 30)); with 1 / N^2, in two exact
         // power-of-two steps
-        const int ex = 2 * (tau + *a.sigma - 30);
-        const int e1 = ex / 2, e2 = ex - e1;
-        const double f = a.pscale * ot_pow2(e1) * ot_pow2(e2);
-        const int64_t j = t * kOtRows + row;
+        const double f = a.pscale * ot_pow2(es) * ot_pow2(es);
+        const int64_t j = jt;
+        if (j < a.npencils) {
 #pragma unroll
-        for (int y = 0; y < kOtL; ++y) {
-          const double s = acc[y] + __hiloint2double((int)w[2 * y + 1], (int)w[2 * y]);
-          const double pv = s * f;
-          const int64_t yl = j + ((int64_t)y << lna);
-          a.hist[yl] = pv;
-          const int64_t yy = a.rk + (yl << a.sh);
-          better(best, besty, pv, yy);
-          wsum = fma(pv, (double)yy, wsum);
-          psum += pv;
+          for (int y = 0; y < kOtL; ++y) {
+            const double s = acc[y] + __hiloint2double((int)w[2 * y + 1], (int)w[2 * y]);
+            const double pv = s * f;
+            const int64_t yl = j + ((int64_t)y << lna);
+            a.hist[yl] = pv;
+            const int64_t yy = a.rk + (yl << a.sh);
+            better(best, besty, pv, yy);
+            wsum = fma(pv, (double)yy, wsum);
+            psum += pv;
+          }
         }
       }
     }
     if (!ok) atomicExch(&fail, 1);
-    if (h == 0) {  // readout partial of this CTA: the four h = 0 warps
+    if (MODE == 1 && h == 0) {  // readout partial of this CTA: the four h = 0 warps
       for (int off = 16; off > 0; off >>= 1) {
         const double ob = __shfl_xor_sync(0xffffffffu, best, off);
         const int64_t oy = __shfl_xor_sync(0xffffffffu, besty, off);
@@ -503,9 +525,11 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0) {
-    Partial r = sp[0];
-    for (int w = 1; w < 4; ++w) merge_partial(r, sp[w]);
-    a.parts[blockIdx.x] = r;
+    if (MODE == 1) {
+      Partial r = sp[0];
+      for (int w = 1; w < 4; ++w) merge_partial(r, sp[w]);
+      a.parts[blockIdx.x] = r;
+    }
     if (fail) atomicExch(a.err, (int)QPE_ERR_TIMEOUT);
   }
   if (warp == 3)
@@ -518,13 +542,17 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_top_kernel(OzTopArgs a
 size_t oz_top_table_bytes() { return kOtBBytes + 256; }
 
 cudaError_t configure_oz_top_kernel() {
-  return cudaFuncSetAttribute(level_oz_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOtSmem);
+  cudaError_t e = cudaFuncSetAttribute(level_oz_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOtSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(level_oz_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOtSmem);
 }
 
-// The table's digits, then the persistent kernel (one CTA per SM, at most one
-// per tile). Returns the launches or -1; *grid_out = the readout partials.
-int launch_oz_top(const Instance& in, char* ws, const LevelArgs<double2>& la, cudaStream_t s, cudaEvent_t* top_ev,
-                  int64_t* grid_out) {
+// One FP64 level on the tensor cores: the level table's digits, then the
+// persistent kernel (one CTA per SM, at most one per tile). top: the final
+// level (histogram + readout partials; *grid_out = the partials), otherwise
+// X into la.xout. Returns the launches or -1.
+int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, bool top, cudaStream_t s,
+                    cudaEvent_t* top_ev, int64_t* grid_out) {
   char* btab = ws + in.off_tctab;
   int* sigma = reinterpret_cast<int*>(btab + kOtBBytes);
   if (launch_k(oz_top_table_kernel, dim3(1), dim3(256), 0, s, la.tab, reinterpret_cast<unsigned short*>(btab),
@@ -532,6 +560,7 @@ int launch_oz_top(const Instance& in, char* ws, const LevelArgs<double2>& la, cu
     return -1;
   OzTopArgs a{};
   a.seeds = la.seeds;
+  a.xout = la.xout;
   a.btab = reinterpret_cast<const uint4*>(btab);
   a.sigma = sigma;
   a.tw_lo = la.tw_lo;
@@ -539,7 +568,8 @@ int launch_oz_top(const Instance& in, char* ws, const LevelArgs<double2>& la, cu
   a.hist = la.hist;
   a.parts = la.parts;
   a.err = reinterpret_cast<int*>(ws + in.off_err);
-  a.ntiles = (int64_t(1) << (la.logna - la.sh)) / kOtRows;
+  a.npencils = int64_t(1) << (la.logna - la.sh);
+  a.ntiles = (a.npencils + kOtRows - 1) / kOtRows;
   a.nmeas = la.nmeas;
   a.logna = la.logna;
   a.htw = la.htw;
@@ -551,10 +581,12 @@ int launch_oz_top(const Instance& in, char* ws, const LevelArgs<double2>& la, cu
   int64_t grid = in.nsm > 0 ? in.nsm : 1;
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid > kReduceBlocks) grid = kReduceBlocks;
-  if (top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
-  if (launch_k(level_oz_top_kernel, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a) != cudaSuccess) return -1;
-  if (top_ev && record_event(top_ev[1], s) != cudaSuccess) return -1;
-  *grid_out = grid;
+  if (top && top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
+  const cudaError_t e = top ? launch_k(level_oz_kernel<1>, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a)
+                            : launch_k(level_oz_kernel<0>, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a);
+  if (e != cudaSuccess) return -1;
+  if (top && top_ev && record_event(top_ev[1], s) != cudaSuccess) return -1;
+  if (grid_out) *grid_out = grid;
   return 2;
 }
 

@@ -157,13 +157,12 @@ def test_fp64_level_tc_plans(q):
         st, _, h = q.plan_workspace(nmat, nmeas, prec, flags | q.FLAG_LEVEL_TC)
         assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0, (nmat, nmeas, prec, flags)
         q.LIB.qpe_destroy(h)
-    # sharded: each rank needs a whole tile of its own pencils
-    st, _, h = q.plan_shard_workspace(4, 14, q.FP64, q.FLAG_LEVEL_TC, 1, 4)
-    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 1
-    q.LIB.qpe_destroy(h)
-    st, _, h = q.plan_shard_workspace(4, 12, q.FP64, q.FLAG_LEVEL_TC, 1, 8)
-    assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0
-    q.LIB.qpe_destroy(h)
+    # sharded: decided on the level's whole pencil count, as unsharded (a rank
+    # with fewer than 128 pencils runs one partial tile)
+    for world in (4, 8, 16):
+        st, _, h = q.plan_shard_workspace(4, 12, q.FP64, q.FLAG_LEVEL_TC, 1, world)
+        assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 1
+        q.LIB.qpe_destroy(h)
 
 
 def test_bf16x3_is_refused_everywhere(q):
