@@ -457,6 +457,37 @@ qpe_status qpe_shard_finish(qpe_plan_t plan);
  */
 qpe_status qpe_merge_shard_readouts(const qpe_shard_readout_t* parts, int32_t world, qpe_readout_t* out);
 
+/*
+ * qpe_host_alloc / qpe_host_free: page-locked host memory (cudaHostAlloc) of
+ * `bytes` bytes for a plan's host-side inputs and outputs (U, psi, the
+ * histogram of qpe_probs, the state of qpe_state). Copies between the device
+ * and such memory run at the host link's rate, which is not the case for every
+ * page-locked buffer (on GB300 hosts, a large buffer pinned by another route
+ * may be read or written at a fraction of it). The caller owns the memory
+ * and frees it with qpe_host_free (not with free()). QPE_ERR_ARG for
+ * bytes == 0 or ptr == NULL; QPE_ERR_CUDA if the allocation fails, with
+ * *ptr = NULL. qpe_host_free(NULL) is QPE_OK.
+ */
+qpe_status qpe_host_alloc(size_t bytes, void** ptr);
+qpe_status qpe_host_free(void* ptr);
+
+/*
+ * qpe_set_host_histogram: every following whole run of `instance` also copies
+ * its histogram (N / 2^shard_log doubles, local index order as qpe_probs) into
+ * `host`, page-locked memory from qpe_host_alloc that stays valid while it is
+ * set. Where the top level allows it (the FP64 top level on the tensor cores,
+ * QPE_FLAG_LEVEL_TC) the copy overlaps the computation: that level runs in
+ * eight tile ranges and a copy stream forked from the plan's stream moves each
+ * range's bins while the next range computes, joining the plan's stream before
+ * the run ends; otherwise it follows the run on the plan's stream. The copy is
+ * complete when qpe_sync or qpe_probs returns; qpe_probs with probs == host
+ * does not copy again. host = NULL stops the copies. QPE_ERR_ARG if host is
+ * not page-locked host memory, QPE_ERR_STATE before qpe_bind,
+ * QPE_ERR_UNSUPPORTED for batched plans and sharded plans of the plain
+ * schedule. A graph-replayed plan captures the new copies at its next run.
+ */
+qpe_status qpe_set_host_histogram(qpe_plan_t plan, int32_t instance, double* host);
+
 const char* qpe_status_string(qpe_status s);
 /* Last error message recorded on the plan ("" if none; static text for NULL). */
 const char* qpe_last_error(qpe_plan_t plan);

@@ -262,6 +262,11 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
         cudaError_t e = record_event(p->ev[QPE_STAGE_REDUCE], p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventRecord");
       }
+      if (in.host_hist && !qpe::oz_top_copies_host_histogram(in)) {
+        cudaError_t e = cudaMemcpyAsync(in.host_hist, p->ws + in.off_hist, (size_t)(in.N >> in.shard_log) * 8,
+                                        cudaMemcpyDeviceToHost, p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "host histogram copy");
+      }
       in.state_stage = QPE_STAGE_REDUCE;
       in.state_natural = true;
       in.state_valid = in.keep_state;
@@ -317,6 +322,11 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
     if (timing) {
       cudaError_t e = record_event(p->ev[last], p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "cudaEventRecord");
+    }
+    if (in.host_hist && last == QPE_STAGE_REDUCE) {
+      cudaError_t e = cudaMemcpyAsync(in.host_hist, p->ws + in.off_hist, (size_t)(in.N >> in.shard_log) * 8,
+                                      cudaMemcpyDeviceToHost, p->stream);
+      if (e != cudaSuccess) return cuda_fail(p, e, "host histogram copy");
     }
   }
   *launches = n;
@@ -1050,6 +1060,23 @@ qpe_status qpe_shard_finish(qpe_plan_t p) {
   return QPE_OK;
 }
 
+qpe_status qpe_host_alloc(size_t bytes, void** ptr) {
+  if (!ptr) return QPE_ERR_ARG;
+  *ptr = nullptr;
+  if (bytes == 0) return QPE_ERR_ARG;
+  if (cudaHostAlloc(ptr, bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return QPE_ERR_CUDA;
+  }
+  return QPE_OK;
+}
+
+qpe_status qpe_host_free(void* ptr) {
+  if (!ptr) return QPE_OK;
+  return cudaFreeHost(ptr) == cudaSuccess ? QPE_OK : QPE_ERR_CUDA;
+}
+
 qpe_status qpe_merge_shard_readouts(const qpe_shard_readout_t* parts, int32_t world, qpe_readout_t* out) {
   if (!parts || !out || world < 1) return QPE_ERR_ARG;
   int64_t am = -1;
@@ -1277,7 +1304,7 @@ qpe_status qpe_probs(qpe_plan_t p, int32_t instance, double* probs, int64_t* arg
   if (st != QPE_OK) return st;
   if (in->state_stage != QPE_STAGE_REDUCE) return fail(p, QPE_ERR_STATE, "REDUCE has not run");
   cudaError_t e = cudaSuccess;
-  if (probs)
+  if (probs && probs != in->host_hist)  // the host histogram buffer already holds the run's bins
     e = cudaMemcpyAsync(probs, p->ws + in->off_hist, (size_t)(in->N >> in->shard_log) * 8,
                         kind_from_device(ptr_is_device), p->stream);
   qpe::Scalars s;
@@ -1435,9 +1462,43 @@ qpe_status qpe_selftest_timeout(qpe_plan_t p, int32_t instance, uint32_t polls) 
   return QPE_OK;
 }
 
+qpe_status qpe_set_host_histogram(qpe_plan_t p, int32_t instance, double* host) {
+  if (!p) return QPE_ERR_ARG;
+  if (!p->bound) return fail(p, QPE_ERR_STATE, "qpe_bind first");
+  if (p->batched) return fail(p, QPE_ERR_UNSUPPORTED, "batched plans hand out histograms with qpe_probs");
+  Instance* in;
+  qpe_status st = get_instance(p, instance, &in);
+  if (st != QPE_OK) return st;
+  if (in->shard_plain) return fail(p, QPE_ERR_UNSUPPORTED, "a sharded plain plan's histogram comes after the exchange");
+  if (host) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return fail(p, QPE_ERR_ARG, "the host histogram must be page-locked host memory (qpe_host_alloc)");
+    }
+    if (!in->copy_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&in->copy_stream, cudaStreamNonBlocking);
+      for (int c = 0; e == cudaSuccess && c <= qpe::kHostChunks; ++c)
+        e = cudaEventCreateWithFlags(&in->copy_ev[c], cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(p, e, "copy stream");
+    }
+  }
+  in->host_hist = host;
+  if (p->graph_exec) {  // the next run captures the new copies
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  return QPE_OK;
+}
+
 qpe_status qpe_destroy(qpe_plan_t p) {
   if (!p) return QPE_OK;
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  for (Instance& in : p->inst) {
+    for (cudaEvent_t ev : in.copy_ev)
+      if (ev) cudaEventDestroy(ev);
+    if (in.copy_stream) cudaStreamDestroy(in.copy_stream);
+  }
   for (cudaEvent_t ev : p->ev)
     if (ev) cudaEventDestroy(ev);
   delete p;

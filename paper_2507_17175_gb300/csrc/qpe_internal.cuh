@@ -179,6 +179,7 @@ struct Partial {
 };
 
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
+constexpr int kHostChunks = 8;       // parts of a top level whose histogram is copied out while the next computes
 
 // The readout's merge rule, used by every kernel that combines partials: the
 // larger probability wins, an exact tie goes to the lower y, and a NaN best is
@@ -303,6 +304,12 @@ struct Instance {
   int tc_top_prec = 0;
   bool oz_levels = false;  // FP64: every 8-point level with a 128-pencil tile per rank on the tensor cores
   size_t off_tctab = 0;    // the table operands (fp16 / tf32 splits, or the FP64 table's digit slabs)
+  // qpe_set_host_histogram: every run also copies the histogram into this
+  // page-locked host buffer (overlapped with the FP64 tensor-core top level,
+  // which then runs in kHostChunks parts); its copy stream and fork / join events
+  double* host_hist = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[9] = {};
   int nsm = 0;           // multiprocessors of the bound device
   bool keep_state = false;
   bool loaded = false;
@@ -577,6 +584,7 @@ size_t oz_top_table_bytes();
 cudaError_t configure_oz_top_kernel();
 int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, bool top, cudaStream_t s,
                     cudaEvent_t* top_ev, int64_t* grid_out);
+bool oz_top_copies_host_histogram(const Instance& in);
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 // a level of a sharded plan computes only this rank's outcomes when it has at

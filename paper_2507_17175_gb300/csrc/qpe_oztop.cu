@@ -45,6 +45,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace qpe {
 using namespace tcg;
 
@@ -208,7 +210,7 @@ struct OzTopArgs {
   Partial* parts;
   int* err;
   int64_t npencils;  // local pencils (a power of two)
-  int64_t ntiles;    // tiles of 128 pencils (one partial tile below 128 pencils)
+  int64_t tile_begin, tile_end;  // this launch's tiles of 128 pencils (one partial tile below 128 pencils)
   int nmeas, logna, htw, sh, rk, seed_sh, seed_rk;
   double pscale;   // 1 / N^2
 };
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
   if (warp < 3) {
     // ------------------------------------------------------------ producers
     int it = 0;
-    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+    for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end; t += gridDim.x, ++it) {
       const int tb = it & 1;
       if (it >= 1 && !mbar_wait(&a_empty, (it - 1) & 1)) {
         atomicExch(&fail, 1);
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       int it = 0;
       uint32_t g = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+      for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end && ok; t += gridDim.x, ++it) {
         if (!mbar_wait(&a_full, it & 1) || *vfail) {
           ok = false;
           break;
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
     int it = 0;
     uint32_t g = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+    for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end && ok; t += gridDim.x, ++it) {
       const int tb = it & 1;
       bool got = mbar_wait(&a_full, it & 1);  // this tile's twiddles and scales are written
       if (!__all_sync(0xffffffffu, got && !*vfail)) {
@@ -550,7 +552,10 @@ cudaError_t configure_oz_top_kernel() {
 // One FP64 level on the tensor cores: the level table's digits, then the
 // persistent kernel (one CTA per SM, at most one per tile). top: the final
 // level (histogram + readout partials; *grid_out = the partials), otherwise
-// X into la.xout. Returns the launches or -1.
+// X into la.xout. A top level whose instance has a host histogram runs in
+// kHostChunks tile ranges; after each, a copy stream forked from s copies
+// that range's bins to the host while the next range computes, and s joins
+// it at the end. Returns the launches or -1.
 int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, bool top, cudaStream_t s,
                     cudaEvent_t* top_ev, int64_t* grid_out) {
   char* btab = ws + in.off_tctab;
@@ -566,10 +571,9 @@ int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, 
   a.tw_lo = la.tw_lo;
   a.tw_hi = la.tw_hi;
   a.hist = la.hist;
-  a.parts = la.parts;
   a.err = reinterpret_cast<int*>(ws + in.off_err);
   a.npencils = int64_t(1) << (la.logna - la.sh);
-  a.ntiles = (a.npencils + kOtRows - 1) / kOtRows;
+  const int64_t ntiles = (a.npencils + kOtRows - 1) / kOtRows;
   a.nmeas = la.nmeas;
   a.logna = la.logna;
   a.htw = la.htw;
@@ -578,16 +582,50 @@ int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, 
   a.seed_sh = la.seed_sh;
   a.seed_rk = la.seed_rk;
   a.pscale = la.pscale;
-  int64_t grid = in.nsm > 0 ? in.nsm : 1;
-  if (grid > a.ntiles) grid = a.ntiles;
-  if (grid > kReduceBlocks) grid = kReduceBlocks;
+  const int lna = la.logna - la.sh;
+  const bool chunked = top && in.host_hist && in.copy_stream;
+  const int parts = chunked ? (int)std::min<int64_t>(kHostChunks, ntiles) : 1;
+  int64_t nparts = 0;
+  int launches = 1;
   if (top && top_ev && record_event(top_ev[0], s) != cudaSuccess) return -1;
-  const cudaError_t e = top ? launch_k(level_oz_kernel<1>, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a)
-                            : launch_k(level_oz_kernel<0>, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a);
-  if (e != cudaSuccess) return -1;
+  for (int c = 0; c < parts; ++c) {
+    a.tile_begin = ntiles * c / parts;
+    a.tile_end = ntiles * (c + 1) / parts;
+    int64_t grid = in.nsm > 0 ? in.nsm : 1;
+    if (grid > a.tile_end - a.tile_begin) grid = a.tile_end - a.tile_begin;
+    if (grid > kReduceBlocks / parts) grid = kReduceBlocks / parts;
+    a.parts = la.parts + nparts;  // each part's CTAs write their own readout partials
+    nparts += grid;
+    const cudaError_t e = top ? launch_k(level_oz_kernel<1>, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a)
+                              : launch_k(level_oz_kernel<0>, dim3((unsigned)grid), dim3(kOtThreads), kOtSmem, s, a);
+    if (e != cudaSuccess) return -1;
+    ++launches;
+    if (chunked) {
+      // bins j + (y << lna) of this part's pencils j, for every y < 8
+      if (cudaEventRecord(in.copy_ev[c], s) != cudaSuccess) return -1;
+      if (cudaStreamWaitEvent(in.copy_stream, in.copy_ev[c], 0) != cudaSuccess) return -1;
+      const int64_t j0 = a.tile_begin * kOtRows;
+      const int64_t j1 = std::min<int64_t>(a.tile_end * kOtRows, a.npencils);
+      for (int y = 0; y < kOtL; ++y) {
+        const int64_t o = j0 + ((int64_t)y << lna);
+        if (cudaMemcpyAsync(in.host_hist + o, la.hist + o, (size_t)(j1 - j0) * sizeof(double), cudaMemcpyDeviceToHost,
+                            in.copy_stream) != cudaSuccess)
+          return -1;
+      }
+    }
+  }
   if (top && top_ev && record_event(top_ev[1], s) != cudaSuccess) return -1;
-  if (grid_out) *grid_out = grid;
-  return 2;
+  if (chunked) {  // s waits for the last copies
+    if (cudaEventRecord(in.copy_ev[kHostChunks], in.copy_stream) != cudaSuccess) return -1;
+    if (cudaStreamWaitEvent(s, in.copy_ev[kHostChunks], 0) != cudaSuccess) return -1;
+  }
+  if (grid_out) *grid_out = nparts;
+  return launches;
+}
+
+// whether launch_oz_level copies the instance's histogram to the host itself
+bool oz_top_copies_host_histogram(const Instance& in) {
+  return in.tc_top && in.tc_top_prec == QPE_FP64 && in.host_hist && in.copy_stream;
 }
 
 }  // namespace qpe

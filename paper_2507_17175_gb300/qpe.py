@@ -101,6 +101,9 @@ _sig = {
     "qpe_readout_static": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "qpe_measure_fma_peak": (ctypes.c_int, [_i32, _i32, _i32, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
                                             ctypes.POINTER(ctypes.c_double), _vp]),
+    "qpe_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "qpe_set_host_histogram": (ctypes.c_int, [_vp, _i32, _vp]),
+    "qpe_host_free": (ctypes.c_int, [_vp]),
     "qpe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qpe_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -121,6 +124,34 @@ class QpeError(RuntimeError):
 
 def status_string(st: int) -> str:
     return _lib.qpe_status_string(st).decode()
+
+
+class _HostBuffer:
+    """Owner of one qpe_host_alloc block; freed when the last array over it goes."""
+
+    def __init__(self, nbytes: int):
+        self.ptr = _vp()
+        st = _lib.qpe_host_alloc(nbytes, ctypes.byref(self.ptr))
+        if st != OK:
+            raise QpeError(st, f"qpe_host_alloc({nbytes}): {status_string(st)}")
+        self.nbytes = nbytes
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value:
+            _lib.qpe_host_free(self.ptr)
+            self.ptr = _vp()
+
+
+def host_array(shape, dtype=np.float64) -> np.ndarray:
+    """A numpy array in page-locked host memory from qpe_host_alloc (device
+    copies into and out of it run at the host link's rate); the memory is freed
+    with the last reference to the array."""
+    dtype = np.dtype(dtype)
+    count = int(np.prod(shape))
+    buf = _HostBuffer(max(1, count) * dtype.itemsize)
+    raw = (ctypes.c_char * (max(1, count) * dtype.itemsize)).from_address(buf.ptr.value)
+    raw._qpe_buffer = buf  # the array's base (the ctypes block) keeps the allocation alive
+    return np.frombuffer(raw, dtype=dtype, count=count).reshape(shape)
 
 
 def plan_workspace(nmat: int, nmeas: int, prec: int = C64_FP32, flags: int = 0):
@@ -304,6 +335,14 @@ class Plan:
             raise ValueError("U and psi must both be host or both be device buffers")
         self._keep = (U, psi)
         self._check(_lib.qpe_load(self._h, instance, pu, pp, self.nmat, self.nmeas, du), "qpe_load")
+
+    def set_host_histogram(self, host, instance: int = 0):
+        """Every following run also copies the histogram into ``host`` (a
+        host_array of N float64, or None to stop), overlapped with the
+        computation where the top level allows it."""
+        ptr = None if host is None else host.ctypes.data
+        self._check(_lib.qpe_set_host_histogram(self._h, instance, ptr), "qpe_set_host_histogram")
+        self._host_hist = host
 
     def run(self):
         self._check(_lib.qpe_run(self._h), "qpe_run")

@@ -237,3 +237,13 @@ def test_interleave_shards(q):
     P = np.arange(32, dtype=np.float64)
     parts = [P[r::4] for r in range(4)]
     assert np.array_equal(q.interleave_shards(parts), P)
+
+
+def test_host_alloc_arguments(q):
+    """qpe_host_alloc refuses a zero size and a NULL result pointer; freeing
+    NULL is fine (the allocation itself needs a GPU and is tested there)."""
+    import ctypes
+    p = ctypes.c_void_p()
+    assert q.LIB.qpe_host_alloc(0, ctypes.byref(p)) == q.ERR_ARG and not p.value
+    assert q.LIB.qpe_host_alloc(64, None) == q.ERR_ARG
+    assert q.LIB.qpe_host_free(None) == q.OK

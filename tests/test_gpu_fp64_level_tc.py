@@ -141,3 +141,56 @@ def test_c5_full_size_against_closed_form(q):
     plan.close()
     del plan
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec,flags,nmeas", [(0, 0x200, 20), (0, 0x202, 20), (1, 0x2, 18), (0, 0x200, 13)])
+def test_host_histogram_copied_during_the_run(q, prec, flags, nmeas):
+    """qpe_set_host_histogram: after each run the host buffer holds the
+    run's histogram bit for bit (the FP64 tensor-core top level copies it in
+    eight parts while it computes; other paths copy after the run), across
+    graph replays and a changed input; qpe_probs into that buffer returns the
+    same readout without copying again."""
+    import torch
+    rng = np.random.default_rng(nmeas + flags)
+    a = W.haar_instance(rng, 4, nmeas, superposition=True)
+    b = W.haar_instance(rng, 4, nmeas, superposition=True)
+    plan = q.Plan(4, nmeas, prec, flags)
+    host = q.host_array(1 << nmeas)
+    plan.set_host_histogram(host)
+    dev = torch.empty(1 << nmeas, dtype=torch.float64, device="cuda")
+    for inst in (a, b, a):
+        host[...] = -1.0
+        plan.load(inst.U, inst.psi)
+        plan.run()
+        plan.sync()
+        ref = plan.probs(dev)
+        assert np.array_equal(host, dev.cpu().numpy())
+        got = plan.probs(host)
+        assert got[1:] == ref[1:]
+    plan.set_host_histogram(None)
+    host[...] = -1.0
+    plan.run()
+    plan.sync()
+    assert np.all(host == -1.0)  # no copy once unset
+    with pytest.raises(q.QpeError) as e:
+        plan.set_host_histogram(np.zeros(1 << nmeas))  # pageable memory
+    assert e.value.status == q.ERR_ARG
+    plan.close()
+
+
+def test_host_histogram_of_a_shard(q):
+    rng = np.random.default_rng(5)
+    inst = W.haar_instance(rng, 4, 14, superposition=True)
+    parts = []
+    for r in range(2):
+        sp = q.ShardedPlan(4, 14, q.FP64, q.FLAG_LEVEL_TC, r, 2)
+        host = q.host_array(1 << 13)
+        sp.set_host_histogram(host)
+        sp.load(inst.U, inst.psi)
+        sp.run()
+        P = sp.probs()[0]
+        assert np.array_equal(host, P)
+        parts.append(P.copy())
+        sp.close()
+    ref = gates.qpe_probabilities(inst.U, inst.psi, 14)
+    assert np.abs(q.interleave_shards(parts) - ref).max() <= 1e-10

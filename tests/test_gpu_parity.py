@@ -477,3 +477,23 @@ def test_paper_analytic_family(q, prec, flags):
         P, am, _, _ = plan.probs()
         assert am == y
         assert abs(P[y] - p) <= (1e-10 if prec == 0 else 2e-5)
+
+
+def test_host_buffers_from_the_library(q):
+    """qpe.host_array (qpe_host_alloc, page-locked) as the host side of
+    qpe_load and qpe_probs: the same histogram and readout as numpy buffers."""
+    rng = np.random.default_rng(91)
+    inst = W.haar_instance(rng, 3, 12, superposition=True)
+    U_h = q.host_array(inst.U.shape, np.complex128)
+    U_h[...] = inst.U
+    psi_h = q.host_array(inst.psi.shape, np.complex128)
+    psi_h[...] = inst.psi
+    hist_h = q.host_array(inst.N, np.float64)
+    plan = q.Plan(inst.nmat, inst.nmeas, q.FP64)
+    plan.load(U_h, psi_h)
+    plan.run()
+    _, am, pa, pm = plan.probs(hist_h)
+    P, am2, pa2, pm2 = plan.probs()
+    assert np.array_equal(hist_h, P) and (am, pa, pm) == (am2, pa2, pm2)
+    assert np.abs(P - gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas)).max() <= 1e-10
+    del hist_h, U_h, psi_h
