@@ -207,12 +207,13 @@ def level_flops(N: int, d: int, r_top: int) -> float:
 
 def oz_top_fp64_ops(N: int, d: int, r_top: int) -> float:
     """FP64 instructions of the tensor-core FP64 top level (d = 16, r_top = 3):
-    per complex output point 16.5 in the drain (2 per real to turn the integer
-    digit sums into FP64, the twiddle 4 x 7 / 8, the 8-point DFT 56 / 8, |X|^2
-    2); per pencil 92 in the producers (the digit scaling and conversion of 32
-    reals, 7 twiddles); per bin 6 for the scale and the readout."""
+    per complex output point 12.5 in the drain (the twiddle 4 x 7 / 8, the
+    8-point DFT 56 / 8, |X|^2 2; the integer digit sums become FP64 by integer
+    operations); per pencil 28 in the producers (7 twiddles; the digits come
+    from the bits by integer operations); per bin 6 for the scale, the
+    hand-over sum and the readout."""
     L = 1 << r_top
-    return 16.5 * N * d + 92.0 * (N // L) + 6.0 * N
+    return 12.5 * N * d + 28.0 * (N // L) + 6.0 * N
 
 
 def bench_ours(args, rank, world, local_rank):
@@ -393,7 +394,7 @@ def bench_ours(args, rank, world, local_rank):
                     "traffic": recorded_traffic("level_oz_top_c5_fp64"),
                     "kernel": "level_oz_top_kernel (tcgen05 digit products + FP64 drain)",
                     "kernel_ms": round(t_k, 3), "fp64_instr_per_launch": ops,
-                    "fp64_instr_count": "16.5 per complex output point (drain) + 92 per pencil (producers) + 6 per "
+                    "fp64_instr_count": "12.5 per complex output point (drain) + 28 per pencil (producers) + 6 per "
                                         "bin (readout)",
                     "peak_source": "measured: FP64 FMA loop on every SM, CUDA events (qpe_measure_fma_peak), "
                                    "one instruction = one FMA = 2 flop",

@@ -468,7 +468,49 @@ __device__ __forceinline__ void reduce_block(const C* __restrict__ X, double* __
   // widening of the stored value)
   const bool narrow32 = sizeof(C) == 8 && lpr < 32;
   float best_f = -1.f, wsum_f = 0.f, wcomp_f = 0.f, psum_f = 0.f, pcomp_f = 0.f;
-  for (int64_t p0 = gw * rpw; p0 < N; p0 += tw * rpw) {
+  // rows of at most 64 bytes: one thread per outcome y, in y order (coalesced
+  // histogram stores), reading the row at y's digit-reversed position (whole
+  // 32-byte sectors); every lane runs the readout
+  const bool per_y = d * (int)sizeof(C) <= 64;
+  if (per_y) {
+    const int64_t tstep = nblk * blockDim.x;
+    for (int64_t y = bidx * blockDim.x + threadIdx.x; y < N; y += tstep) {
+      const C* row = X + (y_to_pos(g, n, y) << logd);
+      if constexpr (sizeof(C) == 8) {
+        float f = 0.f;
+        for (int k = 0; k < d; ++k) {
+          const C v = __ldg(row + k);
+          f = fmaf(v.x, v.x, fmaf(v.y, v.y, f));
+        }
+        const float v = f * (float)scale;  // scale is a power of two
+        hist[y] = widen_nonneg(v);
+        if (v > best_f || (v == best_f && y < by)) {
+          best_f = v;
+          by = y;
+        }
+        float t1 = v * (float)y - wcomp_f;
+        float t2 = wsum_f + t1;
+        wcomp_f = (t2 - wsum_f) - t1;
+        wsum_f = t2;
+        t1 = v - pcomp_f;
+        t2 = psum_f + t1;
+        pcomp_f = (t2 - psum_f) - t1;
+        psum_f = t2;
+      } else {
+        double acc = 0.0;
+        for (int k = 0; k < d; ++k) {
+          const C v = __ldg(row + k);
+          acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        }
+        const double v = acc * scale;
+        hist[y] = v;
+        better(best, by, v, y);
+        wsum += v * (double)y;
+        psum += v;
+      }
+    }
+  }
+  for (int64_t p0 = per_y ? N : gw * rpw; p0 < N; p0 += tw * rpw) {
     const int64_t p = p0 + lane / lpr;
     const int sub = lane % lpr;
     double acc = 0.0;
@@ -538,7 +580,7 @@ __device__ __forceinline__ void reduce_block(const C* __restrict__ X, double* __
       }
     }
   }
-  if (narrow32) {
+  if (narrow32 || (per_y && sizeof(C) == 8)) {
     best = best_f < 0.f ? -1.0 : widen_nonneg(best_f);
     wsum = (double)wsum_f;
     psum = (double)psum_f;

@@ -20,10 +20,12 @@
 // exact in FP32. With acc_w the weight sums,
 //   T = 2^(tau + sigma - 30) (hi + 2^-32 lo),
 //   hi = sum_(w<=2) acc_w 2^(8 (2 - w)),  lo = sum_(w>=3) acc_w 2^(8 (6 - w)),
-// integers below 2^36 and 2^46, turned into FP64 exactly by the magic-number
-// construction and combined with one rounding. The omitted pairs and the
-// digit rounding lie at 2^-53 of |Z| |M| K, the error bound of an FP64 dot
-// product. Twiddles, the 8-point DFT, |X|^2 and the readout run in FP64; the
+// integers below 2^36 and 2^46. The drain forms V = 2^26 hi + floor(lo / 2^6)
+// (below 2^62; the dropped bits are 2^-26 of a unit, 2^-60 of the pencil's
+// scale) and turns V 2^-26 into FP64 by integer operations on the bits (one
+// rounding to nearest even), so the FP64 pipe, this kernel's bound, is left
+// to the twiddles, the DFT and |X|^2. The omitted digit pairs and the digit
+// rounding lie at 2^-53 of |Z| |M| K, the error bound of an FP64 dot product. Twiddles, the 8-point DFT, |X|^2 and the readout run in FP64; the
 // scale 2^(2 (tau + sigma - 30)) goes into the histogram's 1 / N^2 (MODE 1),
 // or 2^(tau + sigma - 30) into the twiddles and the m_b = 0 term (MODE 0).
 //
@@ -68,11 +70,28 @@ constexpr size_t kOtTwBytes = (size_t)kOtRows * (kOtL - 1) * sizeof(double2);
 constexpr size_t kOtSmem = kOtBBytes + kOtABytes + 2 * kOtTwBytes + 2 * kOtRows * sizeof(int) + 1024;
 static_assert(kOtSmem <= 227 * 1024, "shared memory of the FP64 top level");
 
-// 2^52 + 2^51: an integer v with |v| < 2^51 becomes the double 2^52 + 2^51 + v
-// when added to these bits; kOtMagicC = (2^52 + 2^51) (1 + 2^-32) undoes both
-// offsets in hi + 2^-32 lo.
-constexpr long long kOtMagic = 0x4338000000000000LL;
-constexpr double kOtMagicC = 6755399441055744.0 + 1572864.0;
+// v 2^e2 in FP64 for an integer 0 < |v| < 2^62 (and a result in the normal
+// range), rounded to nearest even, by integer operations: the leading one's
+// position sets the exponent, the 53 bits below it (with the rounding carry
+// running into the exponent) the significand. v = 0 gives 0.
+__device__ __forceinline__ double ot_i64_to_f64(long long v, int e2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  const int sh = 11 - lz;  // bits below the 53 kept
+  unsigned long long m;
+  if (sh <= 0) {
+    m = a << (-sh);
+  } else {
+    const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    m = (a >> sh) + ((rem > half || (rem == half && ((a >> sh) & 1))) ? 1ull : 0ull);
+  }
+  // m holds the leading one at bit 52 (or is 2^53 after a carry): adding it to
+  // (exponent - 1) << 52 yields the bits of the result
+  const unsigned long long eb = (unsigned long long)(1023 + 62 - lz + e2) << 52;
+  return __longlong_as_double((long long)(sgn | (eb + m)));
+}
 
 __device__ __forceinline__ double ot_pow2(int e) {  // 2^e, -1022 <= e <= 1023
   return __longlong_as_double((long long)(1023 + e) << 52);
@@ -86,9 +105,26 @@ __device__ __forceinline__ int ot_scale_exp(int emax) {
   return t < -960 ? -960 : t;
 }
 
+// round(x 2^(55 - t)) for |x| < 2^t by integer operations on x's bits (x =
+// M 2^(E - 1075), M the 53-bit significand; halves round away from zero);
+// zero and subnormal x give 0
+__device__ __forceinline__ long long ot_fixed(double x, int t) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0) return 0;
+  const long long M = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
+  const int k = E - 1020 - t;  // x 2^(55 - t) = M 2^k, k <= 2
+  long long F = 0;
+  if (k >= 0)
+    F = M << k;
+  else if (k > -54)
+    F = (M + (1LL << (-k - 1))) >> (-k);
+  return b < 0 ? -F : F;
+}
+
 // balanced base-256 digits of round(x 2^(55 - t)), most significant first
-__device__ __forceinline__ void ot_digits(double x, double sc, int (&dg)[kOtS]) {
-  long long F = __double2ll_rn(x * sc);  // |F| <= 2^55
+__device__ __forceinline__ void ot_digits(double x, int t, int (&dg)[kOtS]) {
+  long long F = ot_fixed(x, t);  // |F| <= 2^55
 #pragma unroll
   for (int s = kOtS - 1; s >= 1; --s) {
     int r = (int)(F & 255);
@@ -182,7 +218,6 @@ __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __rest
   atomicMax(&emax_s, em);
   __syncthreads();
   const int sg = ot_scale_exp(emax_s);
-  const double sc = ot_pow2(55 - sg);
   for (int e = threadIdx.x; e < kOtN * 32; e += blockDim.x) {
     const int n = e >> 5, k2 = e & 31;
     const int i = n >> 4, mb = (n >> 1) & 7, c = n & 1;
@@ -190,7 +225,7 @@ __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __rest
     const double2 m = tab[k * (kOtL * kOtD) + mb * kOtD + i];
     const double v = c == 0 ? (cp == 0 ? m.x : -m.y) : (cp == 0 ? m.y : m.x);
     int dg[kOtS];
-    ot_digits(v, sc, dg);
+    ot_digits(v, sg, dg);
 #pragma unroll
     for (int s = 0; s < kOtS; ++s)
       out[((size_t)(s >> 1) * kOtN + n) * 64 + (s & 1) * 32 + k2] = (unsigned short)ot_bf16(dg[s]);
@@ -295,16 +330,15 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
           emax = max(emax, (int)((__double_as_longlong(z[k].y) >> 52) & 0x7ff));
         }
         const int tau = ot_scale_exp(emax);
-        const double sc = ot_pow2(55 - tau);
         // digit s of reals 4 g .. 4 g + 3 (two complex values) -> the half g & 1
         // of chunk (s & 1) 4 + (g >> 1) of slab s >> 1
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
           int dg[4][kOtS];
-          ot_digits(z[2 * g].x, sc, dg[0]);
-          ot_digits(z[2 * g].y, sc, dg[1]);
-          ot_digits(z[2 * g + 1].x, sc, dg[2]);
-          ot_digits(z[2 * g + 1].y, sc, dg[3]);
+          ot_digits(z[2 * g].x, tau, dg[0]);
+          ot_digits(z[2 * g].y, tau, dg[1]);
+          ot_digits(z[2 * g + 1].x, tau, dg[2]);
+          ot_digits(z[2 * g + 1].y, tau, dg[3]);
 #pragma unroll
           for (int s = 0; s < kOtS; ++s) {
             const uint32_t w0 = ot_bf16(dg[0][s]) | (ot_bf16(dg[1][s]) << 16);
@@ -434,8 +468,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
             const int e = 2 * m + cc;
             const long long hi = ((long long)g0[e] << 16) + g1[e];
             const long long lo = ((long long)g2[e] << 16) + g3[e];
-            const double val =
-                fma(__longlong_as_double(lo + kOtMagic), 0x1p-32, __longlong_as_double(hi + kOtMagic) - kOtMagicC);
+            const double val = ot_i64_to_f64((hi << 26) + (lo >> 6), -26);
             if (cc == 0)
               re = val;
             else
