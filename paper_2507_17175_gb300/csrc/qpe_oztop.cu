@@ -432,29 +432,30 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         // weights -> integer groups: g0 = acc_0, g1 = 2^8 acc_1 + acc_2,
         // g2 = 2^8 acc_3 + acc_4, g3 = 2^8 acc_5 + acc_6 (all below 2^31)
         const uint32_t col = lane_base + (uint32_t)buf * kOtBufCols + (uint32_t)(h * 16);
+        // the seven weights' loads in flight together, one wait
         int g0[16], g1[16], g2[16], g3[16];
-        uint32_t v[16];
-        tmem_ld16(col, v);
+        uint32_t v0[16], v1[16], v2[16], v3[16], v4[16], v5[16], v6[16];
+        tmem_ld16_async(col, v0);
+        tmem_ld16_async(col + 32, v1);
+        tmem_ld16_async(col + 64, v2);
+        tmem_ld16_async(col + 96, v3);
+        tmem_ld16_async(col + 128, v4);
+        tmem_ld16_async(col + 160, v5);
+        tmem_ld16_async(col + 192, v6);
+        tmem_wait16(v0);
+        tmem_after_wait16(v1);
+        tmem_after_wait16(v2);
+        tmem_after_wait16(v3);
+        tmem_after_wait16(v4);
+        tmem_after_wait16(v5);
+        tmem_after_wait16(v6);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) g0[e] = __float2int_rn(__uint_as_float(v[e]));
-        tmem_ld16(col + 32, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) g1[e] = __float2int_rn(__uint_as_float(v[e])) << 8;
-        tmem_ld16(col + 64, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) g1[e] += __float2int_rn(__uint_as_float(v[e]));
-        tmem_ld16(col + 96, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) g2[e] = __float2int_rn(__uint_as_float(v[e])) << 8;
-        tmem_ld16(col + 128, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) g2[e] += __float2int_rn(__uint_as_float(v[e]));
-        tmem_ld16(col + 160, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) g3[e] = __float2int_rn(__uint_as_float(v[e])) << 8;
-        tmem_ld16(col + 192, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) g3[e] += __float2int_rn(__uint_as_float(v[e]));
+        for (int e = 0; e < 16; ++e) {
+          g0[e] = __float2int_rn(__uint_as_float(v0[e]));
+          g1[e] = (__float2int_rn(__uint_as_float(v1[e])) << 8) + __float2int_rn(__uint_as_float(v2[e]));
+          g2[e] = (__float2int_rn(__uint_as_float(v3[e])) << 8) + __float2int_rn(__uint_as_float(v4[e]));
+          g3[e] = (__float2int_rn(__uint_as_float(v5[e])) << 8) + __float2int_rn(__uint_as_float(v6[e]));
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&t_empty[buf]);
