@@ -122,16 +122,19 @@ typedef enum {
                                   /* 28 exact bf16 digit products accumulated  */
                                   /* in integers (the Ozaki scheme); single-   */
                                   /* instance plans                            */
-#define QPE_FLAG_LEVEL_TC 0x200u /* QPE_FP64, nmat = 4, fused schedule with   */
-                                 /* an 8-point top level: that level's        */
-                                 /* contraction on the tcgen05 tensor cores   */
-                                 /* with FP64-grade accuracy (7 balanced      */
-                                 /* 8-bit digits per operand, per-pencil and  */
-                                 /* table power-of-two scales, 28 exact bf16  */
-                                 /* digit products folded in integers; the    */
-                                 /* twiddles, DFT, |X|^2 and readout in FP64);*/
-                                 /* ignored where those conditions do not     */
-                                 /* hold (QPE_INFO_TC_TOP_LEVEL tells)        */
+#define QPE_FLAG_LEVEL_TC 0x200u /* QPE_FP64: contractions on the tcgen05   */
+                                 /* tensor cores with FP64-grade accuracy (7  */
+                                 /* balanced 8-bit digits per operand at      */
+                                 /* power-of-two row scales, 28 exact bf16    */
+                                 /* digit products folded in integers): with  */
+                                 /* nmat = 4 the fused schedule's 8-point     */
+                                 /* levels of >= 128 pencils, the top level   */
+                                 /* included (QPE_INFO_TC_TOP_LEVEL tells;    */
+                                 /* twiddles, DFT, |X|^2, readout in FP64);   */
+                                 /* with nmat >= 8 the plain schedule's       */
+                                 /* doubling levels of >= 128 rows (single-   */
+                                 /* instance and sharded plans); ignored      */
+                                 /* elsewhere                                 */
 #define QPE_FLAG_CHECK_UNITARY 0x40u /* the POWERS stage first forms U^dagger */
                                      /* U in FP64; if any entry of            */
                                      /* U^dagger U - I exceeds 1e-8 in        */

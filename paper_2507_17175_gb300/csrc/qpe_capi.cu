@@ -87,7 +87,11 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
     in.off_recv = take(in.state_bytes);
   }
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
-  if (in.oz_square) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
+  // FP64 plain doubling levels of at least 128 rows on the tensor cores
+  in.oz_gates = prec == QPE_FP64 && (flags & QPE_FLAG_LEVEL_TC) && !in.fused && !batched && in.nmat >= 8 &&
+                !(flags & QPE_FLAG_GATE_SWEEP) && in.nmeas - in.shard_log >= 8;
+  if (in.oz_square || in.oz_gates) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
+  if (in.oz_gates) in.off_ozgate = take(qpe::oz_gate_bytes(in.nmat, (int64_t)(N >> in.shard_log)));
   // the fused top level on the tensor cores, d = 16, histogram only: a split
   // precision with a 16-point top level and at least one tile of 128 pencils
   // per rank, or FP64 (QPE_FLAG_LEVEL_TC) with an 8-point one of at least 128
@@ -200,7 +204,7 @@ qpe_status enqueue_stages(qpe_plan_t p, int first, int last, int64_t* launches) 
     if (!in.loaded) return fail(p, QPE_ERR_STATE, "qpe_load has not been called for every instance");
     // the error word covers one run: cleared where a whole run, or the first
     // stage that can set it, begins
-    if (first == QPE_STAGE_POWERS || (first == QPE_STAGE_SWEEP && is_tc(p->prec))) {
+    if (first == QPE_STAGE_POWERS || (first == QPE_STAGE_SWEEP && (is_tc(p->prec) || in.oz_gates))) {
       cudaError_t e = cudaMemsetAsync(p->ws + in.off_err, 0, sizeof(int), p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
     }
@@ -1145,7 +1149,8 @@ qpe_status qpe_bind(qpe_plan_t p, void* d_ws, size_t bytes, void* stream) {
     return fail(p, QPE_ERR_ARG, "QPE_FLAG_GRAPH needs a non-default stream");
   cudaError_t e = qpe::configure_kernels();
   if (e == cudaSuccess) e = qpe::configure_batched_kernels();
-  if (e == cudaSuccess && (is_tc(p->prec) || (p->flags & QPE_FLAG_SQUARE_TC))) e = qpe::configure_tc_kernels();
+  if (e == cudaSuccess && (is_tc(p->prec) || (p->flags & (QPE_FLAG_SQUARE_TC | QPE_FLAG_LEVEL_TC))))
+    e = qpe::configure_tc_kernels();
   if (e == cudaSuccess && (p->flags & QPE_FLAG_LEVEL_TC)) e = qpe::configure_oz_top_kernel();
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute");
   {

@@ -282,6 +282,8 @@ struct Instance {
   size_t off_err = 0;   // int32 device error word (bounded waits)
   size_t off_tcsplit = 0;  // split operands of the tensor-core levels
   size_t off_ozsq = 0;     // scales + digit slices of the tensor-core squaring
+  bool oz_gates = false;   // FP64 plain doubling levels on the tensor cores (QPE_FLAG_LEVEL_TC, d >= 256)
+  size_t off_ozgate = 0;   // their state-row scales and digit slices
   bool oz_square = false;  // U^(2^k) squared on the tensor cores (QPE_FLAG_SQUARE_TC, d >= 256)
   size_t state_bytes;
   bool has_state = true;  // the workspace holds an N x d state buffer
@@ -425,12 +427,19 @@ struct TcRound {  // one level j across the tensor-core instances
 
 // The digit-product GEMM of the tensor-core squaring (P_(k+1) = P_k^2).
 struct OzArgs {
-  const int* tau;  // row scales of E
-  const int* sig;  // column scales of B
-  double2* C;      // P_(k+1), complex128 d x d
+  const int* tau;  // row scales of the first operand (rows of E; state rows for a gate level)
+  const int* sig;  // scales of the second operand's rows (columns n of E; for a gate level the rows of
+                   // E(P), row n scaled like row n mod d of P)
+  double2* C;      // squaring: P_(k+1), complex128 d x d
   float2* C32;     // its complex64 copy, or null
   int d;
   int* err;
+  // a gate level (M > 0): out = A B^T with A the digits of state rows 0 .. M-1
+  // ([Re | Im], K = 2d) and B those of E(P) (N = 2d rows); row r of out is
+  // row row_out + r of S (columns n < d the real parts, n >= d the imaginary)
+  int64_t M = 0;
+  double2* S = nullptr;
+  int64_t row_out = 0;
 };
 // One instance's squaring step in a grouped launch: the digit slices' tensor
 // maps, P_k, the slice buffers, and the item's first scale block, first slice
@@ -585,6 +594,9 @@ cudaError_t configure_oz_top_kernel();
 int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, bool top, cudaStream_t s,
                     cudaEvent_t* top_ev, int64_t* grid_out);
 bool oz_top_copies_host_histogram(const Instance& in);
+// FP64 plain doubling levels on the tensor cores
+size_t oz_gate_bytes(int nmat, int64_t rows);
+int launch_oz_gate_level(const Instance& in, char* ws, int j, int pow_off, cudaStream_t s);
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 // a level of a sharded plan computes only this rank's outcomes when it has at

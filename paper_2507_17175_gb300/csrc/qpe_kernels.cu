@@ -897,6 +897,8 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, i
       int r;
       if (tc && in.d >= 32 && (int64_t(1) << j) >= 128)
         r = launch_tc_level(in, ws, prec, j, s, sh);
+      else if (sizeof(C) == 16 && in.oz_gates && (int64_t(1) << j) >= 128)
+        r = launch_oz_gate_level(in, ws, j, sh, s);
       else
         r = launch_rows_times_pt<C>(S, P + (j + sh) * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j},
                                     s);
@@ -918,6 +920,8 @@ int launch_sweep(const Instance& in, char* ws, bool gate_mode, cudaStream_t s, i
       r = launch_rows_times_pt<C>(S, P + j * dd, in.N / 2, (int)in.d, GateRows{j}, s);
     else if (tc && in.d >= 32 && (int64_t(1) << j) >= 128)
       r = launch_tc_level(in, ws, prec, j, s);  // tensor cores once a level fills 128-row tiles
+    else if (sizeof(C) == 16 && in.oz_gates && (int64_t(1) << j) >= 128)
+      r = launch_oz_gate_level(in, ws, j, 0, s);  // FP64: exact digit products on the tensor cores
     else
       r = launch_rows_times_pt<C>(S, P + j * dd, int64_t(1) << j, (int)in.d, DoublingRows{int64_t(1) << j}, s);
     if (r < 0) return -1;

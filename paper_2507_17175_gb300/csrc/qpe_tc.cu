@@ -595,6 +595,46 @@ __global__ void __launch_bounds__(256) oz_slice_b_kernel(const double2* __restri
 }
 
 
+// Digits of the state rows 0 .. M-1 for a gate level: row r = [Re S_r | Im S_r]
+// (2d reals) at its own scale tau[r]: A[(s M + r) 2d + k]. One CTA per row at
+// a time; a non-finite entry sets the error word.
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(const double2* __restrict__ S, int64_t M, int d,
+                                                            int* __restrict__ tau, __nv_bfloat16* __restrict__ A,
+                                                            int* __restrict__ err) {
+  pdl_begin();
+  __shared__ double wm[8];
+  __shared__ int t_s;
+  const int64_t stride = M * 2 * (int64_t)d;
+  for (int64_t r = blockIdx.x; r < M; r += gridDim.x) {
+    const double2* row = S + r * d;
+    double mx = 0.0;
+    bool finite = true;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+      const double2 p = row[k];
+      finite = finite && isfinite(p.x) && isfinite(p.y);
+      mx = fmax(mx, fmax(fabs(p.x), fabs(p.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+    if (__syncthreads_or(!finite) && threadIdx.x == 0) atomicCAS(err, 0, (int)QPE_ERR_NUMERIC);
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wm[w]);
+      t_s = oz_exponent(fmax(mx, wm[0]));
+      tau[r] = t_s;
+    }
+    __syncthreads();
+    const int t = t_s;
+    __nv_bfloat16* out = A + r * 2 * (int64_t)d;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+      const double2 p = row[k];
+      oz_digits(p.x, t, out + k, stride);
+      oz_digits(p.y, t, out + d + k, stride);
+    }
+    __syncthreads();  // wm and t_s are reused by the next row
+  }
+  pdl_trigger();
+}
+
 // One CTA per 128 x 64 tile of out (rows m0.. of E, columns n0.. < d).
 // K-block by K-block (64 elements of K), every digit tile is loaded once: the
 // seven B digit tiles of the K-block (resident, two buffers) and the seven A
@@ -746,7 +786,9 @@ __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CU
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = a.d, d2 = 2 * d;
-  const int m_tiles = d2 / kBM, n_tiles = d / kOzBN;
+  // squaring: out (2d x d) = E B^T; gate level: out (M x 2d) = A E(P)^T
+  const int mrows = a.M ? (int)a.M : d2, ncols = a.M ? d2 : d;
+  const int m_tiles = mrows / kBM, n_tiles = ncols / kOzBN;
   int m_tile, n_tile;
   {
     const int per_group = kGroupM * n_tiles;
@@ -801,7 +843,7 @@ __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CU
         if (*((volatile int*)&fail)) break;
         mbar_expect_tx(&b_full[bb], kOzBSet);
         for (int t = 0; t < kOzS; ++t)
-          tma_load_2d(bset + bb * kOzBSet + t * kOzB, mapB, &b_full[bb], kb * 64, t * d + n0);
+          tma_load_2d(bset + bb * kOzBSet + t * kOzB, mapB, &b_full[bb], kb * 64, t * ncols + n0);
         ++b_issued;
         bool go = true;
         for (int s = 0; s < kOzS; ++s, ++it) {
@@ -816,7 +858,7 @@ __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CU
             break;
           }
           mbar_expect_tx(&a_full[st], kOzA);
-          tma_load_2d(aring + st * kOzA, mapA, &a_full[st], kb * 64, s * d2 + m0);
+          tma_load_2d(aring + st * kOzA, mapA, &a_full[st], kb * 64, s * mrows + m0);
           ++a_issued;
         }
         if (!go) break;
@@ -858,7 +900,20 @@ __device__ __forceinline__ void oz_square_tile(const CUtensorMap* mapA, const CU
     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 32);
     for (int kb = 0; kb < kblocks && ok; ++kb)
       ok = oz_drain_kblock<0>(taddr, kb, kblocks, acc_full, acc_empty, &fail, lane, hi, lo);
-    if (ok) {
+    if (ok && a.M) {
+      // gate level: product row r -> state row row_out + r; this thread's 32
+      // columns are all real (n < d) or all imaginary parts
+      const int64_t r = m0 + row;
+      const int t = a.tau[r];
+      const int c0 = n0 + h * 32, im = c0 >= d ? 1 : 0, j0 = c0 - im * d;
+      double* vr = reinterpret_cast<double*>(a.S + (a.row_out + r) * d + j0) + im;
+#pragma unroll
+      for (int n = 0; n < 32; ++n) {
+        const double val = fma((double)lo[n], 0x1p-64, (double)hi[n] * 0x1p-32);
+        const int e = t + a.sig[j0 + n] + 2;
+        vr[2 * n] = val == 0.0 ? 0.0 : val * pow2d(e < -1022 ? -1022 : e);
+      }
+    } else if (ok) {
       const int gm = m0 + row;  // row of E: real part of P row gm, or imaginary part of row gm - d
       const int i = gm < d ? gm : gm - d;
       const int t = a.tau[i];
@@ -1050,6 +1105,58 @@ int launch_square_oz(const Instance& in, char* ws, int k, bool want_c64, cudaStr
     return -1;
   OzArgs a{tau, sig, C, P32 ? P32 + k * dd : nullptr, d, err};
   const unsigned grid = (unsigned)((2 * d / kBM) * (d / kOzBN));
+  e = launch_k(oz_square_kernel, dim3(grid), dim3(kOzThreads), oz_smem(), s, mA, mB, a);
+  return e == cudaSuccess ? 4 : -1;
+}
+
+// Workspace of the FP64 gate levels on the tensor cores: the state rows'
+// scales and digit slices of the largest level (M = rows / 2).
+size_t oz_gate_bytes(int nmat, int64_t rows) {
+  const size_t d = (size_t)1 << nmat, M = (size_t)(rows / 2);
+  return ((M * sizeof(int) + 255) & ~size_t(255)) + (size_t)kOzS * M * 2 * d * 2 + 256;
+}
+
+// Doubling level j of the FP64 plain schedule on the tensor cores (d >= 256,
+// M = 2^j >= 128): S[M + r] = P_(j + pow_off) S[r] for r < M as digit products,
+// A = the digits of state rows 0 .. M-1, B = the digits of E(P). Returns the
+// launches or -1.
+int launch_oz_gate_level(const Instance& in, char* ws, int j, int pow_off, cudaStream_t s) {
+  const int d = (int)in.d;
+  const int64_t dd = in.d * in.d, M = int64_t(1) << j;
+  const double2* P = reinterpret_cast<const double2*>(ws + in.off_pow64) + (j + pow_off) * dd;
+  double2* S = reinterpret_cast<double2*>(ws + in.off_state);
+  int* err = reinterpret_cast<int*>(ws + in.off_err);
+  // B: E(P)'s rows at the scales of P's rows (the squaring's first-operand slices)
+  char* base = ws + in.off_ozsq;
+  int* tauP = reinterpret_cast<int*>(base);
+  int* sigP = tauP + d;
+  __nv_bfloat16* B = reinterpret_cast<__nv_bfloat16*>(base + ((2 * (size_t)d * sizeof(int) + 255) & ~size_t(255)));
+  // A: the state rows
+  char* gbase = ws + in.off_ozgate;
+  const int64_t Mmax = (in.N >> in.shard_log) / 2;
+  int* tauA = reinterpret_cast<int*>(gbase);
+  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(gbase + ((Mmax * sizeof(int) + 255) & ~size_t(255)));
+  cudaError_t e = launch_k(oz_scale_kernel, dim3(2 * d), dim3(256), 0, s, P, d, tauP, sigP, err);
+  const unsigned eb = (unsigned)std::min<int64_t>((dd + 255) / 256, 152 * 16);
+  if (e == cudaSuccess)
+    e = launch_k(oz_slice_a_kernel, dim3(eb), dim3(256), 0, s, P, d, (const int*)tauP, B, (float2*)nullptr);
+  if (e == cudaSuccess)
+    e = launch_k(oz_slice_rows_kernel, dim3((unsigned)std::min<int64_t>(M, 152 * 8)), dim3(256), 0, s,
+                 (const double2*)S, M, d, tauA, A, err);
+  if (e != cudaSuccess) return -1;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, A, kTcBF16, (int64_t)kOzS * M, 2 * (int64_t)d, kBM) ||
+      !make_map(&mB, B, kTcBF16, (int64_t)kOzS * 2 * d, 2 * (int64_t)d, kOzBN))
+    return -1;
+  OzArgs a{};
+  a.tau = tauA;
+  a.sig = tauP;
+  a.d = d;
+  a.err = err;
+  a.M = M;
+  a.S = S;
+  a.row_out = M;
+  const unsigned grid = (unsigned)((M / kBM) * (2 * d / kOzBN));
   e = launch_k(oz_square_kernel, dim3(grid), dim3(kOzThreads), oz_smem(), s, mA, mB, a);
   return e == cudaSuccess ? 4 : -1;
 }

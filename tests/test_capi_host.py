@@ -157,6 +157,12 @@ def test_fp64_level_tc_plans(q):
         st, _, h = q.plan_workspace(nmat, nmeas, prec, flags | q.FLAG_LEVEL_TC)
         assert st == q.OK and q.LIB.qpe_query(h, q.INFO_TC_TOP_LEVEL) == 0, (nmat, nmeas, prec, flags)
         q.LIB.qpe_destroy(h)
+    # the plain schedule (d >= 256): the state rows' digit slices of the largest level
+    st, w0, h = q.plan_workspace(8, 12, q.FP64, 0)
+    q.LIB.qpe_destroy(h)
+    st, w1, h = q.plan_workspace(8, 12, q.FP64, q.FLAG_LEVEL_TC)
+    q.LIB.qpe_destroy(h)
+    assert w1 - w0 >= 7 * (1 << 11) * 512 * 2
     # sharded: decided on the level's whole pencil count, as unsharded (a rank
     # with fewer than 128 pencils runs one partial tile)
     for world in (4, 8, 16):

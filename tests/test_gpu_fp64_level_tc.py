@@ -194,3 +194,59 @@ def test_host_histogram_of_a_shard(q):
         sp.close()
     ref = gates.qpe_probabilities(inst.U, inst.psi, 14)
     assert np.abs(q.interleave_shards(parts) - ref).max() <= 1e-10
+
+
+# ------------------------------------------- the plain schedule's FP64 gates
+@pytest.mark.parametrize("nmat,nmeas", [(8, 9), (9, 8), (10, 8)])
+def test_plain_gate_rows_on_tensor_cores(q, nmat, nmeas):
+    """QPE_FLAG_LEVEL_TC on the plain schedule (d >= 256): the doubling levels of
+    at least 128 rows are exact digit products; row m after the gates equals
+    the oracle's 2^(-n/2) U^m psi to FP64 accuracy."""
+    rng = np.random.default_rng(5 * nmat + nmeas)
+    U = W.haar_unitary(rng, 1 << nmat)
+    psi = W.random_state(rng, 1 << nmat, 1)[:, 0]
+    plan = q.Plan(nmat, nmeas, q.FP64, q.FLAG_LEVEL_TC)
+    plan.load(U, psi)
+    plan.run_stages(q.STAGE_POWERS, q.STAGE_SWEEP)
+    S = plan.state()
+    ref = gates.qpe_after_sweeps(U, psi, nmeas)
+    tol = 1e-12 * np.abs(psi).max() * (1 << nmat) / np.sqrt(1 << nmeas)
+    assert np.abs(S - ref).max() <= tol
+    plan.close()
+
+
+@pytest.mark.parametrize("nmat,nmeas", [(8, 12), (9, 10), (10, 9)])
+def test_plain_fp64_gates_against_oracle_and_fp64_units(q, nmat, nmeas):
+    rng = np.random.default_rng(17 * nmat + nmeas)
+    inst = W.haar_instance(rng, nmat, nmeas, superposition=True)
+    ref = gates.qpe_probabilities(inst.U, inst.psi, nmeas)
+    (P, am, pa, pm), _ = _run(q, inst, q.FLAG_LEVEL_TC)
+    assert np.abs(P - ref).max() <= 1e-10
+    top2 = np.sort(ref)[-2:]
+    if top2[1] - top2[0] > 1e-9:
+        assert am == readout.argmax_lowest(ref)
+    assert abs(pm - readout.phase_weighted_mean(ref)) <= 1e-9
+    (P1, am1, _, pm1), _ = _run(q, inst, 0)
+    assert np.abs(P - P1).max() <= 1e-12 and am == am1
+
+
+def test_c3_fp64_gates_on_tensor_cores_against_closed_form(q):
+    """C3 (Nmat = 12, Nmeas = 20, 32 qubits, 64 GiB complex128 state) with the
+    doubling GEMMs as digit products (and the squaring on the tensor cores):
+    every bin against the closed form to the input's FP64 floor."""
+    import torch
+    inst = W.c3()
+    plan = q.Plan(inst.nmat, inst.nmeas, q.FP64, q.FLAG_LEVEL_TC | q.FLAG_SQUARE_TC)
+    plan.load(inst.U, inst.psi)
+    plan.run()
+    P, am, pa, pm = plan.probs()
+    Q = fejer.probabilities(inst.phases, inst.weights, inst.nmeas)
+    tol = max(1e-10, 2 * inst.N * U64 * np.sqrt(inst.d))
+    assert np.abs(P - Q).max() <= tol
+    order = np.argsort(Q)
+    if Q[order[-1]] - Q[order[-2]] > 10 * tol:
+        assert am == order[-1]
+    assert abs(pm - readout.phase_weighted_mean(Q)) <= 1e-8
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()

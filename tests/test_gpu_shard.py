@@ -111,7 +111,7 @@ def test_c5_complex64_two_shards_full_size(q):
 
 @pytest.mark.parametrize("prec,nmat,nmeas,world,flags", [(0, 7, 8, 2, 0), (1, 7, 10, 4, 0), (1, 3, 12, 4, 0x8),
                                                          (0, 2, 9, 8, 0x8), (3, 8, 10, 2, 0), (1, 5, 14, 2, 0x8),
-                                                         (3, 7, 12, 4, 0)])
+                                                         (3, 7, 12, 4, 0), (0, 8, 10, 2, 0x200)])
 def test_plain_shards_with_one_exchange(q, prec, nmat, nmeas, world, flags):
     """The plain schedule split over `world` ranks by the low measurement bits
     of the rows: local controlled gates and QFT^-1 passes, one all-to-all of
