@@ -88,10 +88,11 @@ size_t layout_instance(Instance& in, int prec, uint32_t flags, size_t base, bool
   }
   in.oz_square = (flags & QPE_FLAG_SQUARE_TC) && in.nmat >= 8 && in.nmeas >= 2;
   // FP64 plain doubling levels of at least 128 rows on the tensor cores
-  in.oz_gates = prec == QPE_FP64 && (flags & QPE_FLAG_LEVEL_TC) && !in.fused && !batched && in.nmat >= 8 &&
+  // (a batched plan's instances share one row-digit buffer per level instead)
+  in.oz_gates = prec == QPE_FP64 && (flags & QPE_FLAG_LEVEL_TC) && !in.fused && in.nmat >= 8 &&
                 !(flags & QPE_FLAG_GATE_SWEEP) && in.nmeas - in.shard_log >= 8;
   if (in.oz_square || in.oz_gates) in.off_ozsq = take(qpe::oz_square_bytes(in.nmat));
-  if (in.oz_gates) in.off_ozgate = take(qpe::oz_gate_bytes(in.nmat, (int64_t)(N >> in.shard_log)));
+  if (in.oz_gates && !batched) in.off_ozgate = take(qpe::oz_gate_bytes(in.nmat, (int64_t)(N >> in.shard_log)));
   // the fused top level on the tensor cores, d = 16, histogram only: a split
   // precision with a 16-point top level and at least one tile of 128 pencils
   // per rank, or FP64 (QPE_FLAG_LEVEL_TC) with an 8-point one of at least 128
@@ -361,6 +362,11 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
   bm.dbl_rounds.clear();
   bm.oz_items.clear();
   bm.oz_steps.clear();
+  bm.gate_p.clear();
+  bm.gate_g.clear();
+  bm.gate_r.clear();
+  bm.gate_rounds.clear();
+  bm.gate_buf_bytes = 0;
   bm.tc_split.clear();
   bm.tc_gemm.clear();
   bm.tc_rounds.clear();
@@ -590,11 +596,48 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
         ++bm.ninit;
       }
       // level j of an instance runs on the tensor cores once it fills 128-row
-      // tiles and 128-column tiles (2d >= 128), on the CUDA cores otherwise
+      // tiles and 128-column tiles (2d >= 128), on the CUDA cores otherwise;
+      // FP64 with QPE_FLAG_LEVEL_TC: as exact digit products for d >= 256
       auto on_tc = [&](const Instance& in, int j) {
         return is_tc(p->prec) && (int64_t(1) << j) >= 128 && in.d >= 64;
       };
+      auto on_oz = [&](const Instance& in, int j) { return in.oz_gates && (int64_t(1) << j) >= 128; };
       for (int j = 0; j < bm.maxn_plain; ++j) {
+        {
+          // the instances' row digits share one buffer per level (its largest
+          // total sizes the buffer)
+          qpe::GateRound G{};
+          G.j = j;
+          G.p_off = (int)bm.gate_p.size();
+          G.r_off = (int)bm.gate_r.size();
+          G.g_off = (int)bm.gate_g.size();
+          size_t bytes = 0;
+          for (int i : pl) {
+            const Instance& in = p->inst[i];
+            if (in.nmeas <= j || !on_oz(in, j)) continue;
+            qpe::OzItem pit{}, git{};
+            qpe::RowSliceItem rit{};
+            char* rowbuf = ws ? ws + bm.off_gatebuf + bytes : nullptr;
+            if (!qpe::oz_gate_items(in, ws, j, rowbuf, &pit, &rit, &git)) throw std::runtime_error("tensor map");
+            pit.sb0 = G.sblocks;
+            pit.e0 = G.elems;
+            G.sblocks += 2 * in.d;
+            G.elems += in.d * in.d;
+            rit.tile0 = G.rows;
+            G.rows += int64_t(1) << j;
+            git.tile0 = G.tiles;
+            G.tiles += qpe::oz_gate_tiles(in, j);
+            bytes += qpe::oz_gate_round_bytes(in, j);
+            bm.gate_p.push_back(pit);
+            bm.gate_r.push_back(rit);
+            bm.gate_g.push_back(git);
+          }
+          G.p_n = (int)bm.gate_p.size() - G.p_off;
+          G.r_n = (int)bm.gate_r.size() - G.r_off;
+          G.g_n = (int)bm.gate_g.size() - G.g_off;
+          if (G.g_n > 0) bm.gate_rounds.push_back(G);
+          bm.gate_buf_bytes = std::max(bm.gate_buf_bytes, bytes);
+        }
         {
           qpe::TcRound T{};
           T.j = j;
@@ -625,7 +668,7 @@ void build_batch_meta(qpe_plan_t p, char* ws, int nsm) {
           int64_t tiles = 0;
           for (int i : pl) {
             const Instance& in = p->inst[i];
-            if (in.nmeas <= j || on_tc(in, j) || std::min<int64_t>(in.d, 64) != dclass) continue;
+            if (in.nmeas <= j || on_tc(in, j) || on_oz(in, j) || std::min<int64_t>(in.d, 64) != dclass) continue;
             int BM = 0, BN = 0;
             qpe::doubling_tile((int)in.d, &BM, &BN);
             qpe::DblItem<C> it{};
@@ -721,6 +764,10 @@ size_t place_batch_meta(qpe::BatchMeta& bm, size_t off) {
   bm.off_oz = take(bm.oz_items.size() * sizeof(qpe::OzItem));
   bm.off_tcsp = take(bm.tc_split.size() * sizeof(qpe::TcSplitItem));
   bm.off_tcgm = take(bm.tc_gemm.size() * sizeof(qpe::TcGemmItem));
+  bm.off_gate_p = take(bm.gate_p.size() * sizeof(qpe::OzItem));
+  bm.off_gate_g = take(bm.gate_g.size() * sizeof(qpe::OzItem));
+  bm.off_gate_r = take(bm.gate_r.size() * sizeof(qpe::RowSliceItem));
+  bm.off_gatebuf = take(bm.gate_buf_bytes);
   return off;
 }
 
@@ -743,6 +790,9 @@ qpe_status upload_batch_meta(qpe_plan_t p) {
               {bm.off_red, bm.red_items.data(), bm.red_items.size()},
               {bm.off_finp, bm.fin_plain.data(), bm.fin_plain.size() * sizeof(qpe::FinItem)},
               {bm.off_oz, bm.oz_items.data(), bm.oz_items.size() * sizeof(qpe::OzItem)},
+              {bm.off_gate_p, bm.gate_p.data(), bm.gate_p.size() * sizeof(qpe::OzItem)},
+              {bm.off_gate_g, bm.gate_g.data(), bm.gate_g.size() * sizeof(qpe::OzItem)},
+              {bm.off_gate_r, bm.gate_r.data(), bm.gate_r.size() * sizeof(qpe::RowSliceItem)},
               {bm.off_tcsp, bm.tc_split.data(), bm.tc_split.size() * sizeof(qpe::TcSplitItem)},
               {bm.off_tcgm, bm.tc_gemm.data(), bm.tc_gemm.size() * sizeof(qpe::TcGemmItem)}};
   for (const Blk& b : blks) {
@@ -817,7 +867,7 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
   if (!mark(0)) return cuda_fail(p, cudaGetLastError(), "cudaEventRecord");
   // error words of the instances whose kernels can set them, cleared per run
   for (Instance& in : p->inst)
-    if (in.oz_square || (is_tc(p->prec) && !in.fused)) {
+    if (in.oz_square || in.oz_gates || (is_tc(p->prec) && !in.fused)) {
       cudaError_t e = cudaMemsetAsync(ws + in.off_err, 0, sizeof(int), p->stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "error word reset");
     }
@@ -892,6 +942,13 @@ qpe_status enqueue_batched(qpe_plan_t p, int64_t* launches) {
           if (R.j == j &&
               !chk(qpe::launch_doubling_grouped<C>(reinterpret_cast<const qpe::DblItem<C>*>(ws + bm.off_dbl) + R.item_off,
                                                    R.nitems, R.tiles, R.dclass, p->stream)))
+            return false;
+        for (const qpe::GateRound& G : bm.gate_rounds)
+          if (G.j == j &&
+              !chk(qpe::launch_oz_gate_grouped(reinterpret_cast<const qpe::OzItem*>(ws + bm.off_gate_p) + G.p_off,
+                                               reinterpret_cast<const qpe::RowSliceItem*>(ws + bm.off_gate_r) + G.r_off,
+                                               reinterpret_cast<const qpe::OzItem*>(ws + bm.off_gate_g) + G.g_off, G,
+                                               p->stream)))
             return false;
         for (const qpe::TcRound& T : bm.tc_rounds)
           if (T.j == j &&

@@ -453,6 +453,27 @@ struct OzItem {
   float2* A32;
   int64_t sb0, e0, tile0;
 };
+// The state rows 0 .. M-1 of one instance cut into digits for a batched FP64
+// gate level (row scales and digit planes in the round's shared buffer);
+// tile0 = its first row in the launch's numbering.
+struct RowSliceItem {
+  const double2* S;
+  int64_t M;
+  int d;
+  int* tau;
+  void* A;
+  int* err;
+  int64_t tile0;
+};
+struct GateRound {  // FP64 doubling level j on the tensor cores across the batched instances
+  int j;
+  int p_off, p_n;            // P_j's scale + slicing items (OzItem, squaring layout)
+  int64_t sblocks, elems;
+  int r_off, r_n;            // the state rows' slicing items
+  int64_t rows;
+  int g_off, g_n;            // the digit-product GEMM items (OzItem with a gate level's OzArgs)
+  int64_t tiles;
+};
 struct OzStep {  // squaring step k across the tensor-core instances
   int k, item_off, nitems;
   int64_t sblocks, elems, tiles;
@@ -475,6 +496,10 @@ struct BatchMeta {
   std::vector<DblRound> dbl_rounds;
   std::vector<OzItem> oz_items;  // tensor-core squarings, grouped per step
   std::vector<OzStep> oz_steps;
+  std::vector<OzItem> gate_p, gate_g;  // FP64 gate levels on the tensor cores, grouped per level
+  std::vector<RowSliceItem> gate_r;
+  std::vector<GateRound> gate_rounds;
+  size_t gate_buf_bytes = 0, off_gatebuf = 0, off_gate_p = 0, off_gate_g = 0, off_gate_r = 0;
   std::vector<TcSplitItem> tc_split;  // tensor-core levels (j >= 7, 2d >= 128), grouped per level
   std::vector<TcGemmItem> tc_gemm;
   std::vector<TcRound> tc_rounds;
@@ -597,6 +622,14 @@ bool oz_top_copies_host_histogram(const Instance& in);
 // FP64 plain doubling levels on the tensor cores
 size_t oz_gate_bytes(int nmat, int64_t rows);
 int launch_oz_gate_level(const Instance& in, char* ws, int j, int pow_off, cudaStream_t s);
+// batched: bytes of one level's row digits in the round buffer; the three items
+// of instance `in` at level j (rowbuf: its part of the round buffer; maps and
+// pointers only when ws is a bound workspace); the round's grouped launches
+size_t oz_gate_round_bytes(const Instance& in, int j);
+bool oz_gate_items(const Instance& in, char* ws, int j, char* rowbuf, OzItem* pit, RowSliceItem* rit, OzItem* git);
+int64_t oz_gate_tiles(const Instance& in, int j);
+int launch_oz_gate_grouped(const OzItem* pits, const RowSliceItem* rits, const OzItem* gits, const GateRound& R,
+                           cudaStream_t s);
 int level_max_bits(int logd, size_t esize, size_t smem_cap);
 std::vector<Level> make_levels(int nmeas, int logd, size_t esize, int rtop);
 // a level of a sharded plan computes only this rank's outcomes when it has at

@@ -595,42 +595,57 @@ __global__ void __launch_bounds__(256) oz_slice_b_kernel(const double2* __restri
 }
 
 
-// Digits of the state rows 0 .. M-1 for a gate level: row r = [Re S_r | Im S_r]
-// (2d reals) at its own scale tau[r]: A[(s M + r) 2d + k]. One CTA per row at
-// a time; a non-finite entry sets the error word.
+// Digits of state row r for a gate level: [Re S_r | Im S_r] (2d reals) at the
+// row's own scale tau[r], A[(s M + r) 2d + k]; the whole CTA takes part. A
+// non-finite entry sets the error word.
+__device__ __forceinline__ void oz_slice_row(const double2* __restrict__ S, int64_t M, int d, int* __restrict__ tau,
+                                             __nv_bfloat16* __restrict__ A, int* __restrict__ err, int64_t r) {
+  __shared__ double wm[8];
+  __shared__ int t_s;
+  const double2* row = S + r * d;
+  double mx = 0.0;
+  bool finite = true;
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    const double2 p = row[k];
+    finite = finite && isfinite(p.x) && isfinite(p.y);
+    mx = fmax(mx, fmax(fabs(p.x), fabs(p.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  if (__syncthreads_or(!finite) && threadIdx.x == 0) atomicCAS(err, 0, (int)QPE_ERR_NUMERIC);
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wm[w]);
+    t_s = oz_exponent(fmax(mx, wm[0]));
+    tau[r] = t_s;
+  }
+  __syncthreads();
+  const int t = t_s;
+  const int64_t stride = M * 2 * (int64_t)d;
+  __nv_bfloat16* out = A + r * 2 * (int64_t)d;
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    const double2 p = row[k];
+    oz_digits(p.x, t, out + k, stride);
+    oz_digits(p.y, t, out + d + k, stride);
+  }
+  __syncthreads();  // wm and t_s are reused by the next row
+}
+
 __global__ void __launch_bounds__(256) oz_slice_rows_kernel(const double2* __restrict__ S, int64_t M, int d,
                                                             int* __restrict__ tau, __nv_bfloat16* __restrict__ A,
                                                             int* __restrict__ err) {
   pdl_begin();
-  __shared__ double wm[8];
-  __shared__ int t_s;
-  const int64_t stride = M * 2 * (int64_t)d;
-  for (int64_t r = blockIdx.x; r < M; r += gridDim.x) {
-    const double2* row = S + r * d;
-    double mx = 0.0;
-    bool finite = true;
-    for (int k = threadIdx.x; k < d; k += blockDim.x) {
-      const double2 p = row[k];
-      finite = finite && isfinite(p.x) && isfinite(p.y);
-      mx = fmax(mx, fmax(fabs(p.x), fabs(p.y)));
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
-    if (__syncthreads_or(!finite) && threadIdx.x == 0) atomicCAS(err, 0, (int)QPE_ERR_NUMERIC);
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wm[w]);
-      t_s = oz_exponent(fmax(mx, wm[0]));
-      tau[r] = t_s;
-    }
-    __syncthreads();
-    const int t = t_s;
-    __nv_bfloat16* out = A + r * 2 * (int64_t)d;
-    for (int k = threadIdx.x; k < d; k += blockDim.x) {
-      const double2 p = row[k];
-      oz_digits(p.x, t, out + k, stride);
-      oz_digits(p.y, t, out + d + k, stride);
-    }
-    __syncthreads();  // wm and t_s are reused by the next row
+  for (int64_t r = blockIdx.x; r < M; r += gridDim.x) oz_slice_row(S, M, d, tau, A, err, r);
+  pdl_trigger();
+}
+
+// The state rows of every listed instance (batched gate level): global row
+// g of the launch is row g - tile0 of its item.
+__global__ void __launch_bounds__(256) oz_slice_rows_grouped_kernel(const RowSliceItem* __restrict__ items,
+                                                                    int nitems, int64_t rows) {
+  pdl_begin();
+  for (int64_t g = blockIdx.x; g < rows; g += gridDim.x) {
+    const RowSliceItem& it = items[find_item(items, nitems, g)];
+    oz_slice_row(it.S, it.M, it.d, it.tau, static_cast<__nv_bfloat16*>(it.A), it.err, g - it.tile0);
   }
   pdl_trigger();
 }
@@ -1158,6 +1173,52 @@ int launch_oz_gate_level(const Instance& in, char* ws, int j, int pow_off, cudaS
   a.row_out = M;
   const unsigned grid = (unsigned)((M / kBM) * (2 * d / kOzBN));
   e = launch_k(oz_square_kernel, dim3(grid), dim3(kOzThreads), oz_smem(), s, mA, mB, a);
+  return e == cudaSuccess ? 4 : -1;
+}
+
+size_t oz_gate_round_bytes(const Instance& in, int j) {
+  const size_t M = (size_t)1 << j, d = (size_t)in.d;
+  return ((M * sizeof(int) + 255) & ~size_t(255)) + (((size_t)kOzS * M * 2 * d * 2 + 255) & ~size_t(255));
+}
+
+int64_t oz_gate_tiles(const Instance& in, int j) { return ((int64_t(1) << j) / kBM) * (2 * in.d / kOzBN); }
+
+bool oz_gate_items(const Instance& in, char* ws, int j, char* rowbuf, OzItem* pit, RowSliceItem* rit, OzItem* git) {
+  // P_j's digits in the squaring's layout (the item of squaring step j + 1 reads P_j)
+  if (!oz_square_item(in, ws, j + 1, false, pit)) return false;
+  const int d = (int)in.d;
+  const int64_t M = int64_t(1) << j;
+  int* tauA = reinterpret_cast<int*>(rowbuf);
+  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(rowbuf + ((M * sizeof(int) + 255) & ~size_t(255)));
+  double2* S = ws ? reinterpret_cast<double2*>(ws + in.off_state) : nullptr;
+  int* err = ws ? reinterpret_cast<int*>(ws + in.off_err) : nullptr;
+  *rit = RowSliceItem{S, M, d, tauA, A, err, 0};
+  *git = OzItem{};
+  git->a.tau = tauA;
+  git->a.sig = pit->a.tau;  // E(P)'s row n scaled like row n mod d of P
+  git->a.d = d;
+  git->a.err = err;
+  git->a.M = M;
+  git->a.S = S;
+  git->a.row_out = M;
+  if (!ws) return true;
+  return make_map(&git->mA, A, kTcBF16, (int64_t)kOzS * M, 2 * (int64_t)d, kBM) &&
+         make_map(&git->mB, pit->A, kTcBF16, (int64_t)kOzS * 2 * d, 2 * (int64_t)d, kOzBN);
+}
+
+// One batched FP64 gate level: P_j's scales and digits per instance, the
+// state rows' digits, the digit-product GEMM; four grouped launches.
+int launch_oz_gate_grouped(const OzItem* pits, const RowSliceItem* rits, const OzItem* gits, const GateRound& R,
+                           cudaStream_t s) {
+  if (R.g_n <= 0) return 0;
+  const unsigned eb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((R.elems + 255) / 256, 152 * 16));
+  cudaError_t e = launch_k(oz_scale_grouped_kernel, dim3((unsigned)R.sblocks), dim3(256), 0, s, pits, R.p_n);
+  if (e == cudaSuccess) e = launch_k(oz_slice_grouped_kernel, dim3(eb), dim3(256), 0, s, pits, R.p_n, R.elems);
+  if (e == cudaSuccess)
+    e = launch_k(oz_slice_rows_grouped_kernel, dim3((unsigned)std::min<int64_t>(R.rows, 152 * 16)), dim3(256), 0, s,
+                 rits, R.r_n, R.rows);
+  if (e == cudaSuccess)
+    e = launch_k(oz_square_grouped_kernel, dim3((unsigned)R.tiles), dim3(kOzThreads), oz_smem(), s, gits, R.g_n);
   return e == cudaSuccess ? 4 : -1;
 }
 

@@ -24,6 +24,8 @@ def main(argv=None):
     ap.add_argument("--single", action="store_true", help="also time one plan per instance")
     ap.add_argument("--autotune", action="store_true", help="let qpe_bind pick the squaring tiles")
     ap.add_argument("--square-tc", action="store_true", help="square U^(2^k) of d >= 256 on the tensor cores")
+    ap.add_argument("--level-tc", action="store_true",
+                    help="FP64: doubling levels of d >= 256 as exact digit products on the tensor cores")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="also run the plain FP64 batched plan and report the histograms' L1 difference")
     args = ap.parse_args(argv)
@@ -36,7 +38,7 @@ def main(argv=None):
     shapes = [(i.nmat, i.nmeas) for i in insts]
     stream = torch.cuda.Stream()
     flags = (qpe.FLAG_GRAPH | qpe.FLAG_TIMING | (qpe.FLAG_AUTOTUNE if args.autotune else 0) |
-             (qpe.FLAG_SQUARE_TC if args.square_tc else 0))
+             (qpe.FLAG_SQUARE_TC if args.square_tc else 0) | (qpe.FLAG_LEVEL_TC if args.level_tc else 0))
     bp = qpe.BatchedPlan(shapes, prec, flags, stream=stream)
     dev_inputs = [(torch.from_numpy(i.U).cuda(), torch.from_numpy(i.psi).cuda()) for i in insts]
     for k, (U, psi) in enumerate(dev_inputs):

@@ -250,3 +250,36 @@ def test_c3_fp64_gates_on_tensor_cores_against_closed_form(q):
     plan.close()
     del plan
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------- batched plans: gate rounds
+BATCH = [(8, 9), (3, 8), (9, 10), (10, 8), (4, 12), (8, 12), (2, 7), (9, 8), (8, 7), (10, 10)]
+
+
+@pytest.mark.parametrize("flags", [0x200, 0x200 | 0x2, 0x200 | 0x100 | 0x2])
+def test_batched_fp64_gate_rounds(q, flags):
+    """A batched FP64 plan with QPE_FLAG_LEVEL_TC: every level of at least 128
+    rows of the d >= 256 instances is one grouped digit-product round across
+    them; (8, 7) stays on the FP64 units and the fused instances are as
+    before. Each instance against the oracle, and against the batched plan
+    without the flag within a few units of rounding; twice (graph replay)."""
+    rng = np.random.default_rng(91)
+    insts = [W.haar_instance(rng, a, b, superposition=True) for a, b in BATCH]
+    bp = q.BatchedPlan(BATCH, q.FP64, flags)
+    ref_plan = q.BatchedPlan(BATCH, q.FP64, flags & ~0x200)
+    for i, inst in enumerate(insts):
+        bp.load(i, inst.U, inst.psi)
+        ref_plan.load(i, inst.U, inst.psi)
+    ref_plan.run()
+    for rep in range(2):
+        bp.run()
+        for i, inst in enumerate(insts):
+            P, am, pa, pm = bp.probs(i)
+            ref = gates.qpe_probabilities(inst.U, inst.psi, inst.nmeas)
+            assert np.abs(P - ref).max() <= 1e-10, (i, BATCH[i])
+            top2 = np.sort(ref)[-2:]
+            if top2[1] - top2[0] > 1e-9:
+                assert am == readout.argmax_lowest(ref)
+            assert abs(pm - readout.phase_weighted_mean(ref)) <= 1e-9
+            P1, am1, _, _ = ref_plan.probs(i)
+            assert np.abs(P - P1).max() <= 1e-12 and am == am1, (i, BATCH[i])
