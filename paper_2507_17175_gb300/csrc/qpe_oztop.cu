@@ -18,16 +18,24 @@
 // w = s + t <= 6 are formed; a pair's products are integers of at most 2^14,
 // so a weight's accumulator (w + 1 pairs over K = 32) stays below 2^22 and is
 // exact in FP32. With acc_w the weight sums,
-//   T = 2^(tau + sigma - 30) (hi + 2^-32 lo),
-//   hi = sum_(w<=2) acc_w 2^(8 (2 - w)),  lo = sum_(w>=3) acc_w 2^(8 (6 - w)),
-// integers below 2^36 and 2^46. The drain forms V = 2^26 hi + floor(lo / 2^6)
-// (below 2^62; the dropped bits are 2^-26 of a unit, 2^-60 of the pencil's
-// scale) and turns V 2^-26 into FP64 by integer operations on the bits (one
-// rounding to nearest even), so the FP64 pipe, this kernel's bound, is left
-// to the twiddles, the DFT and |X|^2. The omitted digit pairs and the digit
-// rounding lie at 2^-53 of |Z| |M| K, the error bound of an FP64 dot product. Twiddles, the 8-point DFT, |X|^2 and the readout run in FP64; the
-// scale 2^(2 (tau + sigma - 30)) goes into the histogram's 1 / N^2 (MODE 1),
-// or 2^(tau + sigma - 30) into the twiddles and the m_b = 0 term (MODE 0).
+//   T = 2^(tau + sigma - 62) E,  E = sum_w acc_w 2^(8 (6 - w)),
+// |T| < 32 2^(tau + sigma), so |E| < 2^67. The omitted digit pairs and the
+// digit rounding lie at 2^-53 of |Z| |M| K, the error bound of an FP64 dot
+// product.
+//
+// GB300 issues an FP64 instruction at 1/32 of the rate of a 32-bit integer
+// one, so the epilogue stays in 64-bit fixed point until |X|^2: the drain
+// reads each accumulator as an int (a magic-number addition in FP32), forms
+// W = floor(E / 2^10) (|W| < 2^57 + 1, units 2^(tau + sigma - 52)),
+// multiplies by the twiddles held in Q61 (round(w 2^61), split at bit 31 into
+// int32 halves so that every partial product is one 32 x 32 -> 64-bit
+// multiply-add; at most 3 units off), runs the 8-point DFT on the integers
+// (|X| < 8 sqrt(2) 2^57 < 2^61; the factor cos(pi / 4) also in Q61) and turns
+// X into FP64 by integer operations on the bits (the unit's power of two goes
+// into the exponent; rounded half away from zero). The fixed point's
+// truncations are a few units, 2^-55 of the pencil's bound |T| < 2^(tau +
+// sigma + 5), below the contraction's own error. |X|^2 and the readout run in
+// FP64; a lower level (MODE 0) stores X in FP64.
 //
 // Roles (384 threads, one CTA per SM, persistent over the tiles):
 //   warps 0-2   producers: Z rows -> digit tiles (shared memory, 128-byte
@@ -38,8 +46,8 @@
 //               M = 128, N = 32 into seven weight accumulators (224 columns;
 //               two chunk buffers);
 //   warps 4-11  drain: two warps per tensor-memory lane quarter, one column i
-//               each (16 table rows) per chunk; weights -> integers -> FP64,
-//               twiddle, DFT, then |X|^2 (the two warps' sums meet through
+//               each (16 table rows) per chunk; weights -> fixed point,
+//               twiddle, DFT, FP64, then |X|^2 (the two warps' sums meet through
 //               tensor memory columns 448-463) or the store of X.
 // Every wait is a bounded mbarrier wait; an expired wait sets QPE_ERR_TIMEOUT.
 #include "qpe_internal.cuh"
@@ -70,31 +78,104 @@ constexpr size_t kOtTwBytes = (size_t)kOtRows * (kOtL - 1) * sizeof(double2);
 constexpr size_t kOtSmem = kOtBBytes + kOtABytes + 2 * kOtTwBytes + 2 * kOtRows * sizeof(int) + 1024;
 static_assert(kOtSmem <= 227 * 1024, "shared memory of the FP64 top level");
 
-// v 2^e2 in FP64 for an integer 0 < |v| < 2^62 (and a result in the normal
-// range), rounded to nearest even, by integer operations: the leading one's
-// position sets the exponent, the 53 bits below it (with the rounding carry
-// running into the exponent) the significand. v = 0 gives 0.
-__device__ __forceinline__ double ot_i64_to_f64(long long v, int e2) {
-  if (v == 0) return 0.0;
-  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
-  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+// v 2^e2 in FP64 for a signed integer |v| < 2^63, by integer operations on
+// the bits: the leading one's position sets the exponent, the 53 bits from it
+// the significand, rounded half away from zero on the magnitude (a carry runs
+// into the exponent). v = 0, and results below 2^-1022, give 0.
+__device__ __forceinline__ double ot_fix_to_f64(long long v, int e2) {
+  const unsigned long long sg = (unsigned long long)(v >> 63);  // 0 or all ones
+  const unsigned long long a = ((unsigned long long)v ^ sg) - sg;
   const int lz = __clzll((long long)a);
-  const int sh = 11 - lz;  // bits below the 53 kept
-  unsigned long long m;
-  if (sh <= 0) {
-    m = a << (-sh);
-  } else {
-    const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    m = (a >> sh) + ((rem > half || (rem == half && ((a >> sh) & 1))) ? 1ull : 0ull);
-  }
-  // m holds the leading one at bit 52 (or is 2^53 after a carry): adding it to
-  // (exponent - 1) << 52 yields the bits of the result
-  const unsigned long long eb = (unsigned long long)(1023 + 62 - lz + e2) << 52;
-  return __longlong_as_double((long long)(sgn | (eb + m)));
+  const unsigned long long n = a << (lz & 63);  // leading one at bit 63
+  const unsigned long long m = (n >> 11) + ((n >> 10) & 1ull);
+  const int eb = 1086 - lz + e2;  // biased exponent of a 2^e2
+  // m has its leading one at bit 52 (or is 2^53 after a carry): adding it to
+  // (eb - 1) << 52 gives the bits of the result
+  const unsigned long long bits = ((unsigned long long)(eb - 1) << 52) + m;
+  return (a == 0 || eb <= 0) ? 0.0 : __longlong_as_double((long long)(bits | (sg << 63)));
 }
 
-__device__ __forceinline__ double ot_pow2(int e) {  // 2^e, -1022 <= e <= 1023
-  return __longlong_as_double((long long)(1023 + e) << 52);
+// A weight accumulator (an exact integer |acc| < 2^22 in FP32) as an int:
+// adding 1.5 2^23 places acc + 2^22 in the low mantissa bits, exactly.
+__device__ __forceinline__ int ot_acc(uint32_t u) {
+  return (int)__float_as_uint(__fadd_rn(__uint_as_float(u), 12582912.0f)) - 0x4B400000;
+}
+
+// The drain's fixed point W = floor(E / 2^10) of one T component from its
+// seven weight sums, E = sum_w a_w 2^(8 (6 - w)), T = 2^(tau + sigma - 62) E.
+__device__ __forceinline__ long long ot_weights_fix(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, uint32_t u4,
+                                                    uint32_t u5, uint32_t u6) {
+  long long w = (long long)((ot_acc(u5) * 256 + ot_acc(u6)) >> 10);
+  w += (long long)ot_acc(u4) * 64;
+  w += (long long)ot_acc(u3) * 16384;
+  w += (long long)ot_acc(u2) * 4194304;
+  w += (long long)ot_acc(u1) * 1073741824;
+  w += (long long)(ot_acc(u0) * 64) * 4294967296LL;
+  return w;
+}
+
+// (wr + i wi) (qr + i qi) 2^-61 for a twiddle in Q61 (q = round(w 2^61)),
+// with both operands split at bit 31 (h = x >> 31, l = x mod 2^31): the
+// products l l 2^-61 (below 2) are dropped and the middle sum is floored.
+// q = (qr h, qr l, qi h, qi l).
+__device__ __forceinline__ void ot_tw_fix(long long& wr, long long& wi, int4 q) {
+  const int rh = (int)(wr >> 31), rl = (int)(wr & 0x7fffffff);
+  const int ih = (int)(wi >> 31), il = (int)(wi & 0x7fffffff);
+  const long long sr = (long long)rh * q.y + (long long)rl * q.x - (long long)ih * q.w - (long long)il * q.z;
+  const long long si = (long long)rh * q.w + (long long)rl * q.z + (long long)ih * q.y + (long long)il * q.x;
+  wr = 2 * ((long long)rh * q.x - (long long)ih * q.z) + (sr >> 30);
+  wi = 2 * ((long long)rh * q.z + (long long)ih * q.x) + (si >> 30);
+}
+
+// x cos(pi / 4) in the same fixed point (cos(pi / 4) 2^61 rounded, split as in
+// ot_tw_fix)
+__device__ __forceinline__ long long ot_rot_fix(long long x) {
+  constexpr long long kC = 1630477228166597777LL;  // round(2^61 / sqrt(2))
+  constexpr int ch = (int)(kC >> 31), cl = (int)(kC & 0x7fffffff);
+  const int xh = (int)(x >> 31), xl = (int)(x & 0x7fffffff);
+  return 2 * ((long long)xh * ch) + (((long long)xh * cl + (long long)xl * ch) >> 30);
+}
+
+// 8-point DFT X[k] = sum_n x[n] exp(-2 pi i n k / 8) on fixed-point values
+// (re, im interleaved: x[2 n], x[2 n + 1]), natural order in and out (radix-2
+// decimation in frequency; -i by exchange, (+-1 - i) / sqrt 2 by ot_rot_fix)
+__device__ __forceinline__ void ot_dft8_fix(long long (&x)[16]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const long long ur = x[2 * p], ui = x[2 * p + 1], vr = x[2 * p + 8], vi = x[2 * p + 9];
+    x[2 * p] = ur + vr;
+    x[2 * p + 1] = ui + vi;
+    const long long dr = ur - vr, di = ui - vi;
+    if (p == 0) { x[8] = dr; x[9] = di; }
+    if (p == 1) { x[10] = ot_rot_fix(dr + di); x[11] = ot_rot_fix(di - dr); }
+    if (p == 2) { x[12] = di; x[13] = -dr; }
+    if (p == 3) { x[14] = ot_rot_fix(di - dr); x[15] = -ot_rot_fix(dr + di); }
+  }
+#pragma unroll
+  for (int g = 0; g < 8; g += 4) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int a = 2 * (g + p), b = 2 * (g + p + 2);
+      const long long ur = x[a], ui = x[a + 1], vr = x[b], vi = x[b + 1];
+      x[a] = ur + vr;
+      x[a + 1] = ui + vi;
+      if (p == 0) { x[b] = ur - vr; x[b + 1] = ui - vi; }
+      else { x[b] = ui - vi; x[b + 1] = vr - ur; }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < 8; g += 2) {
+    const long long ur = x[2 * g], ui = x[2 * g + 1], vr = x[2 * g + 2], vi = x[2 * g + 3];
+    x[2 * g] = ur + vr;
+    x[2 * g + 1] = ui + vi;
+    x[2 * g + 2] = ur - vr;
+    x[2 * g + 3] = ui - vi;
+  }
+  long long t;
+  t = x[2]; x[2] = x[8]; x[8] = t;
+  t = x[3]; x[3] = x[9]; x[9] = t;
+  t = x[6]; x[6] = x[12]; x[12] = t;
+  t = x[7]; x[7] = x[13]; x[13] = t;
 }
 
 // the largest exponent field among the values, as the scale exponent t with
@@ -140,45 +221,6 @@ __device__ __forceinline__ uint32_t ot_bf16(int v) { return __float_as_uint((flo
 
 __device__ __forceinline__ double2 ot_cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-
-// 8-point DFT X[k] = sum_n x[n] exp(-2 pi i n k / 8), natural order in and out
-// (radix-2 decimation in frequency; the factors -i and (+-1 - i) / sqrt 2 by
-// additions)
-__device__ __forceinline__ void ot_dft8(double2 (&x)[8]) {
-  constexpr double c = 0.70710678118654752440;
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const double2 u = x[p], v = x[p + 4];
-    x[p] = make_double2(u.x + v.x, u.y + v.y);
-    const double2 d = make_double2(u.x - v.x, u.y - v.y);
-    if (p == 0) x[4] = d;
-    if (p == 1) x[5] = make_double2(c * (d.x + d.y), c * (d.y - d.x));
-    if (p == 2) x[6] = make_double2(d.y, -d.x);
-    if (p == 3) x[7] = make_double2(c * (d.y - d.x), -c * (d.x + d.y));
-  }
-#pragma unroll
-  for (int g = 0; g < 8; g += 4) {
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const double2 u = x[g + p], v = x[g + p + 2];
-      x[g + p] = make_double2(u.x + v.x, u.y + v.y);
-      const double2 d = make_double2(u.x - v.x, u.y - v.y);
-      x[g + p + 2] = p == 0 ? d : make_double2(d.y, -d.x);
-    }
-  }
-#pragma unroll
-  for (int g = 0; g < 8; g += 2) {
-    const double2 u = x[g], v = x[g + 1];
-    x[g] = make_double2(u.x + v.x, u.y + v.y);
-    x[g + 1] = make_double2(u.x - v.x, u.y - v.y);
-  }
-  double2 t = x[1];
-  x[1] = x[4];
-  x[4] = t;
-  t = x[3];
-  x[3] = x[6];
-  x[6] = t;
 }
 
 // The MMAs of one chunk: pair (S, T) into weight S + T, two K = 16 steps of
@@ -258,7 +300,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   unsigned char* Bs = base;
   unsigned char* As = base + kOtBBytes;
-  double2* twS = reinterpret_cast<double2*>(As + kOtABytes);  // [2][128][7]
+  int4* twS = reinterpret_cast<int4*>(As + kOtABytes);  // [2][128][7] twiddles in Q61, split at bit 31
   int* tauS = reinterpret_cast<int*>(twS + 2 * kOtRows * (kOtL - 1));  // [2][128]
   __shared__ uint64_t a_full, a_empty, tw_empty[2], t_full[2], t_empty[2], sq_full, sq_empty, mma_done;
   __shared__ uint32_t tmem_slot;
@@ -348,17 +390,15 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
           }
         }
         const int64_t ya = a.rk + (j << a.sh);
-        double2* tw = twS + (tb * kOtRows + p) * (kOtL - 1);
-        // MODE 0: the output scale 2^(tau + sigma - 30) rides on the twiddles
-        const int es = tau + sigma - 30;
-        const double tsc = MODE == 0 ? ot_pow2(es) : 1.0;
+        int4* tw = twS + (tb * kOtRows + p) * (kOtL - 1);
 #pragma unroll
         for (int m = 1; m < kOtL; ++m) {
           const int64_t ex = (((int64_t)m * ya) & lvl_mask) << lvl_shift;
           const double2 w = ot_cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
-          tw[m - 1] = MODE == 0 ? make_double2(w.x * tsc, w.y * tsc) : w;
+          const long long qr = ot_fixed(w.x, -6), qi = ot_fixed(w.y, -6);  // round(w 2^61)
+          tw[m - 1] = make_int4((int)(qr >> 31), (int)(qr & 0x7fffffff), (int)(qi >> 31), (int)(qi & 0x7fffffff));
         }
-        tauS[tb * kOtRows + p] = es;
+        tauS[tb * kOtRows + p] = tau + sigma - 30;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&a_full);
       }
@@ -413,9 +453,9 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         ok = false;
         break;
       }
-      const double2* tw = twS + (tb * kOtRows + row) * (kOtL - 1);
-      const int es = tauS[tb * kOtRows + row];  // this pencil's scale exponent tau + sigma - 30
-      const double sc0 = MODE == 0 ? ot_pow2(es) : 1.0;
+      const int4* tw = twS + (tb * kOtRows + row) * (kOtL - 1);
+      // X in units of 2^(tau + sigma - 52) (the fixed point below)
+      const int e2 = tauS[tb * kOtRows + row] - 22;
       const int64_t jt = t * kOtRows + row;     // local pencil index
       double acc[kOtL];
 #pragma unroll
@@ -429,11 +469,8 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
           ok = false;
           break;
         }
-        // weights -> integer groups: g0 = acc_0, g1 = 2^8 acc_1 + acc_2,
-        // g2 = 2^8 acc_3 + acc_4, g3 = 2^8 acc_5 + acc_6 (all below 2^31)
         const uint32_t col = lane_base + (uint32_t)buf * kOtBufCols + (uint32_t)(h * 16);
         // the seven weights' loads in flight together, one wait
-        int g0[16], g1[16], g2[16], g3[16];
         uint32_t v0[16], v1[16], v2[16], v3[16], v4[16], v5[16], v6[16];
         tmem_ld16_async(col, v0);
         tmem_ld16_async(col + 32, v1);
@@ -449,47 +486,31 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         tmem_after_wait16(v4);
         tmem_after_wait16(v5);
         tmem_after_wait16(v6);
+        // T[m_b] (columns 2 m_b + c of this half) as 64-bit fixed point
+        long long x[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          g0[e] = __float2int_rn(__uint_as_float(v0[e]));
-          g1[e] = (__float2int_rn(__uint_as_float(v1[e])) << 8) + __float2int_rn(__uint_as_float(v2[e]));
-          g2[e] = (__float2int_rn(__uint_as_float(v3[e])) << 8) + __float2int_rn(__uint_as_float(v4[e]));
-          g3[e] = (__float2int_rn(__uint_as_float(v5[e])) << 8) + __float2int_rn(__uint_as_float(v6[e]));
-        }
+        for (int e = 0; e < 16; ++e) x[e] = ot_weights_fix(v0[e], v1[e], v2[e], v3[e], v4[e], v5[e], v6[e]);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&t_empty[buf]);
-        // T[m_b] (columns 2 m_b + c of this half) in units of 2^(tau + sigma - 30)
-        double2 x[kOtL];
+        // twiddles w_N^(m_b y_a) (m_b >= 1), then the 8-point DFT over m_b
 #pragma unroll
-        for (int m = 0; m < kOtL; ++m) {
-          double re, im;
-#pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            const int e = 2 * m + cc;
-            const long long hi = ((long long)g0[e] << 16) + g1[e];
-            const long long lo = ((long long)g2[e] << 16) + g3[e];
-            const double val = ot_i64_to_f64((hi << 26) + (lo >> 6), -26);
-            if (cc == 0)
-              re = val;
-            else
-              im = val;
-          }
-          x[m] = make_double2(re, im);
-        }
-#pragma unroll
-        for (int m = 1; m < kOtL; ++m) x[m] = ot_cmul(x[m], tw[m - 1]);
-        if (MODE == 0) x[0] = make_double2(x[0].x * sc0, x[0].y * sc0);
-        ot_dft8(x);
+        for (int m = 1; m < kOtL; ++m) ot_tw_fix(x[2 * m], x[2 * m + 1], tw[m - 1]);
+        ot_dft8_fix(x);
         if (MODE == 0) {
           const int i = 2 * c + h;
           if (jt < a.npencils) {
 #pragma unroll
-            for (int y = 0; y < kOtL; ++y) a.xout[((jt + ((int64_t)y << lna)) << 4) + i] = x[y];
+            for (int y = 0; y < kOtL; ++y)
+              a.xout[((jt + ((int64_t)y << lna)) << 4) + i] =
+                  make_double2(ot_fix_to_f64(x[2 * y], e2), ot_fix_to_f64(x[2 * y + 1], e2));
           }
         } else {
 #pragma unroll
-          for (int y = 0; y < kOtL; ++y) acc[y] = fma(x[y].x, x[y].x, fma(x[y].y, x[y].y, acc[y]));
+          for (int y = 0; y < kOtL; ++y) {
+            const double re = ot_fix_to_f64(x[2 * y], e2), im = ot_fix_to_f64(x[2 * y + 1], e2);
+            acc[y] = fma(re, re, fma(im, im, acc[y]));
+          }
         }
       }
       __syncwarp();
@@ -527,9 +548,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&sq_empty);
-        // |T|^2 carried 2^(2 (tau + sigma - 30)); with 1 / N^2, in two exact
-        // power-of-two steps
-        const double f = a.pscale * ot_pow2(es) * ot_pow2(es);
+        const double f = a.pscale;  // 1 / N^2
         const int64_t j = jt;
         if (j < a.npencils) {
 #pragma unroll

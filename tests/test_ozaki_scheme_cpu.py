@@ -19,13 +19,17 @@ The squaring (P_(k+1) = P_k^2, K = 2d):
     a wrong weight shift or a window that skips a K-block fails it.
 
 The FP64 level (d = 16, K = 32 per pencil row, one scale for the table):
-  * a weight's sum over K = 32 stays below 2^22, the int32 groups below 2^31,
-    hi and lo below 2^36 and 2^46, the drain's fixed point
-    V = 2^26 hi + floor(lo / 2^6) below 2^62 (one signed 64-bit integer), and
-    V 2^-26 rounded once to FP64 is within 2^-26 + 1 ulp of hi + 2^-32 lo;
+  * a weight's sum over K = 32 stays below 2^22 and reads back exactly
+    through the FP32 magic-number addition; the drain's fixed point
+    W = floor(E / 2^10), E = sum_w acc_w 2^(8 (6 - w)), equals the exact
+    floor and stays below 2^57 + 2;
   * T against the extended-precision contraction within the FP64 dot
-    product's bound, then twiddle, 8-point DFT and |X|^2 against numpy's;
-  * a wrong group shift or a sign slip in the table's real embedding fails.
+    product's bound; the Q61 twiddle products (split at bit 31) below 2^58,
+    the integer 8-point DFT below 2^61, and X converted to FP64 (rounded half
+    away from zero) against numpy's FFT of the exact T within a few units of
+    rounding, |X|^2 likewise;
+  * a wrong weight shift, a sign slip in the table's real embedding, in the
+    twiddle's cross term or in the DFT's rotation fails.
 """
 import numpy as np
 import pytest
@@ -156,9 +160,93 @@ def test_extreme_digits_bound():
 
 
 # ---------------------------------------------------------------- FP64 level
-def level_T(Z, M, group_err=False, sign_err=False):
-    """The level kernel's T[p][m][i] for pencils Z (P x 16 complex) and the
-    table M (8 x 16 x 16 complex, T = M Z), modelled step by step."""
+MAGIC = 0x4B400000            # bits of 1.5 * 2^23
+Q61 = 1 << 61
+C_Q61 = 1630477228166597777   # round(2^61 / sqrt(2))
+
+
+def q61(x):
+    """round(x 2^61), halves away from zero, exactly (x a float64)."""
+    from fractions import Fraction
+    f = Fraction(float(x)) * Q61
+    r = int(abs(f) + Fraction(1, 2))
+    return r if f >= 0 else -r
+
+
+def split31(v):
+    return v >> 31, v & 0x7FFFFFFF
+
+
+def tw_fix(wr, wi, qr, qi, plant=None):
+    """(wr + i wi)(qr + i qi) 2^-61 as the drain forms it (operands split at
+    bit 31, the low x low products dropped, the middle sums floored)."""
+    rh, rl = split31(wr)
+    ih, il = split31(wi)
+    qrh, qrl = split31(qr)
+    qih, qil = split31(qi)
+    sr = rh * qrl + rl * qrh - ih * qil - il * qih
+    si = rh * qil + rl * qih + (ih * qrl if plant != "tw_sign" else -ih * qrl) + il * qrh
+    assert abs(sr) < 2 ** 63 and abs(si) < 2 ** 63
+    return 2 * (rh * qrh - ih * qih) + (sr >> 30), 2 * (rh * qih + ih * qrh) + (si >> 30)
+
+
+def rot_fix(x):
+    xh, xl = split31(x)
+    ch, cl = split31(C_Q61)
+    return 2 * xh * ch + ((xh * cl + xl * ch) >> 30)
+
+
+def dft8_fix(x, plant=None):
+    """The drain's 8-point DFT on integers (x: 8 complex as [re, im] pairs)."""
+    x = [list(v) for v in x]
+    for p in range(4):
+        (ur, ui), (vr, vi) = x[p], x[p + 4]
+        x[p] = [ur + vr, ui + vi]
+        dr, di = ur - vr, ui - vi
+        if p == 0:
+            x[4] = [dr, di]
+        elif p == 1:
+            x[5] = [rot_fix(dr + di), rot_fix(di - dr)]
+        elif p == 2:
+            x[6] = [di, -dr]
+        else:
+            x[7] = [rot_fix(di - dr), -rot_fix(dr + di)] if plant != "rot" else [rot_fix(dr - di), -rot_fix(dr + di)]
+    for g in (0, 4):
+        for p in range(2):
+            (ur, ui), (vr, vi) = x[g + p], x[g + p + 2]
+            x[g + p] = [ur + vr, ui + vi]
+            x[g + p + 2] = [ur - vr, ui - vi] if p == 0 else [ui - vi, vr - ur]
+    for g in range(0, 8, 2):
+        (ur, ui), (vr, vi) = x[g], x[g + 1]
+        x[g], x[g + 1] = [ur + vr, ui + vi], [ur - vr, ui - vi]
+    x[1], x[4] = x[4], x[1]
+    x[3], x[6] = x[6], x[3]
+    return x
+
+
+def fix_to_f64(v, e2):
+    """v 2^e2 with the significand rounded half away from zero to 53 bits;
+    below 2^-1022: 0."""
+    a = abs(v)
+    if a == 0:
+        return 0.0
+    nb = a.bit_length()
+    if nb > 53:
+        sh = nb - 53
+        m, ex = (a >> sh) + ((a >> (sh - 1)) & 1), sh
+    else:
+        m, ex = a, 0
+    if nb + e2 - 1 < -1022:
+        return 0.0
+    r = float(np.ldexp(float(m), ex + e2))
+    return r if v > 0 else -r
+
+
+def level_fix(Z, M, ya, N, plant=None):
+    """The level kernel for pencils Z (P x 16 complex) and the table M
+    (8 x 16 x 16 complex, T = M Z), modelled step by step with exact
+    integers: returns T (as the fixed point W carries it) and, per pencil,
+    X[y][i] in FP64 and the bins sum_i |X[y][i]|^2."""
     Pn = Z.shape[0]
     A = np.empty((Pn, 32))
     A[:, 0::2], A[:, 1::2] = Z.real, Z.imag                  # k2 = 2 k + c'
@@ -169,7 +257,7 @@ def level_T(Z, M, group_err=False, sign_err=False):
                 n = 16 * i + 2 * m + c
                 re, im = M[m, i].real, M[m, i].imag
                 if c == 0:
-                    B[n, 0::2], B[n, 1::2] = re, (im if sign_err else -im)
+                    B[n, 0::2], B[n, 1::2] = re, (im if plant == "sign" else -im)
                 else:
                     B[n, 0::2], B[n, 1::2] = im, re
     emax = np.array([max(int(np.frexp(np.abs(r).max())[1]) + 1022 if np.abs(r).max() > 0 else 0, 0) for r in A])
@@ -179,50 +267,98 @@ def level_T(Z, M, group_err=False, sign_err=False):
     Bd = digits(B, np.full((256, 1), sig))
     acc = [sum(Ad[s] @ Bd[w - s].T for s in range(w + 1)) for w in range(S)]   # P x 256 each
     assert max(np.abs(a).max() for a in acc) < 2 ** 22
-    g0, g1 = acc[0], acc[1] * 256 + acc[2]
-    g2, g3 = acc[3] * 256 + acc[4], acc[5] * 256 + acc[6]
-    assert max(np.abs(g).max() for g in (g0, g1, g2, g3)) < 2 ** 31
-    hi = (g0 << 16) + g1
-    lo = (g2 << (8 if group_err else 16)) + g3
-    assert np.abs(hi).max() < 2 ** 36 and np.abs(lo).max() < 2 ** 46
-    V = (hi << 26) + (lo >> 6)                               # the drain's 62-bit fixed point (floor)
-    assert np.abs(V).max() < 2 ** 62
-    raw = V.astype(np.float64) * 2.0 ** -26                  # one rounding to nearest even
-    exact = hi.astype(np.longdouble) + lo.astype(np.longdouble) * np.longdouble(2.0) ** -32
-    assert np.all(np.abs(raw - exact) <= 2.0 ** -26 + U64 * np.abs(exact))
-    Tr = np.ldexp(raw, (tau + sig - 30)[:, None]).reshape(Pn, 16, 8, 2)  # [p][i][m][c]
-    return (Tr[..., 0] + 1j * Tr[..., 1]).transpose(0, 2, 1)             # [p][m][i]
+    # the accumulators read back as ints: FP32 acc + 1.5 2^23, bits - MAGIC
+    for a in acc:
+        f = a.astype(np.float32) + np.float32(12582912.0)
+        assert np.array_equal(f.view(np.int32).astype(np.int64) - MAGIC, a)
+    sh = [38, 30, 22, 14, 6]
+    if plant == "group":
+        sh[3] = 15
+    W = ((acc[5] * 256 + acc[6]) >> 10)
+    for w in range(5):
+        W = W + (acc[w] << sh[w])
+    E = sum(acc[w].astype(object) * (1 << (8 * (6 - w))) for w in range(S))
+    if plant is None:
+        assert np.all(W.astype(object) == E // 1024)        # floor(E / 2^10)
+    assert np.abs(W).max() < 2 ** 57 + 2
+    T = np.ldexp(W.astype(np.float64), (tau + sig - 52)[:, None]).reshape(Pn, 16, 8, 2)
+    T = (T[..., 0] + 1j * T[..., 1]).transpose(0, 2, 1)     # [p][m][i] (exact up to FP64 rounding of W)
+    Wr = W.reshape(Pn, 16, 8, 2)
+    X = np.zeros((Pn, 8, 16), dtype=np.complex128)
+    for p in range(Pn):
+        tw = np.exp(-2j * np.pi * (np.arange(8) * int(ya[p]) % N) / N)
+        q = [(q61(t.real), q61(t.imag)) for t in tw]
+        for i in range(16):
+            x = [[int(Wr[p, i, m, 0]), int(Wr[p, i, m, 1])] for m in range(8)]
+            for m in range(1, 8):
+                x[m] = list(tw_fix(x[m][0], x[m][1], *q[m], plant=plant))
+                assert max(abs(x[m][0]), abs(x[m][1])) < 2 ** 58
+            X8 = dft8_fix(x, plant)
+            assert max(max(abs(v[0]), abs(v[1])) for v in X8) < 2 ** 61
+            e2 = int(tau[p] + sig - 52)
+            for y in range(8):
+                X[p, y, i] = complex(fix_to_f64(X8[y][0], e2), fix_to_f64(X8[y][1], e2))
+    hist = (X.real ** 2 + X.imag ** 2).sum(2)
+    return T, X, hist, np.ldexp(1.0, tau + sig - 52)
 
 
 def _level_inputs(seed):
     rng = np.random.default_rng(seed)
-    Z = (rng.standard_normal((40, 16)) + 1j * rng.standard_normal((40, 16))) * np.exp(rng.uniform(-20, 20, 40))[:, None]
+    Z = (rng.standard_normal((24, 16)) + 1j * rng.standard_normal((24, 16))) * np.exp(rng.uniform(-20, 20, 24))[:, None]
     Z[5] = 0.0
     Z[6] *= 1e-200
     V = np.linalg.qr(rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16)))[0]
     M = np.stack([np.linalg.matrix_power(V, m) for m in range(8)])
-    return Z, M
+    ya = rng.integers(0, 1 << 12, 24)
+    return Z, M, ya, 1 << 15
+
+
+def _level_ref(Z, M, ya, N):
+    Tref = np.einsum("mik,pk->pmi", M.astype(np.clongdouble), Z.astype(np.clongdouble))
+    w = np.exp(-2j * np.pi * (np.outer(ya, np.arange(8)) % N) / N)
+    Xref = np.fft.fft(Tref.astype(np.complex128) * w[:, :, None], axis=1)
+    return Tref, Xref
 
 
 def test_fp64_level_contraction_and_epilogue():
-    Z, M = _level_inputs(3)
-    T = level_T(Z, M)
-    Tref = np.einsum("mik,pk->pmi", M.astype(np.clongdouble), Z.astype(np.clongdouble))
+    Z, M, ya, N = _level_inputs(3)
+    T, X, hist, unit = level_fix(Z, M, ya, N)
+    Tref, Xref = _level_ref(Z, M, ya, N)
+    # the contraction within the FP64 dot product's bound plus the fixed
+    # point's floor (one unit of 2^(tau + sigma - 52), 2^-57 of the pencil's
+    # bound |T| < 2^(tau + sigma + 5)) and the FP64 rounding of W
     bound = np.einsum("mik,pk->pmi", np.abs(M), np.abs(Z))
-    assert np.all(np.abs(T - Tref) <= 8 * U64 * bound + 1e-300)
-    # twiddle, 8-point DFT over m (exp(-2 pi i m y / 8)) and |X|^2 summed over i
-    ya = np.arange(40)
-    w = np.exp(-2j * np.pi * np.outer(ya, np.arange(8)) / 2 ** 12)
-    X = np.fft.fft(T * w[:, :, None], axis=1)
-    Xref = np.fft.fft(Tref.astype(np.complex128) * w[:, :, None], axis=1)
-    hist, href = (np.abs(X) ** 2).sum(2), (np.abs(Xref) ** 2).sum(2)
-    assert np.all(np.abs(hist - href) <= 1e-13 * href.max(axis=1, keepdims=True) + 1e-300)
+    assert np.all(np.abs(T - Tref) <= 8 * U64 * bound + 2 * unit[:, None, None] + 1e-300)
+    # twiddle and 8-point DFT in fixed point against numpy's FFT of the exact
+    # T: within a few units of rounding of each pencil's largest |X|
+    scale = np.abs(Xref).max(axis=(1, 2), keepdims=True)
+    assert np.all(np.abs(X - Xref) <= 64 * U64 * scale + 1e-300)
+    href = (np.abs(Xref) ** 2).sum(2)
+    assert np.all(np.abs(hist - href) <= 256 * U64 * href.max(axis=1, keepdims=True) + 1e-300)
     assert np.all(hist[5] == 0.0)
 
 
-@pytest.mark.parametrize("plant", ["group", "sign"])
+def test_fp64_level_fix_to_f64_rounding():
+    """The integer-to-FP64 conversion: exact below 2^53, half away from zero
+    above, a carry into the exponent, the unit's power of two, flush below
+    2^-1022."""
+    assert fix_to_f64(12345, -3) == 12345 / 8
+    assert fix_to_f64(-(2 ** 53 + 1), 0) == -float(2 ** 53 + 2)     # half: away from zero
+    assert fix_to_f64(2 ** 54 + 1, 0) == float(2 ** 54)
+    assert fix_to_f64(2 ** 60 - 1, -60) == 1.0                       # carry into the exponent
+    assert fix_to_f64(3, -1025) == 0.0 and fix_to_f64(1, -1022) == 2.0 ** -1022
+    import math
+    from fractions import Fraction
+    rng = np.random.default_rng(1)
+    for v in rng.integers(-(2 ** 62), 2 ** 62, 200):
+        v = int(v)
+        r = fix_to_f64(v, -40)
+        assert abs(Fraction(r) - Fraction(v, 2 ** 40)) <= Fraction(math.ulp(r)) / 2
+
+
+@pytest.mark.parametrize("plant", ["group", "sign", "tw_sign", "rot"])
 def test_fp64_level_planted_mistakes_fail(plant):
-    Z, M = _level_inputs(4)
-    T = level_T(Z, M, group_err=plant == "group", sign_err=plant == "sign")
-    Tref = np.einsum("mik,pk->pmi", M, Z)
-    assert np.abs(T - Tref).max() > 1e-10 * np.abs(Tref).max()
+    Z, M, ya, N = _level_inputs(4)
+    T, X, hist, _ = level_fix(Z, M, ya, N, plant=plant)
+    _, Xref = _level_ref(Z, M, ya, N)
+    assert np.abs(X - Xref).max() > 1e-10 * np.abs(Xref).max()
