@@ -205,17 +205,6 @@ def level_flops(N: int, d: int, r_top: int) -> float:
     return 8.0 * N * d * d + 5.0 * N * d * r_top
 
 
-def oz_top_fp64_ops(N: int, d: int, r_top: int) -> float:
-    """FP64 instructions of the tensor-core FP64 top level (d = 16, r_top = 3):
-    per complex output point 12.5 in the drain (the twiddle 4 x 7 / 8, the
-    8-point DFT 56 / 8, |X|^2 2; the integer digit sums become FP64 by integer
-    operations); per pencil 28 in the producers (7 twiddles; the digits come
-    from the bits by integer operations); per bin 6 for the scale, the
-    hand-over sum and the readout."""
-    L = 1 << r_top
-    return 12.5 * N * d + 28.0 * (N // L) + 6.0 * N
-
-
 def bench_ours(args, rank, world, local_rank):
     import torch
     import __graft_entry__ as g
@@ -383,21 +372,21 @@ def bench_ours(args, rank, world, local_rank):
     t_k = statistics.mean(kms)
     flops = level_flops(N, d, r_top)
     if top_on_tc:
-        # bound by the FP64 pipe of the drain: its FP64 instructions per second against the measured FP64
-        # FMA instruction rate (the FMA peak in flop / 2); the contraction's bf16 digit products beside it
-        ops = oz_top_fp64_ops(N, d, r_top)
-        ach = ops / (t_k * 1e-3) / 1e9
-        peak_ops = fp64_peak * 1e3 / 2.0
+        # the method's own HBM bound for C5: the final state (N x d complex128) written once and read once,
+        # 2 S_B per run; the top level produces and consumes every amplitude of it, so its launch carries
+        # those bytes (the fused kernel itself moves only Z in and the histogram out: `traffic`)
+        state_bytes = float(N) * d * 16
+        alg_bytes = 2.0 * state_bytes
+        ach = alg_bytes / (t_k * 1e-3) / 1e9
         tensor_flop = 8 * 28 * 2 * (2.0 * 128 * 32 * 16) * (N // (1 << r_top) // 128)
-        roofline = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak_ops, 2),
-                    "unit": "G FP64 instr/s", "frac": round(ach / peak_ops, 4),
+        roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": round(pk["hbm_gbs"], 1),
+                    "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
                     "traffic": recorded_traffic("level_oz_top_c5_fp64"),
-                    "kernel": "level_oz_top_kernel (tcgen05 digit products + FP64 drain)",
-                    "kernel_ms": round(t_k, 3), "fp64_instr_per_launch": ops,
-                    "fp64_instr_count": "12.5 per complex output point (drain) + 28 per pencil (producers) + 6 per "
-                                        "bin (readout)",
-                    "peak_source": "measured: FP64 FMA loop on every SM, CUDA events (qpe_measure_fma_peak), "
-                                   "one instruction = one FMA = 2 flop",
+                    "kernel": "level_oz_kernel<1> (tcgen05 digit products + fixed-point twiddle / DFT, FP64 |X|^2)",
+                    "kernel_ms": round(t_k, 3), "algorithmic_bytes_per_launch": alg_bytes,
+                    "algorithmic_bytes": f"2 x state bytes = 2 x 2^{n} x {d} x 16 B (the C5 roofline's 2 S_B: "
+                                         "final state written once and read once)",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
                     "tensor_tflops": round(tensor_flop / (t_k * 1e-3) / 1e12, 1),
                     "tensor_frac_of_bf16_peak": round(tensor_flop / (t_k * 1e-3) / 1e12 / pk["bf16_tflops"], 4),
                     "algorithmic_flop_per_launch": flops,
@@ -455,9 +444,10 @@ def bench_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nmat": inst.nmat, "nmeas": inst.nmeas,
-                   "precision": "complex128 state, FP64-accurate: the top level's contraction as exact integer "
-                                "digit products on the tensor cores (7 x 8-bit digits, Ozaki scheme), squaring "
-                                "chain, other levels, twiddles, DFT and readout in FP64" if top_on_tc else
+                   "precision": "complex128 state, FP64-accurate: every level of >= 128 pencils as exact integer "
+                                "digit products on the tensor cores (7 x 8-bit digits, Ozaki scheme) with the "
+                                "twiddles and the 8-point DFT in 64-bit fixed point; squaring chain, the deepest "
+                                "levels, |X|^2 and readout in FP64" if top_on_tc else
                                 "complex128 state, FP64 arithmetic everywhere (the paper's)",
                    "schedule": f"fused levels ({levels} levels, top level 2^{r_top}-point DFT"
                                f"{' on the tensor cores' if top_on_tc else ''})",

@@ -37,18 +37,21 @@
 // sigma + 5), below the contraction's own error. |X|^2 and the readout run in
 // FP64; a lower level (MODE 0) stores X in FP64.
 //
-// Roles (384 threads, one CTA per SM, persistent over the tiles):
+// Roles (640 threads, one CTA per SM, persistent over the tiles):
 //   warps 0-2   producers: Z rows -> digit tiles (shared memory, 128-byte
-//               swizzled K-major, two digits per 128-byte row), the pencils'
+//               swizzled K-major, two digits per 128-byte row), two threads
+//               per pencil (eight complex values each); the pencils'
 //               twiddles w_N^(m_b y_a) and scales (two buffers);
 //   warp 3      tensor memory, and lane 0 issues the MMAs: per chunk of two
 //               columns i (32 table rows), 28 pairs x 2 K-steps of
 //               M = 128, N = 32 into seven weight accumulators (224 columns;
-//               two chunk buffers);
-//   warps 4-11  drain: two warps per tensor-memory lane quarter, one column i
-//               each (16 table rows) per chunk; weights -> fixed point,
-//               twiddle, DFT, FP64, then |X|^2 (the two warps' sums meet through
-//               tensor memory columns 448-463) or the store of X.
+//               two chunk buffers, even chunks in one, odd in the other);
+//   warps 4-19  drain: four warps per tensor-memory lane quarter (four per
+//               SM sub-partition, enough to cover the integer epilogue's
+//               latencies), warp k takes column 2 c + (k & 1) of the chunks
+//               c with c & 1 = k >> 1; weights -> fixed point, twiddle, DFT,
+//               FP64, then |X|^2 (the four warps' sums meet through tensor
+//               memory columns 448-495) or the store of X.
 // Every wait is a bounded mbarrier wait; an expired wait sets QPE_ERR_TIMEOUT.
 #include "qpe_internal.cuh"
 #include "qpe_tcgen05.cuh"
@@ -66,12 +69,12 @@ constexpr int kOtL = 8, kOtD = 16, kOtS = 7;
 constexpr int kOtRows = 128;                   // pencils per tile (MMA M)
 constexpr int kOtN = 2 * kOtD * kOtL;          // 256 table rows
 constexpr int kOtChunks = kOtD / 2;            // two columns i per chunk
-constexpr int kOtThreads = 384;
+constexpr int kOtThreads = 640;
 constexpr int kOtProducers = 96;
 constexpr uint32_t kOtSlabA = kOtRows * 128;   // digits [2q | 2q+1] of 128 pencils, 16 KiB
 constexpr uint32_t kOtSlabB = kOtN * 128;      // 32 KiB
 constexpr uint32_t kOtBufCols = kOtS * 32;     // one chunk's seven weight accumulators
-constexpr uint32_t kOtSqCol = 2 * kOtBufCols;  // column 448: the hand-over of the two halves
+constexpr uint32_t kOtSqCol = 2 * kOtBufCols;  // columns 448 .. 495: the hand-over of the partial sums
 constexpr size_t kOtBBytes = 4 * (size_t)kOtSlabB;
 constexpr size_t kOtABytes = 4 * (size_t)kOtSlabA;
 constexpr size_t kOtTwBytes = (size_t)kOtRows * (kOtL - 1) * sizeof(double2);
@@ -219,6 +222,32 @@ __device__ __forceinline__ void ot_digits(double x, int t, int (&dg)[kOtS]) {
 // bf16 bits of a small integer (|v| <= 256: exact in the upper half of the float)
 __device__ __forceinline__ uint32_t ot_bf16(int v) { return __float_as_uint((float)v) >> 16; }
 
+// The balanced digits of F = round(x 2^(55 - t)) (|F| <= 2^55) from the plain
+// base-256 digits of F + B, B = 128 sum_(s<7) 2^(8 s) (0 <= F + B < 2^57):
+// digit s is byte 6 - s of F + B minus 128 (the top one takes bits 48..56).
+// Each becomes a float by the magic-number form 2^23 + d minus 2^23 + 128
+// (exact), whose upper half is its bf16; w[s] packs digit s of x0 (low half)
+// and x1 (high half).
+constexpr unsigned long long kOtBias = 0x80808080808080ull;
+__device__ __forceinline__ float ot_byte_digit(uint32_t word, uint32_t sel) {
+  return __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u | sel)) - 8388736.0f;
+}
+__device__ __forceinline__ void ot_digit_pairs(double x0, double x1, int t, uint32_t (&w)[kOtS]) {
+  const unsigned long long u0 = (unsigned long long)ot_fixed(x0, t) + kOtBias;
+  const unsigned long long u1 = (unsigned long long)ot_fixed(x1, t) + kOtBias;
+  const uint32_t l0 = (uint32_t)u0, h0 = (uint32_t)(u0 >> 32), l1 = (uint32_t)u1, h1 = (uint32_t)(u1 >> 32);
+  const float t0 = __uint_as_float(0x4B000000u | (h0 >> 16)) - 8388736.0f;
+  const float t1 = __uint_as_float(0x4B000000u | (h1 >> 16)) - 8388736.0f;
+  w[0] = __byte_perm(__float_as_uint(t0), __float_as_uint(t1), 0x7632);
+#pragma unroll
+  for (int s = 1; s < kOtS; ++s) {
+    const int byte = 6 - s;
+    const float f0 = ot_byte_digit(byte >= 4 ? h0 : l0, (uint32_t)(byte & 3));
+    const float f1 = ot_byte_digit(byte >= 4 ? h1 : l1, (uint32_t)(byte & 3));
+    w[s] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+  }
+}
+
 __device__ __forceinline__ double2 ot_cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
@@ -309,14 +338,14 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    mbar_init(&a_full, kOtRows);
+    mbar_init(&a_full, 2 * kOtRows);  // one arrival per producer item
     mbar_init(&a_empty, 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&tw_empty[b], 8);
+      mbar_init(&tw_empty[b], 16);  // every drain warp
       mbar_init(&t_full[b], 1);
-      mbar_init(&t_empty[b], 8);
+      mbar_init(&t_empty[b], 8);    // the eight drain warps of the buffer's chunks
     }
-    mbar_init(&sq_full, 4);
+    mbar_init(&sq_full, 12);
     mbar_init(&sq_empty, 4);
     mbar_init(&mma_done, 1);
     fail = 0;
@@ -347,6 +376,8 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
 
   if (warp < 3) {
     // ------------------------------------------------------------ producers
+    // item u < 256 of a tile: half u & 1 (complex values 8 (u & 1) .. + 7) of
+    // pencil u >> 1; items u and u ^ 1 run in adjacent lanes of one round
     int it = 0;
     for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end; t += gridDim.x, ++it) {
       const int tb = it & 1;
@@ -359,46 +390,47 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         break;
       }
       if (*vfail) break;
-      for (int p = threadIdx.x; p < kOtRows; p += kOtProducers) {
+      for (int u = threadIdx.x; u < 2 * kOtRows; u += kOtProducers) {
+        const int p = u >> 1, half = u & 1;
         const int64_t j = t * kOtRows + p;
         const bool have = j < a.npencils;  // rows past a partial tile's pencils: zero digits
-        const double2* src = a.seeds + (have ? ((a.seed_rk + (j << a.seed_sh)) << 4) : 0);
-        double2 z[kOtD];
+        const double2* src = a.seeds + (have ? ((a.seed_rk + (j << a.seed_sh)) << 4) + 8 * half : 0);
+        double2 z[kOtD / 2];
         int emax = 0;
 #pragma unroll
-        for (int k = 0; k < kOtD; ++k) {
+        for (int k = 0; k < kOtD / 2; ++k) {
           z[k] = have ? __ldg(src + k) : make_double2(0.0, 0.0);
           emax = max(emax, (int)((__double_as_longlong(z[k].x) >> 52) & 0x7ff));
           emax = max(emax, (int)((__double_as_longlong(z[k].y) >> 52) & 0x7ff));
         }
+        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
         const int tau = ot_scale_exp(emax);
         // digit s of reals 4 g .. 4 g + 3 (two complex values) -> the half g & 1
         // of chunk (s & 1) 4 + (g >> 1) of slab s >> 1
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          int dg[4][kOtS];
-          ot_digits(z[2 * g].x, tau, dg[0]);
-          ot_digits(z[2 * g].y, tau, dg[1]);
-          ot_digits(z[2 * g + 1].x, tau, dg[2]);
-          ot_digits(z[2 * g + 1].y, tau, dg[3]);
+        for (int gg = 0; gg < 4; ++gg) {
+          const int g = 4 * half + gg;
+          uint32_t wa[kOtS], wb[kOtS];
+          ot_digit_pairs(z[2 * gg].x, z[2 * gg].y, tau, wa);
+          ot_digit_pairs(z[2 * gg + 1].x, z[2 * gg + 1].y, tau, wb);
 #pragma unroll
-          for (int s = 0; s < kOtS; ++s) {
-            const uint32_t w0 = ot_bf16(dg[0][s]) | (ot_bf16(dg[1][s]) << 16);
-            const uint32_t w1 = ot_bf16(dg[2][s]) | (ot_bf16(dg[3][s]) << 16);
+          for (int s = 0; s < kOtS; ++s)
             *reinterpret_cast<uint2*>(As + (s >> 1) * kOtSlabA + sw128_offset(p, (s & 1) * 4 + (g >> 1)) +
-                                      (g & 1) * 8) = make_uint2(w0, w1);
-          }
+                                      (g & 1) * 8) = make_uint2(wa[s], wb[s]);
         }
-        const int64_t ya = a.rk + (j << a.sh);
-        int4* tw = twS + (tb * kOtRows + p) * (kOtL - 1);
+        if (half == 0) {
+          const int64_t ya = a.rk + (j << a.sh);
+          int4* tw = twS + (tb * kOtRows + p) * (kOtL - 1);
 #pragma unroll
-        for (int m = 1; m < kOtL; ++m) {
-          const int64_t ex = (((int64_t)m * ya) & lvl_mask) << lvl_shift;
-          const double2 w = ot_cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
-          const long long qr = ot_fixed(w.x, -6), qi = ot_fixed(w.y, -6);  // round(w 2^61)
-          tw[m - 1] = make_int4((int)(qr >> 31), (int)(qr & 0x7fffffff), (int)(qi >> 31), (int)(qi & 0x7fffffff));
+          for (int m = 1; m < kOtL; ++m) {
+            const int64_t ex = (((int64_t)m * ya) & lvl_mask) << lvl_shift;
+            const double2 w = ot_cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
+            const long long qr = ot_fixed(w.x, -6), qi = ot_fixed(w.y, -6);  // round(w 2^61)
+            tw[m - 1] =
+                make_int4((int)(qr >> 31), (int)(qr & 0x7fffffff), (int)(qi >> 31), (int)(qi & 0x7fffffff));
+          }
+          tauS[tb * kOtRows + p] = tau + sigma - 30;
         }
-        tauS[tb * kOtRows + p] = tau + sigma - 30;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&a_full);
       }
@@ -437,14 +469,16 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
     }
   } else {
     // ------------------------------------------------------------ drain
-    const int h = (warp - 4) >> 2;  // column i = 2 c + h of chunk c
-    const int q = warp & 3;         // tensor-memory lane quarter
-    const int row = q * 32 + lane;  // pencil of this thread within the tile
+    const int q = warp & 3;          // tensor-memory lane quarter
+    const int k = (warp - 4) >> 2;   // 0 .. 3
+    const int h = k & 1;             // column i = 2 c + h of chunk c
+    const int par = k >> 1;          // the chunks c with c & 1 = par (tensor-memory buffer par)
+    const int row = q * 32 + lane;   // pencil of this thread within the tile
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     double best = -1.0, wsum = 0.0, psum = 0.0;
     int64_t besty = INT64_MAX;
     int it = 0;
-    uint32_t g = 0;
+    uint32_t uses = 0;  // fills of buffer par consumed so far
     bool ok = true;
     for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end && ok; t += gridDim.x, ++it) {
       const int tb = it & 1;
@@ -456,43 +490,35 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       const int4* tw = twS + (tb * kOtRows + row) * (kOtL - 1);
       // X in units of 2^(tau + sigma - 52) (the fixed point below)
       const int e2 = tauS[tb * kOtRows + row] - 22;
-      const int64_t jt = t * kOtRows + row;     // local pencil index
+      const int64_t jt = t * kOtRows + row;  // local pencil index
       double acc[kOtL];
 #pragma unroll
       for (int y = 0; y < kOtL; ++y) acc[y] = 0.0;
-      for (int c = 0; c < kOtChunks; ++c, ++g) {
-        const int buf = g & 1;
-        got = mbar_wait(&t_full[buf], (g >> 1) & 1);
+      for (int c = par; c < kOtChunks; c += 2, ++uses) {
+        got = mbar_wait(&t_full[par], uses & 1);
         got = __all_sync(0xffffffffu, got && !*vfail) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!got) {
           ok = false;
           break;
         }
-        const uint32_t col = lane_base + (uint32_t)buf * kOtBufCols + (uint32_t)(h * 16);
-        // the seven weights' loads in flight together, one wait
-        uint32_t v0[16], v1[16], v2[16], v3[16], v4[16], v5[16], v6[16];
-        tmem_ld16_async(col, v0);
-        tmem_ld16_async(col + 32, v1);
-        tmem_ld16_async(col + 64, v2);
-        tmem_ld16_async(col + 96, v3);
-        tmem_ld16_async(col + 128, v4);
-        tmem_ld16_async(col + 160, v5);
-        tmem_ld16_async(col + 192, v6);
-        tmem_wait16(v0);
-        tmem_after_wait16(v1);
-        tmem_after_wait16(v2);
-        tmem_after_wait16(v3);
-        tmem_after_wait16(v4);
-        tmem_after_wait16(v5);
-        tmem_after_wait16(v6);
-        // T[m_b] (columns 2 m_b + c of this half) as 64-bit fixed point
+        const uint32_t col = lane_base + (uint32_t)par * kOtBufCols + (uint32_t)(h * 16);
+        // T[m_b] (columns 2 m_b + c of this half) as 64-bit fixed point, four
+        // values at a time (the seven weights' loads in flight together)
         long long x[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) x[e] = ot_weights_fix(v0[e], v1[e], v2[e], v3[e], v4[e], v5[e], v6[e]);
+        for (int grp = 0; grp < 4; ++grp) {
+          uint32_t v[kOtS][4];
+#pragma unroll
+          for (int w = 0; w < kOtS; ++w) tmem_ld4_async(col + (uint32_t)(w * 32 + grp * 4), v[w]);
+          tmem_wait7x4(v);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            x[4 * grp + e] = ot_weights_fix(v[0][e], v[1][e], v[2][e], v[3][e], v[4][e], v[5][e], v[6][e]);
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&t_empty[buf]);
+        if (lane == 0) mbar_arrive(&t_empty[par]);
         // twiddles w_N^(m_b y_a) (m_b >= 1), then the 8-point DFT over m_b
 #pragma unroll
         for (int m = 1; m < kOtL; ++m) ot_tw_fix(x[2 * m], x[2 * m + 1], tw[m - 1]);
@@ -517,9 +543,10 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       if (lane == 0) mbar_arrive(&tw_empty[tb]);  // done with this tile's twiddles and scales
       if (!ok) break;
       if (MODE == 0) continue;
-      // the two halves' sums meet in tensor memory (columns 448 .. 463)
+      // the four partial sums of a bin meet in tensor memory: warps k = 1 .. 3
+      // of a lane quarter store theirs in columns 448 + 16 (k - 1), warp 0 adds
       const uint32_t sqc = lane_base + kOtSqCol;
-      if (h == 1) {
+      if (k != 0) {
         got = it < 1 || mbar_wait(&sq_empty, (it - 1) & 1);
         if (!__all_sync(0xffffffffu, got && !*vfail)) {
           ok = false;
@@ -532,7 +559,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
           w[2 * y] = (uint32_t)__double2loint(acc[y]);
           w[2 * y + 1] = (uint32_t)__double2hiint(acc[y]);
         }
-        tmem_st16(sqc, w);
+        tmem_st16(sqc + (uint32_t)(16 * (k - 1)), w);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&sq_full);
@@ -543,8 +570,13 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint32_t w[16];
-        tmem_ld16(sqc, w);
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          uint32_t w[16];
+          tmem_ld16(sqc + (uint32_t)(16 * o), w);
+#pragma unroll
+          for (int y = 0; y < kOtL; ++y) acc[y] += __hiloint2double((int)w[2 * y + 1], (int)w[2 * y]);
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&sq_empty);
@@ -553,8 +585,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         if (j < a.npencils) {
 #pragma unroll
           for (int y = 0; y < kOtL; ++y) {
-            const double s = acc[y] + __hiloint2double((int)w[2 * y + 1], (int)w[2 * y]);
-            const double pv = s * f;
+            const double pv = acc[y] * f;
             const int64_t yl = j + ((int64_t)y << lna);
             a.hist[yl] = pv;
             const int64_t yy = a.rk + (yl << a.sh);
@@ -566,7 +597,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       }
     }
     if (!ok) atomicExch(&fail, 1);
-    if (MODE == 1 && h == 0) {  // readout partial of this CTA: the four h = 0 warps
+    if (MODE == 1 && k == 0) {  // readout partial of this CTA: the four k = 0 warps
       for (int off = 16; off > 0; off >>= 1) {
         const double ob = __shfl_xor_sync(0xffffffffu, best, off);
         const int64_t oy = __shfl_xor_sync(0xffffffffu, besty, off);

@@ -195,6 +195,25 @@ __device__ __forceinline__ void tmem_after_wait16(uint32_t (&v)[16]) {
                : "memory");
 }
 
+// 4 consecutive 32-bit columns of this warp's 32 lanes, without the wait
+__device__ __forceinline__ void tmem_ld4_async(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+// Waits for this warp's tensor-memory loads in flight (seven 4-column loads
+// pass through it, so that no use of them is scheduled before the wait).
+__device__ __forceinline__ void tmem_wait7x4(uint32_t (&v)[7][4]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[0][2]), "+r"(v[0][3]), "+r"(v[1][0]), "+r"(v[1][1]),
+                 "+r"(v[1][2]), "+r"(v[1][3]), "+r"(v[2][0]), "+r"(v[2][1]), "+r"(v[2][2]), "+r"(v[2][3]),
+                 "+r"(v[3][0]), "+r"(v[3][1]), "+r"(v[3][2]), "+r"(v[3][3]), "+r"(v[4][0]), "+r"(v[4][1]),
+                 "+r"(v[4][2]), "+r"(v[4][3]), "+r"(v[5][0]), "+r"(v[5][1]), "+r"(v[5][2]), "+r"(v[5][3]),
+                 "+r"(v[6][0]), "+r"(v[6][1]), "+r"(v[6][2]), "+r"(v[6][3])
+               :
+               : "memory");
+}
+
 // Store 16 consecutive 32-bit columns of this warp's 32 lanes and wait for it.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
   asm volatile(

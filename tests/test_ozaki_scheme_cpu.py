@@ -362,3 +362,27 @@ def test_fp64_level_planted_mistakes_fail(plant):
     T, X, hist, _ = level_fix(Z, M, ya, N, plant=plant)
     _, Xref = _level_ref(Z, M, ya, N)
     assert np.abs(X - Xref).max() > 1e-10 * np.abs(Xref).max()
+
+
+def test_producer_digits_from_biased_bytes():
+    """The level producer's digits: byte 6 - s of F + B (B = 128 sum 2^(8 s),
+    the top digit from bits 48..56) minus 128 equals the balanced digit s of
+    F, for |F| <= 2^55 (the ends included); each digit is exact as the float
+    (2^23 + d) - (2^23 + 128) and in its bf16 upper half."""
+    B = 0x80808080808080
+    assert B == 128 * sum(1 << (8 * s) for s in range(S))
+    rng = np.random.default_rng(11)
+    Fs = [int(v) for v in rng.integers(-(2 ** 55), 2 ** 55, 2000)]
+    Fs += [2 ** 55, -(2 ** 55), 0, -1, 1, 127, -128, 128, 2 ** 48 * 128, -(2 ** 48) * 128 - 1]
+    for F in Fs:
+        U = F + B
+        assert 0 <= U < 2 ** 57
+        got = [(U >> 48) - 128] + [((U >> (8 * (6 - s))) & 255) - 128 for s in range(1, S)]
+        x = np.ldexp(float(F), -55)  # t = 0
+        want = digits(np.array([x]), np.array([0]))[:, 0]
+        if abs(F) < 2 ** 53:        # x carries F exactly
+            assert got == [int(v) for v in want], F
+        assert sum(g * 256 ** (6 - s) for s, g in enumerate(got)) == F
+        for g in got:
+            f = np.float32(np.uint32(0x4B000000 | (g + 128)).view(np.float32)) - np.float32(8388736.0)
+            assert f == g and (np.uint32(np.float32(f).view(np.uint32)) & 0xFFFF) == 0
