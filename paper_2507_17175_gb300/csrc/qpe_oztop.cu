@@ -68,17 +68,20 @@ namespace {
 constexpr int kOtL = 8, kOtD = 16, kOtS = 7;
 constexpr int kOtRows = 128;                   // pencils per tile (MMA M)
 constexpr int kOtN = 2 * kOtD * kOtL;          // 256 table rows
-constexpr int kOtChunks = kOtD / 2;            // two columns i per chunk
+constexpr int kOtChunks = kOtD;                // one column i (16 table rows) per chunk
 constexpr int kOtThreads = 640;
 constexpr int kOtProducers = 96;
 constexpr uint32_t kOtSlabA = kOtRows * 128;   // digits [2q | 2q+1] of 128 pencils, 16 KiB
-constexpr uint32_t kOtSlabB = kOtN * 128;      // 32 KiB
-constexpr uint32_t kOtBufCols = kOtS * 32;     // one chunk's seven weight accumulators
-constexpr uint32_t kOtSqCol = 2 * kOtBufCols;  // columns 448 .. 495: the hand-over of the partial sums
-constexpr size_t kOtBBytes = 4 * (size_t)kOtSlabB;
-constexpr size_t kOtABytes = 4 * (size_t)kOtSlabA;
-constexpr size_t kOtTwBytes = (size_t)kOtRows * (kOtL - 1) * sizeof(double2);
-constexpr size_t kOtSmem = kOtBBytes + kOtABytes + 2 * kOtTwBytes + 2 * kOtRows * sizeof(int) + 1024;
+constexpr uint32_t kOtBSlab = 16 * 128;        // digits [2q | 2q+1] of one chunk's 16 rows, 2 KiB
+constexpr uint32_t kOtBChunk = 4 * kOtBSlab;   // one chunk's seven digits, 8 KiB
+constexpr int kOtBStages = 6;                  // ring of table chunks
+constexpr uint32_t kOtBufCols = kOtS * 16;     // one chunk's seven weight accumulators (four buffers)
+constexpr uint32_t kOtSqCol = 4 * kOtBufCols;  // columns 448 .. 495: the hand-over of the partial sums
+constexpr size_t kOtBBytes = (size_t)kOtChunks * kOtBChunk;  // the table's image in global memory, 128 KiB
+constexpr size_t kOtABytes = 4 * (size_t)kOtSlabA;           // one tile's digits (two buffers)
+constexpr size_t kOtTwBytes = (size_t)kOtRows * (kOtL - 1) * sizeof(int4);
+constexpr size_t kOtSmem =
+    2 * kOtABytes + kOtBStages * (size_t)kOtBChunk + 2 * kOtTwBytes + 2 * kOtRows * sizeof(int) + 1024;
 static_assert(kOtSmem <= 227 * 1024, "shared memory of the FP64 top level");
 
 // v 2^e2 in FP64 for a signed integer |v| < 2^63, by integer operations on
@@ -252,15 +255,15 @@ __device__ __forceinline__ double2 ot_cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-// The MMAs of one chunk: pair (S, T) into weight S + T, two K = 16 steps of
-// the 32-wide digit (digit s sits in half s & 1 of slab s >> 1).
+// The MMAs of one chunk: pair (S, T) into weight S + T (16 columns each), two
+// K = 16 steps of the 32-wide digit (digit s sits in half s & 1 of slab s >> 1).
 template <int S, int T>
 __device__ __forceinline__ void ot_pairs(uint32_t d0, uint64_t a0, uint64_t b0, uint32_t idesc) {
   if constexpr (S < kOtS) {
     if constexpr (S + T < kOtS) {
       const uint64_t ad = a0 + (uint64_t)((S >> 1) * (kOtSlabA >> 4) + (S & 1) * 4);
-      const uint64_t bd = b0 + (uint64_t)((T >> 1) * (kOtSlabB >> 4) + (T & 1) * 4);
-      const uint32_t d = d0 + (uint32_t)((S + T) * 32);
+      const uint64_t bd = b0 + (uint64_t)((T >> 1) * (kOtBSlab >> 4) + (T & 1) * 4);
+      const uint32_t d = d0 + (uint32_t)((S + T) * 16);
       umma_k<kTcBF16>(d, ad, bd, idesc, S == 0 ? 0u : 1u);
       umma_k<kTcBF16>(d, ad + 2, bd + 2, idesc, 1u);
       ot_pairs<S, T + 1>(d0, a0, b0, idesc);
@@ -272,8 +275,10 @@ __device__ __forceinline__ void ot_pairs(uint32_t d0, uint64_t a0, uint64_t b0, 
 
 // The table's digits: rows n = 16 i + 2 m_b + c, K index k2 = 2 k + c'
 // (value Re M, -Im M, Im M, Re M for (c, c') = (0,0), (0,1), (1,0), (1,1)),
-// stored [slab q][row n][64 bf16] with digit 2q in the first 32 and 2q + 1 in
-// the second; sigma (|M| < 2^sigma) after the digits. One CTA.
+// as the shared-memory image of each chunk (column i): [chunk i][slab q]
+// [row n mod 16][128 bytes, 128-byte swizzled], digit 2q in the first 64
+// bytes of a row and 2q + 1 in the second (the unused digit 7 zero); sigma
+// (|M| < 2^sigma) after the image. One CTA.
 __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __restrict__ tab,
                                                            unsigned short* __restrict__ out, int* __restrict__ sigma) {
   pdl_begin();
@@ -298,8 +303,12 @@ __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __rest
     int dg[kOtS];
     ot_digits(v, sg, dg);
 #pragma unroll
-    for (int s = 0; s < kOtS; ++s)
-      out[((size_t)(s >> 1) * kOtN + n) * 64 + (s & 1) * 32 + k2] = (unsigned short)ot_bf16(dg[s]);
+    for (int s = 0; s < kOtS + 1; ++s) {
+      const int byte = 2 * ((s & 1) * 32 + k2);  // within the 128-byte row
+      const uint32_t off = (uint32_t)i * kOtBChunk + (uint32_t)(s >> 1) * kOtBSlab + sw128_offset(n & 15, byte >> 4) +
+                           (uint32_t)(byte & 15);
+      out[off >> 1] = s < kOtS ? (unsigned short)ot_bf16(dg[s]) : (unsigned short)0;
+    }
   }
   if (threadIdx.x == 0) *sigma = sg;
   pdl_trigger();
@@ -308,7 +317,7 @@ __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __rest
 struct OzTopArgs {
   const double2* seeds;  // Z of the level below (compact when that level is sharded)
   double2* xout;         // MODE 0: X of this level
-  const uint4* btab;     // the table's digit slabs (128 KiB)
+  const unsigned char* btab;  // the table's image, one 8 KiB chunk per column i
   const int* sigma;
   const double2* tw_lo;
   const double2* tw_hi;
@@ -327,23 +336,30 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  unsigned char* Bs = base;
-  unsigned char* As = base + kOtBBytes;
-  int4* twS = reinterpret_cast<int4*>(As + kOtABytes);  // [2][128][7] twiddles in Q61, split at bit 31
+  unsigned char* As = base;                     // [2] tiles' digits
+  unsigned char* Bs = base + 2 * kOtABytes;     // [kOtBStages] table chunks
+  int4* twS = reinterpret_cast<int4*>(Bs + kOtBStages * kOtBChunk);  // [2][128][7] twiddles in Q61, split at bit 31
   int* tauS = reinterpret_cast<int*>(twS + 2 * kOtRows * (kOtL - 1));  // [2][128]
-  __shared__ uint64_t a_full, a_empty, tw_empty[2], t_full[2], t_empty[2], sq_full, sq_empty, mma_done;
+  __shared__ uint64_t a_full[2], a_empty[2], tw_empty[2], b_full[kOtBStages], b_empty[kOtBStages], t_full[4],
+      t_empty[4], sq_full, sq_empty, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   __shared__ Partial sp[4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    mbar_init(&a_full, 2 * kOtRows);  // one arrival per producer item
-    mbar_init(&a_empty, 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&tw_empty[b], 16);  // every drain warp
+      mbar_init(&a_full[b], 2 * kOtRows);  // one arrival per producer item
+      mbar_init(&a_empty[b], 1);
+      mbar_init(&tw_empty[b], 16);         // every drain warp
+    }
+    for (int b = 0; b < kOtBStages; ++b) {
+      mbar_init(&b_full[b], 1);
+      mbar_init(&b_empty[b], 1);
+    }
+    for (int b = 0; b < 4; ++b) {
       mbar_init(&t_full[b], 1);
-      mbar_init(&t_empty[b], 8);    // the eight drain warps of the buffer's chunks
+      mbar_init(&t_empty[b], 4);  // the buffer's drain warp in each lane quarter
     }
     mbar_init(&sq_full, 12);
     mbar_init(&sq_empty, 4);
@@ -357,12 +373,6 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // the table's digit slabs into shared memory, swizzled (16-byte chunks)
-  for (int q = threadIdx.x; q < (int)(kOtBBytes / 16); q += kOtThreads) {
-    const int slab = q / (kOtN * 8), n = (q >> 3) % kOtN, c = q & 7;
-    *reinterpret_cast<uint4*>(Bs + slab * kOtSlabB + sw128_offset(n, c)) = __ldg(a.btab + q);
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -380,16 +390,14 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
     // pencil u >> 1; items u and u ^ 1 run in adjacent lanes of one round
     int it = 0;
     for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end; t += gridDim.x, ++it) {
-      const int tb = it & 1;
-      if (it >= 1 && !mbar_wait(&a_empty, (it - 1) & 1)) {
-        atomicExch(&fail, 1);
-        break;
-      }
-      if (it >= 2 && !mbar_wait(&tw_empty[tb], ((it >> 1) - 1) & 1)) {
+      const int tb = it & 1;  // digit, twiddle and scale buffers of this tile
+      if (it >= 2 && (!mbar_wait(&a_empty[tb], ((it >> 1) - 1) & 1) ||
+                      !mbar_wait(&tw_empty[tb], ((it >> 1) - 1) & 1))) {
         atomicExch(&fail, 1);
         break;
       }
       if (*vfail) break;
+      unsigned char* At = As + tb * kOtABytes;
       for (int u = threadIdx.x; u < 2 * kOtRows; u += kOtProducers) {
         const int p = u >> 1, half = u & 1;
         const int64_t j = t * kOtRows + p;
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
           ot_digit_pairs(z[2 * gg + 1].x, z[2 * gg + 1].y, tau, wb);
 #pragma unroll
           for (int s = 0; s < kOtS; ++s)
-            *reinterpret_cast<uint2*>(As + (s >> 1) * kOtSlabA + sw128_offset(p, (s & 1) * 4 + (g >> 1)) +
+            *reinterpret_cast<uint2*>(At + (s >> 1) * kOtSlabA + sw128_offset(p, (s & 1) * 4 + (g >> 1)) +
                                       (g & 1) * 8) = make_uint2(wa[s], wb[s]);
         }
         if (half == 0) {
@@ -432,57 +440,84 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
           tauS[tb * kOtRows + p] = tau + sigma - 30;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&a_full);
+        mbar_arrive(&a_full[tb]);
       }
     }
   } else if (warp == 3) {
     // ------------------------------------------------------------ MMA issuer
+    // Per tile, 16 chunks (one column i each) into the four tensor-memory
+    // buffers in turn; the table's chunk image streams through a ring of
+    // kOtBStages stages by bulk copies, kOtBStages - 2 chunks ahead (a stage
+    // is refilled once the MMAs of the chunk two back, its last reader, are done).
     if (lane == 0) {
-      const uint32_t idesc = make_idesc<kTcBF16, 32>();
-      const uint64_t a0 = sw128_desc(smem_u32(As)), b00 = sw128_desc(smem_u32(Bs));
-      int it = 0;
-      uint32_t g = 0;
+      const uint32_t idesc = make_idesc<kTcBF16, 16>();
+      const int64_t first = a.tile_begin + blockIdx.x;
+      const int64_t ntile = first < a.tile_end ? (a.tile_end - first + gridDim.x - 1) / gridDim.x : 0;
+      const int64_t total = ntile * kOtChunks;
+      int64_t issued = 0, g = 0;
       bool ok = true;
-      for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end && ok; t += gridDim.x, ++it) {
-        if (!mbar_wait(&a_full, it & 1) || *vfail) {
+      auto issue = [&](int64_t gq) {
+        const int st = (int)(gq % kOtBStages);
+        if (gq >= kOtBStages && !mbar_wait(&b_empty[st], (uint32_t)(((gq / kOtBStages) - 1) & 1))) return false;
+        mbar_expect_tx(&b_full[st], kOtBChunk);
+        bulk_load(Bs + st * kOtBChunk, a.btab + (size_t)(gq % kOtChunks) * kOtBChunk, kOtBChunk, &b_full[st]);
+        return true;
+      };
+      while (ok && issued < total && issued < kOtBStages - 2) {
+        ok = issue(issued);
+        issued += ok ? 1 : 0;
+      }
+      int it = 0;
+      for (int64_t t = first; t < a.tile_end && ok; t += gridDim.x, ++it) {
+        const int ab = it & 1;
+        if (!mbar_wait(&a_full[ab], (it >> 1) & 1) || *vfail) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t a0 = sw128_desc(smem_u32(As + ab * kOtABytes));
         for (int c = 0; c < kOtChunks; ++c, ++g) {
-          const int buf = g & 1;
-          if (g >= 2 && !mbar_wait(&t_empty[buf], ((g >> 1) - 1) & 1)) {
+          if (issued < total) {
+            if (!(ok = issue(issued))) break;
+            ++issued;
+          }
+          const int st = (int)(g % kOtBStages);
+          const int buf = c & 3;
+          if (!mbar_wait(&b_full[st], (uint32_t)((g / kOtBStages) & 1)) ||
+              (g >= 4 && !mbar_wait(&t_empty[buf], (uint32_t)(((g >> 2) - 1) & 1)))) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          ot_pairs<0, 0>(tmem + (uint32_t)buf * kOtBufCols, a0, b00 + (uint64_t)(c * (32 * 128 >> 4)), idesc);
+          ot_pairs<0, 0>(tmem + (uint32_t)buf * kOtBufCols, a0, sw128_desc(smem_u32(Bs + st * kOtBChunk)), idesc);
           umma_commit(&t_full[buf]);
+          umma_commit(&b_empty[st]);
         }
         if (!ok) break;
-        umma_commit(&a_empty);
+        umma_commit(&a_empty[ab]);
       }
       if (!ok) atomicExch(&fail, 1);
-      // every MMA issued has finished before tensor memory is released
+      // every table copy issued has landed and every MMA issued has finished
+      // before shared and tensor memory are released
+      for (int64_t gq = g; gq < issued; ++gq)
+        if (!mbar_wait(&b_full[gq % kOtBStages], (uint32_t)((gq / kOtBStages) & 1))) atomicExch(&fail, 1);
       umma_commit(&mma_done);
       if (!mbar_wait(&mma_done, 0)) atomicExch(&fail, 1);
     }
   } else {
     // ------------------------------------------------------------ drain
     const int q = warp & 3;          // tensor-memory lane quarter
-    const int k = (warp - 4) >> 2;   // 0 .. 3
-    const int h = k & 1;             // column i = 2 c + h of chunk c
-    const int par = k >> 1;          // the chunks c with c & 1 = par (tensor-memory buffer par)
+    const int k = (warp - 4) >> 2;   // 0 .. 3: the chunks (columns i) c = k mod 4, tensor-memory buffer k
     const int row = q * 32 + lane;   // pencil of this thread within the tile
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     double best = -1.0, wsum = 0.0, psum = 0.0;
     int64_t besty = INT64_MAX;
     int it = 0;
-    uint32_t uses = 0;  // fills of buffer par consumed so far
+    uint32_t uses = 0;  // fills of buffer k consumed so far
     bool ok = true;
     for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end && ok; t += gridDim.x, ++it) {
       const int tb = it & 1;
-      bool got = mbar_wait(&a_full, it & 1);  // this tile's twiddles and scales are written
+      bool got = mbar_wait(&a_full[tb], (it >> 1) & 1);  // this tile's twiddles and scales are written
       if (!__all_sync(0xffffffffu, got && !*vfail)) {
         ok = false;
         break;
@@ -494,23 +529,23 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       double acc[kOtL];
 #pragma unroll
       for (int y = 0; y < kOtL; ++y) acc[y] = 0.0;
-      for (int c = par; c < kOtChunks; c += 2, ++uses) {
-        got = mbar_wait(&t_full[par], uses & 1);
+      for (int c = k; c < kOtChunks; c += 4, ++uses) {
+        got = mbar_wait(&t_full[k], uses & 1);
         got = __all_sync(0xffffffffu, got && !*vfail) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!got) {
           ok = false;
           break;
         }
-        const uint32_t col = lane_base + (uint32_t)par * kOtBufCols + (uint32_t)(h * 16);
-        // T[m_b] (columns 2 m_b + c of this half) as 64-bit fixed point, four
+        const uint32_t col = lane_base + (uint32_t)k * kOtBufCols;
+        // T[m_b] (columns 2 m_b + c of the chunk) as 64-bit fixed point, four
         // values at a time (the seven weights' loads in flight together)
         long long x[16];
 #pragma unroll
         for (int grp = 0; grp < 4; ++grp) {
           uint32_t v[kOtS][4];
 #pragma unroll
-          for (int w = 0; w < kOtS; ++w) tmem_ld4_async(col + (uint32_t)(w * 32 + grp * 4), v[w]);
+          for (int w = 0; w < kOtS; ++w) tmem_ld4_async(col + (uint32_t)(w * 16 + grp * 4), v[w]);
           tmem_wait7x4(v);
 #pragma unroll
           for (int e = 0; e < 4; ++e)
@@ -518,13 +553,13 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&t_empty[par]);
+        if (lane == 0) mbar_arrive(&t_empty[k]);
         // twiddles w_N^(m_b y_a) (m_b >= 1), then the 8-point DFT over m_b
 #pragma unroll
         for (int m = 1; m < kOtL; ++m) ot_tw_fix(x[2 * m], x[2 * m + 1], tw[m - 1]);
         ot_dft8_fix(x);
         if (MODE == 0) {
-          const int i = 2 * c + h;
+          const int i = c;
           if (jt < a.npencils) {
 #pragma unroll
             for (int y = 0; y < kOtL; ++y)
@@ -650,7 +685,7 @@ int launch_oz_level(const Instance& in, char* ws, const LevelArgs<double2>& la, 
   OzTopArgs a{};
   a.seeds = la.seeds;
   a.xout = la.xout;
-  a.btab = reinterpret_cast<const uint4*>(btab);
+  a.btab = reinterpret_cast<const unsigned char*>(btab);
   a.sigma = sigma;
   a.tw_lo = la.tw_lo;
   a.tw_hi = la.tw_hi;
