@@ -42,10 +42,13 @@
 //               swizzled K-major, two digits per 128-byte row), two threads
 //               per pencil (eight complex values each); the pencils'
 //               twiddles w_N^(m_b y_a) and scales (two buffers);
-//   warp 3      tensor memory, and lane 0 issues the MMAs: per chunk of two
-//               columns i (32 table rows), 28 pairs x 2 K-steps of
-//               M = 128, N = 32 into seven weight accumulators (224 columns;
-//               two chunk buffers, even chunks in one, odd in the other);
+//   warp 3      tensor memory, and lane 0 issues the MMAs and the table's
+//               copies: per chunk of two columns i (32 table rows), 28 pairs
+//               x 2 K-steps of M = 128, N = 32 into seven weight accumulators
+//               (224 columns; two chunk buffers, even chunks in one, odd in
+//               the other); the digits of two tiles in shared memory (the
+//               producers run a tile ahead) and the table's chunk images
+//               streamed from L2 through a four-stage ring (bulk copies);
 //   warps 4-19  drain: four warps per tensor-memory lane quarter (four per
 //               SM sub-partition, enough to cover the integer epilogue's
 //               latencies), warp k takes column 2 c + (k & 1) of the chunks
@@ -68,15 +71,15 @@ namespace {
 constexpr int kOtL = 8, kOtD = 16, kOtS = 7;
 constexpr int kOtRows = 128;                   // pencils per tile (MMA M)
 constexpr int kOtN = 2 * kOtD * kOtL;          // 256 table rows
-constexpr int kOtChunks = kOtD;                // one column i (16 table rows) per chunk
+constexpr int kOtChunks = kOtD / 2;            // two columns i (32 table rows) per chunk
 constexpr int kOtThreads = 640;
 constexpr int kOtProducers = 96;
 constexpr uint32_t kOtSlabA = kOtRows * 128;   // digits [2q | 2q+1] of 128 pencils, 16 KiB
-constexpr uint32_t kOtBSlab = 16 * 128;        // digits [2q | 2q+1] of one chunk's 16 rows, 2 KiB
-constexpr uint32_t kOtBChunk = 4 * kOtBSlab;   // one chunk's seven digits, 8 KiB
-constexpr int kOtBStages = 6;                  // ring of table chunks
-constexpr uint32_t kOtBufCols = kOtS * 16;     // one chunk's seven weight accumulators (four buffers)
-constexpr uint32_t kOtSqCol = 4 * kOtBufCols;  // columns 448 .. 495: the hand-over of the partial sums
+constexpr uint32_t kOtBSlab = 32 * 128;        // digits [2q | 2q+1] of one chunk's 32 rows, 4 KiB
+constexpr uint32_t kOtBChunk = 4 * kOtBSlab;   // one chunk's seven digits, 16 KiB
+constexpr int kOtBStages = 4;                  // ring of table chunks
+constexpr uint32_t kOtBufCols = kOtS * 32;     // one chunk's seven weight accumulators (two buffers)
+constexpr uint32_t kOtSqCol = 2 * kOtBufCols;  // columns 448 .. 495: the hand-over of the partial sums
 constexpr size_t kOtBBytes = (size_t)kOtChunks * kOtBChunk;  // the table's image in global memory, 128 KiB
 constexpr size_t kOtABytes = 4 * (size_t)kOtSlabA;           // one tile's digits (two buffers)
 constexpr size_t kOtTwBytes = (size_t)kOtRows * (kOtL - 1) * sizeof(int4);
@@ -255,7 +258,7 @@ __device__ __forceinline__ double2 ot_cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-// The MMAs of one chunk: pair (S, T) into weight S + T (16 columns each), two
+// The MMAs of one chunk: pair (S, T) into weight S + T (32 columns each), two
 // K = 16 steps of the 32-wide digit (digit s sits in half s & 1 of slab s >> 1).
 template <int S, int T>
 __device__ __forceinline__ void ot_pairs(uint32_t d0, uint64_t a0, uint64_t b0, uint32_t idesc) {
@@ -263,7 +266,7 @@ __device__ __forceinline__ void ot_pairs(uint32_t d0, uint64_t a0, uint64_t b0, 
     if constexpr (S + T < kOtS) {
       const uint64_t ad = a0 + (uint64_t)((S >> 1) * (kOtSlabA >> 4) + (S & 1) * 4);
       const uint64_t bd = b0 + (uint64_t)((T >> 1) * (kOtBSlab >> 4) + (T & 1) * 4);
-      const uint32_t d = d0 + (uint32_t)((S + T) * 16);
+      const uint32_t d = d0 + (uint32_t)((S + T) * 32);
       umma_k<kTcBF16>(d, ad, bd, idesc, S == 0 ? 0u : 1u);
       umma_k<kTcBF16>(d, ad + 2, bd + 2, idesc, 1u);
       ot_pairs<S, T + 1>(d0, a0, b0, idesc);
@@ -275,8 +278,8 @@ __device__ __forceinline__ void ot_pairs(uint32_t d0, uint64_t a0, uint64_t b0, 
 
 // The table's digits: rows n = 16 i + 2 m_b + c, K index k2 = 2 k + c'
 // (value Re M, -Im M, Im M, Re M for (c, c') = (0,0), (0,1), (1,0), (1,1)),
-// as the shared-memory image of each chunk (column i): [chunk i][slab q]
-// [row n mod 16][128 bytes, 128-byte swizzled], digit 2q in the first 64
+// as the shared-memory image of each chunk (columns 2 c, 2 c + 1): [chunk c]
+// [slab q][row n mod 32][128 bytes, 128-byte swizzled], digit 2q in the first 64
 // bytes of a row and 2q + 1 in the second (the unused digit 7 zero); sigma
 // (|M| < 2^sigma) after the image. One CTA.
 __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __restrict__ tab,
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __rest
 #pragma unroll
     for (int s = 0; s < kOtS + 1; ++s) {
       const int byte = 2 * ((s & 1) * 32 + k2);  // within the 128-byte row
-      const uint32_t off = (uint32_t)i * kOtBChunk + (uint32_t)(s >> 1) * kOtBSlab + sw128_offset(n & 15, byte >> 4) +
+      const uint32_t off = (uint32_t)(i >> 1) * kOtBChunk + (uint32_t)(s >> 1) * kOtBSlab + sw128_offset(n & 31, byte >> 4) +
                            (uint32_t)(byte & 15);
       out[off >> 1] = s < kOtS ? (unsigned short)ot_bf16(dg[s]) : (unsigned short)0;
     }
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(256) oz_top_table_kernel(const double2* __rest
 struct OzTopArgs {
   const double2* seeds;  // Z of the level below (compact when that level is sharded)
   double2* xout;         // MODE 0: X of this level
-  const unsigned char* btab;  // the table's image, one 8 KiB chunk per column i
+  const unsigned char* btab;  // the table's image, one 16 KiB chunk per two columns i
   const int* sigma;
   const double2* tw_lo;
   const double2* tw_hi;
@@ -340,8 +343,8 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
   unsigned char* Bs = base + 2 * kOtABytes;     // [kOtBStages] table chunks
   int4* twS = reinterpret_cast<int4*>(Bs + kOtBStages * kOtBChunk);  // [2][128][7] twiddles in Q61, split at bit 31
   int* tauS = reinterpret_cast<int*>(twS + 2 * kOtRows * (kOtL - 1));  // [2][128]
-  __shared__ uint64_t a_full[2], a_empty[2], tw_empty[2], b_full[kOtBStages], b_empty[kOtBStages], t_full[4],
-      t_empty[4], sq_full, sq_empty, mma_done;
+  __shared__ uint64_t a_full[2], a_empty[2], tw_empty[2], b_full[kOtBStages], b_empty[kOtBStages], t_full[2],
+      t_empty[2], sq_full, sq_empty, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   __shared__ Partial sp[4];
@@ -357,9 +360,9 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       mbar_init(&b_full[b], 1);
       mbar_init(&b_empty[b], 1);
     }
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&t_full[b], 1);
-      mbar_init(&t_empty[b], 4);  // the buffer's drain warp in each lane quarter
+      mbar_init(&t_empty[b], 8);  // the drain warps of the buffer's chunks, two per lane quarter
     }
     mbar_init(&sq_full, 12);
     mbar_init(&sq_empty, 4);
@@ -445,12 +448,12 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
     }
   } else if (warp == 3) {
     // ------------------------------------------------------------ MMA issuer
-    // Per tile, 16 chunks (one column i each) into the four tensor-memory
+    // Per tile, 8 chunks (two columns i each) into the two tensor-memory
     // buffers in turn; the table's chunk image streams through a ring of
     // kOtBStages stages by bulk copies, kOtBStages - 2 chunks ahead (a stage
     // is refilled once the MMAs of the chunk two back, its last reader, are done).
     if (lane == 0) {
-      const uint32_t idesc = make_idesc<kTcBF16, 16>();
+      const uint32_t idesc = make_idesc<kTcBF16, 32>();
       const int64_t first = a.tile_begin + blockIdx.x;
       const int64_t ntile = first < a.tile_end ? (a.tile_end - first + gridDim.x - 1) / gridDim.x : 0;
       const int64_t total = ntile * kOtChunks;
@@ -482,9 +485,9 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
             ++issued;
           }
           const int st = (int)(g % kOtBStages);
-          const int buf = c & 3;
+          const int buf = c & 1;
           if (!mbar_wait(&b_full[st], (uint32_t)((g / kOtBStages) & 1)) ||
-              (g >= 4 && !mbar_wait(&t_empty[buf], (uint32_t)(((g >> 2) - 1) & 1)))) {
+              (g >= 2 && !mbar_wait(&t_empty[buf], (uint32_t)(((g >> 1) - 1) & 1)))) {
             ok = false;
             break;
           }
@@ -507,13 +510,15 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
   } else {
     // ------------------------------------------------------------ drain
     const int q = warp & 3;          // tensor-memory lane quarter
-    const int k = (warp - 4) >> 2;   // 0 .. 3: the chunks (columns i) c = k mod 4, tensor-memory buffer k
+    const int k = (warp - 4) >> 2;   // 0 .. 3
+    const int h = k & 1;             // column i = 2 c + h of chunk c
+    const int par = k >> 1;          // the chunks c with c & 1 = par (tensor-memory buffer par)
     const int row = q * 32 + lane;   // pencil of this thread within the tile
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     double best = -1.0, wsum = 0.0, psum = 0.0;
     int64_t besty = INT64_MAX;
     int it = 0;
-    uint32_t uses = 0;  // fills of buffer k consumed so far
+    uint32_t uses = 0;  // fills of buffer par consumed so far
     bool ok = true;
     for (int64_t t = a.tile_begin + blockIdx.x; t < a.tile_end && ok; t += gridDim.x, ++it) {
       const int tb = it & 1;
@@ -529,23 +534,23 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
       double acc[kOtL];
 #pragma unroll
       for (int y = 0; y < kOtL; ++y) acc[y] = 0.0;
-      for (int c = k; c < kOtChunks; c += 4, ++uses) {
-        got = mbar_wait(&t_full[k], uses & 1);
+      for (int c = par; c < kOtChunks; c += 2, ++uses) {
+        got = mbar_wait(&t_full[par], uses & 1);
         got = __all_sync(0xffffffffu, got && !*vfail) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!got) {
           ok = false;
           break;
         }
-        const uint32_t col = lane_base + (uint32_t)k * kOtBufCols;
-        // T[m_b] (columns 2 m_b + c of the chunk) as 64-bit fixed point, four
+        const uint32_t col = lane_base + (uint32_t)par * kOtBufCols + (uint32_t)(h * 16);
+        // T[m_b] (columns 2 m_b + c of this half) as 64-bit fixed point, four
         // values at a time (the seven weights' loads in flight together)
         long long x[16];
 #pragma unroll
         for (int grp = 0; grp < 4; ++grp) {
           uint32_t v[kOtS][4];
 #pragma unroll
-          for (int w = 0; w < kOtS; ++w) tmem_ld4_async(col + (uint32_t)(w * 16 + grp * 4), v[w]);
+          for (int w = 0; w < kOtS; ++w) tmem_ld4_async(col + (uint32_t)(w * 32 + grp * 4), v[w]);
           tmem_wait7x4(v);
 #pragma unroll
           for (int e = 0; e < 4; ++e)
@@ -553,13 +558,13 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&t_empty[k]);
+        if (lane == 0) mbar_arrive(&t_empty[par]);
         // twiddles w_N^(m_b y_a) (m_b >= 1), then the 8-point DFT over m_b
 #pragma unroll
         for (int m = 1; m < kOtL; ++m) ot_tw_fix(x[2 * m], x[2 * m + 1], tw[m - 1]);
         ot_dft8_fix(x);
         if (MODE == 0) {
-          const int i = c;
+          const int i = 2 * c + h;
           if (jt < a.npencils) {
 #pragma unroll
             for (int y = 0; y < kOtL; ++y)
