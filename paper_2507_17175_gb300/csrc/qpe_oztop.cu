@@ -31,11 +31,12 @@
 // int32 halves so that every partial product is one 32 x 32 -> 64-bit
 // multiply-add; at most 3 units off), runs the 8-point DFT on the integers
 // (|X| < 8 sqrt(2) 2^57 < 2^61; the factor cos(pi / 4) also in Q61) and turns
-// X into FP64 by integer operations on the bits (the unit's power of two goes
-// into the exponent; rounded half away from zero). The fixed point's
-// truncations are a few units, 2^-55 of the pencil's bound |T| < 2^(tau +
-// sigma + 5), below the contraction's own error. |X|^2 and the readout run in
-// FP64; a lower level (MODE 0) stores X in FP64.
+// X into FP64 (the hardware conversion, rounded to nearest; the unit's power
+// of two goes into the exponent bits, or, for |X|^2, into the histogram's
+// scale once per tile). The fixed point's truncations are a few units, 2^-55
+// of the pencil's bound |T| < 2^(tau + sigma + 5), below the contraction's
+// own error. |X|^2 and the readout run in FP64; a lower level (MODE 0) stores
+// X in FP64.
 //
 // Roles (640 threads, one CTA per SM, persistent over the tiles):
 //   warps 0-2   producers: Z rows -> digit tiles (shared memory, 128-byte
@@ -87,40 +88,36 @@ constexpr size_t kOtSmem =
     2 * kOtABytes + kOtBStages * (size_t)kOtBChunk + 2 * kOtTwBytes + 2 * kOtRows * sizeof(int) + 1024;
 static_assert(kOtSmem <= 227 * 1024, "shared memory of the FP64 top level");
 
-// v 2^e2 in FP64 for a signed integer |v| < 2^63, by integer operations on
-// the bits: the leading one's position sets the exponent, the 53 bits from it
-// the significand, rounded half away from zero on the magnitude (a carry runs
-// into the exponent). v = 0, and results below 2^-1022, give 0.
-__device__ __forceinline__ double ot_fix_to_f64(long long v, int e2) {
-  const unsigned long long sg = (unsigned long long)(v >> 63);  // 0 or all ones
-  const unsigned long long a = ((unsigned long long)v ^ sg) - sg;
-  const int lz = __clzll((long long)a);
-  const unsigned long long n = a << (lz & 63);  // leading one at bit 63
-  const unsigned long long m = (n >> 11) + ((n >> 10) & 1ull);
-  const int eb = 1086 - lz + e2;  // biased exponent of a 2^e2
-  // m has its leading one at bit 52 (or is 2^53 after a carry): adding it to
-  // (eb - 1) << 52 gives the bits of the result
-  const unsigned long long bits = ((unsigned long long)(eb - 1) << 52) + m;
-  return (a == 0 || eb <= 0) ? 0.0 : __longlong_as_double((long long)(bits | (sg << 63)));
+// v 2^e for an FP64 v that is zero or normal, by adding e to the exponent
+// field; results below 2^-1022 flush to 0
+__device__ __forceinline__ double ot_scale2(double v, int e) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ff);
+  return (E == 0 || E + e <= 0) ? 0.0 : __longlong_as_double(b + ((long long)e << 52));
 }
 
-// A weight accumulator (an exact integer |acc| < 2^22 in FP32) as an int:
-// adding 1.5 2^23 places acc + 2^22 in the low mantissa bits, exactly.
-__device__ __forceinline__ int ot_acc(uint32_t u) {
-  return (int)__float_as_uint(__fadd_rn(__uint_as_float(u), 12582912.0f)) - 0x4B400000;
+// A weight accumulator (an exact integer |acc| < 2^22 in FP32) plus 1.5 2^23
+// in FP32 is exact and has the bits acc + M, M = 0x4B400000.
+__device__ __forceinline__ uint32_t ot_acc_bits(uint32_t u) {
+  return __float_as_uint(__fadd_rn(__uint_as_float(u), 12582912.0f));
 }
 
 // The drain's fixed point W = floor(E / 2^10) of one T component from its
-// seven weight sums, E = sum_w a_w 2^(8 (6 - w)), T = 2^(tau + sigma - 62) E.
+// seven weight sums, E = sum_w acc_w 2^(8 (6 - w)), T = 2^(tau + sigma - 62) E.
+// With b_w = acc_w + M, the low part acc_5 2^8 + acc_6 = b_5 2^8 + b_6 - 257 M
+// (exact in int32), and the rest sum_(w<5) b_w 2^(8 (6 - w) - 10) minus
+// M sum_(w<5) 2^(8 (6 - w) - 10), modulo 2^64 (W itself fits).
 __device__ __forceinline__ long long ot_weights_fix(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, uint32_t u4,
                                                     uint32_t u5, uint32_t u6) {
-  long long w = (long long)((ot_acc(u5) * 256 + ot_acc(u6)) >> 10);
-  w += (long long)ot_acc(u4) * 64;
-  w += (long long)ot_acc(u3) * 16384;
-  w += (long long)ot_acc(u2) * 4194304;
-  w += (long long)ot_acc(u1) * 1073741824;
-  w += (long long)(ot_acc(u0) * 64) * 4294967296LL;
-  return w;
+  constexpr unsigned long long kMW = 0xe2e2e2e2d0000000ull;  // M (2^38 + 2^30 + 2^22 + 2^14 + 2^6) mod 2^64
+  const int r = (int)(ot_acc_bits(u5) * 256u + ot_acc_bits(u6) - 0x8b400000u) >> 10;  // 257 M mod 2^32
+  unsigned long long w = (unsigned long long)(long long)r - kMW;
+  w += (unsigned long long)ot_acc_bits(u4) * 64u;
+  w += (unsigned long long)ot_acc_bits(u3) * 16384u;
+  w += (unsigned long long)ot_acc_bits(u2) * 4194304u;
+  w += (unsigned long long)ot_acc_bits(u1) * 1073741824u;
+  w += (unsigned long long)(ot_acc_bits(u0) * 64u) << 32;
+  return (long long)w;
 }
 
 // (wr + i wi) (qr + i qi) 2^-61 for a twiddle in Q61 (q = round(w 2^61)),
@@ -569,13 +566,13 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
 #pragma unroll
             for (int y = 0; y < kOtL; ++y)
               a.xout[((jt + ((int64_t)y << lna)) << 4) + i] =
-                  make_double2(ot_fix_to_f64(x[2 * y], e2), ot_fix_to_f64(x[2 * y + 1], e2));
+                  make_double2(ot_scale2(__ll2double_rn(x[2 * y]), e2), ot_scale2(__ll2double_rn(x[2 * y + 1]), e2));
           }
         } else {
 #pragma unroll
           for (int y = 0; y < kOtL; ++y) {
-            const double re = ot_fix_to_f64(x[2 * y], e2), im = ot_fix_to_f64(x[2 * y + 1], e2);
-            acc[y] = fma(re, re, fma(im, im, acc[y]));
+            const double re = __ll2double_rn(x[2 * y]), im = __ll2double_rn(x[2 * y + 1]);
+            acc[y] = fma(re, re, fma(im, im, acc[y]));  // in units of 2^(2 e2)
           }
         }
       }
@@ -620,7 +617,7 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&sq_empty);
-        const double f = a.pscale;  // 1 / N^2
+        const double f = a.pscale * ldexp(1.0, e2) * ldexp(1.0, e2);  // the units and 1 / N^2
         const int64_t j = jt;
         if (j < a.npencils) {
 #pragma unroll

@@ -25,8 +25,8 @@ The FP64 level (d = 16, K = 32 per pencil row, one scale for the table):
     floor and stays below 2^57 + 2;
   * T against the extended-precision contraction within the FP64 dot
     product's bound; the Q61 twiddle products (split at bit 31) below 2^58,
-    the integer 8-point DFT below 2^61, and X converted to FP64 (rounded half
-    away from zero) against numpy's FFT of the exact T within a few units of
+    the integer 8-point DFT below 2^61, and X converted to FP64 (rounded to
+    nearest) against numpy's FFT of the exact T within a few units of
     rounding, |X|^2 likewise;
   * a wrong weight shift, a sign slip in the table's real embedding, in the
     twiddle's cross term or in the DFT's rotation fails.
@@ -225,21 +225,10 @@ def dft8_fix(x, plant=None):
 
 
 def fix_to_f64(v, e2):
-    """v 2^e2 with the significand rounded half away from zero to 53 bits;
-    below 2^-1022: 0."""
-    a = abs(v)
-    if a == 0:
-        return 0.0
-    nb = a.bit_length()
-    if nb > 53:
-        sh = nb - 53
-        m, ex = (a >> sh) + ((a >> (sh - 1)) & 1), sh
-    else:
-        m, ex = a, 0
-    if nb + e2 - 1 < -1022:
-        return 0.0
-    r = float(np.ldexp(float(m), ex + e2))
-    return r if v > 0 else -r
+    """v 2^e2 in FP64: the conversion rounded to nearest (even), the power of
+    two exact; below 2^-1022: 0."""
+    r = float(np.ldexp(float(v), e2))
+    return 0.0 if abs(r) < 2.0 ** -1022 else r
 
 
 def level_fix(Z, M, ya, N, plant=None):
@@ -280,6 +269,18 @@ def level_fix(Z, M, ya, N, plant=None):
     E = sum(acc[w].astype(object) * (1 << (8 * (6 - w))) for w in range(S))
     if plant is None:
         assert np.all(W.astype(object) == E // 1024)        # floor(E / 2^10)
+        # the kernel's form: magic bits b = acc + M, the offsets folded into
+        # one constant modulo 2^64
+        b = [(a + MAGIC).astype(np.uint64) for a in acc]
+        low = ((b[5] * 256 + b[6] - 0x8B400000) & 0xFFFFFFFF).astype(np.int64)
+        low = np.where(low >= 2 ** 31, low - 2 ** 32, low) >> 10
+        kmw = (MAGIC * sum(1 << s_ for s_ in (38, 30, 22, 14, 6))) % 2 ** 64
+        assert kmw == 0xE2E2E2E2D0000000
+        with np.errstate(over="ignore"):
+            Wk = low.astype(np.uint64) - np.uint64(kmw)
+            for w_, sh_ in zip(range(5), (38, 30, 22, 14, 6)):
+                Wk = Wk + b[w_] * np.uint64(1 << sh_)
+        assert np.array_equal(Wk.view(np.int64), W)
     assert np.abs(W).max() < 2 ** 57 + 2
     T = np.ldexp(W.astype(np.float64), (tau + sig - 52)[:, None]).reshape(Pn, 16, 8, 2)
     T = (T[..., 0] + 1j * T[..., 1]).transpose(0, 2, 1)     # [p][m][i] (exact up to FP64 rounding of W)
@@ -336,24 +337,6 @@ def test_fp64_level_contraction_and_epilogue():
     href = (np.abs(Xref) ** 2).sum(2)
     assert np.all(np.abs(hist - href) <= 256 * U64 * href.max(axis=1, keepdims=True) + 1e-300)
     assert np.all(hist[5] == 0.0)
-
-
-def test_fp64_level_fix_to_f64_rounding():
-    """The integer-to-FP64 conversion: exact below 2^53, half away from zero
-    above, a carry into the exponent, the unit's power of two, flush below
-    2^-1022."""
-    assert fix_to_f64(12345, -3) == 12345 / 8
-    assert fix_to_f64(-(2 ** 53 + 1), 0) == -float(2 ** 53 + 2)     # half: away from zero
-    assert fix_to_f64(2 ** 54 + 1, 0) == float(2 ** 54)
-    assert fix_to_f64(2 ** 60 - 1, -60) == 1.0                       # carry into the exponent
-    assert fix_to_f64(3, -1025) == 0.0 and fix_to_f64(1, -1022) == 2.0 ** -1022
-    import math
-    from fractions import Fraction
-    rng = np.random.default_rng(1)
-    for v in rng.integers(-(2 ** 62), 2 ** 62, 200):
-        v = int(v)
-        r = fix_to_f64(v, -40)
-        assert abs(Fraction(r) - Fraction(v, 2 ** 40)) <= Fraction(math.ulp(r)) / 2
 
 
 @pytest.mark.parametrize("plant", ["group", "sign", "tw_sign", "rot"])
