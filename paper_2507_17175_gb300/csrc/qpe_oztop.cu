@@ -426,18 +426,18 @@ __global__ void __launch_bounds__(kOtThreads, 1) level_oz_kernel(OzTopArgs a) {
             *reinterpret_cast<uint2*>(At + (s >> 1) * kOtSlabA + sw128_offset(p, (s & 1) * 4 + (g >> 1)) +
                                       (g & 1) * 8) = make_uint2(wa[s], wb[s]);
         }
-        if (half == 0) {
+        {  // the twiddles w_N^(m_b y_a): m_b = 1 .. 4 by half 0 (with the scale), 5 .. 7 by half 1
           const int64_t ya = a.rk + (j << a.sh);
           int4* tw = twS + (tb * kOtRows + p) * (kOtL - 1);
-#pragma unroll
-          for (int m = 1; m < kOtL; ++m) {
+          const int m0 = half == 0 ? 1 : 5, m1 = half == 0 ? 5 : kOtL;
+          for (int m = m0; m < m1; ++m) {
             const int64_t ex = (((int64_t)m * ya) & lvl_mask) << lvl_shift;
             const double2 w = ot_cmul(__ldg(a.tw_lo + (ex & tw_mask)), __ldg(a.tw_hi + (ex >> a.htw)));
             const long long qr = ot_fixed(w.x, -6), qi = ot_fixed(w.y, -6);  // round(w 2^61)
             tw[m - 1] =
                 make_int4((int)(qr >> 31), (int)(qr & 0x7fffffff), (int)(qi >> 31), (int)(qi & 0x7fffffff));
           }
-          tauS[tb * kOtRows + p] = tau + sigma - 30;
+          if (half == 0) tauS[tb * kOtRows + p] = tau + sigma - 30;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&a_full[tb]);
