@@ -472,7 +472,78 @@ __device__ __forceinline__ void reduce_block(const C* __restrict__ X, double* __
   // histogram stores), reading the row at y's digit-reversed position (whole
   // 32-byte sectors); every lane runs the readout
   const bool per_y = d * (int)sizeof(C) <= 64;
-  if (per_y) {
+  // Blocked digit reversal (at least two digits, the lowest of y >= 5 bits):
+  // a tile is the outcomes y sharing their middle bits, 32 consecutive values
+  // of y's lowest bits times K values of its highest digit. The rows are read
+  // as K consecutive positions (y's highest digit is the position's lowest)
+  // for each of the 32, |X|^2 goes through shared memory, and the bins are
+  // written as 32 consecutive y for each of the K.
+  const int lb = g.count >= 2 ? g.logr[g.count - 1] : 0;
+  const bool blocked = per_y && g.count >= 2 && g.logr[0] >= 5 && blockDim.x == 256;
+  if (blocked) {
+    __shared__ double tile[32 * 129];
+    float* tile_f = reinterpret_cast<float*>(tile);
+    const int K = lb < 7 ? (1 << lb) : 128;
+    const int kc_count = (1 << lb) / K;
+    const int mid_bits = n - 5 - lb;
+    const int64_t ntiles = (int64_t(kc_count)) << mid_bits;
+    const int shift_hi = n - lb;
+    for (int64_t t = bidx; t < ntiles; t += nblk) {
+      const int kc = (int)(t % kc_count);
+      const int64_t mbits = t / kc_count;
+      const int64_t ybase = (mbits << 5);
+      // reads: k fastest across the threads (consecutive positions)
+      for (int e = threadIdx.x; e < 32 * K; e += 256) {
+        const int k = e % K, ylo = e / K;
+        const int64_t y = ybase + ylo + (int64_t(kc * K + k) << shift_hi);
+        const C* row = X + (y_to_pos(g, n, y) << logd);
+        if constexpr (sizeof(C) == 8) {
+          float f = 0.f;
+          for (int q = 0; q < d; ++q) {
+            const C v = __ldg(row + q);
+            f = fmaf(v.x, v.x, fmaf(v.y, v.y, f));
+          }
+          tile_f[ylo * 129 + k] = f * (float)scale;  // scale is a power of two
+        } else {
+          double acc = 0.0;
+          for (int q = 0; q < d; ++q) {
+            const C v = __ldg(row + q);
+            acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+          }
+          tile[ylo * 129 + k] = acc * scale;
+        }
+      }
+      __syncthreads();
+      // writes: 32 consecutive y across the threads
+      for (int e = threadIdx.x; e < 32 * K; e += 256) {
+        const int ylo = e & 31, k = e >> 5;
+        const int64_t y = ybase + ylo + (int64_t(kc * K + k) << shift_hi);
+        if constexpr (sizeof(C) == 8) {
+          const float v = tile_f[ylo * 129 + k];
+          hist[y] = widen_nonneg(v);
+          if (v > best_f || (v == best_f && y < by)) {
+            best_f = v;
+            by = y;
+          }
+          float t1 = v * (float)y - wcomp_f;
+          float t2 = wsum_f + t1;
+          wcomp_f = (t2 - wsum_f) - t1;
+          wsum_f = t2;
+          t1 = v - pcomp_f;
+          t2 = psum_f + t1;
+          pcomp_f = (t2 - psum_f) - t1;
+          psum_f = t2;
+        } else {
+          const double v = tile[ylo * 129 + k];
+          hist[y] = v;
+          better(best, by, v, y);
+          wsum += v * (double)y;
+          psum += v;
+        }
+      }
+      __syncthreads();  // the tile is reused
+    }
+  } else if (per_y) {
     const int64_t tstep = nblk * blockDim.x;
     for (int64_t y = bidx * blockDim.x + threadIdx.x; y < N; y += tstep) {
       const C* row = X + (y_to_pos(g, n, y) << logd);
