@@ -171,6 +171,32 @@ def test_fp64_level_tc_plans(q):
         q.LIB.qpe_destroy(h)
 
 
+def test_fp64_level_tc_batched_workspace(q):
+    """Batched FP64 plans with QPE_FLAG_LEVEL_TC: every doubling level of at
+    least 128 rows of the d >= 256 instances is one grouped digit-product
+    round; the rounds share one row-digit buffer sized by the largest round
+    (here level 11 of the (8, 12) instance: 7 digit planes of 2^11 rows x 512
+    bf16), besides each qualifying instance's squaring digits. Shapes with no
+    such level keep the workspace unchanged."""
+    shapes = [(8, 12), (9, 10), (3, 8), (10, 7)]
+    st, w0, h = q.plan_batched_workspace(shapes, q.FP64, 0)
+    assert st == q.OK
+    q.LIB.qpe_destroy(h)
+    st, w1, h = q.plan_batched_workspace(shapes, q.FP64, q.FLAG_LEVEL_TC)
+    assert st == q.OK
+    q.LIB.qpe_destroy(h)
+    assert w1 - w0 >= 7 * (1 << 11) * 512 * 2
+    # the round buffer is shared: far below the sum over every level and instance
+    per_level = sum(7 * (1 << j) * 2 * (1 << a) * 2 for a, b in shapes if a >= 8 for j in range(7, b) if b >= 8)
+    assert w1 - w0 < per_level + 64 * 2 ** 20
+    for small in ([(3, 8), (7, 12)], [(8, 7), (9, 7)]):
+        st, a0, h = q.plan_batched_workspace(small, q.FP64, 0)
+        q.LIB.qpe_destroy(h)
+        st, a1, h = q.plan_batched_workspace(small, q.FP64, q.FLAG_LEVEL_TC)
+        q.LIB.qpe_destroy(h)
+        assert st == q.OK and a1 == a0, small
+
+
 def test_bf16x3_is_refused_everywhere(q):
     """bf16 hi/lo splits (~16 bits) cannot keep the histogram's L1 error within
     1e-6 of FP64, so no plan accepts QPE_C64_BF16X3."""
