@@ -50,12 +50,44 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-def csrc_hash() -> str:
+# the sources that make up each recorded kernel (its translation unit and the
+# headers it includes); a traffic record holds while their code is unchanged
+KERNEL_SOURCES = {
+    "level_oz_top_c5_fp64": ["paper_2507_17175_gb300/csrc/qpe_oztop.cu", "paper_2507_17175_gb300/csrc/qpe_internal.cuh",
+                             "paper_2507_17175_gb300/csrc/qpe_tcgen05.cuh", "include/qpe.h"],
+}
+
+
+def _code_only(text: str) -> str:
+    """C / C++ source without its comments (string literals kept as they are);
+    csrc_hash also drops blank lines and trailing blanks."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
+def csrc_hash(stage: str = "level_oz_top_c5_fp64") -> str:
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2507_17175_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for rel in KERNEL_SOURCES[stage]:
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+            code = "\n".join(ln.rstrip() for ln in _code_only(fh.read()).splitlines() if ln.strip())
+            h.update(rel.encode() + code.encode())
     return h.hexdigest()[:16]
 
 
@@ -65,7 +97,7 @@ def recorded_traffic(stage: str):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    cur = csrc_hash()
+    cur = csrc_hash(stage) if stage in KERNEL_SOURCES else None
     with open(p) as f:
         for line in f:
             parts = line.split()

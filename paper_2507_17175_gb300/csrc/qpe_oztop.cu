@@ -51,8 +51,8 @@
 //               producers run a tile ahead) and the table's chunk images
 //               streamed from L2 through a four-stage ring (bulk copies);
 //   warps 4-19  drain: four warps per tensor-memory lane quarter (four per
-//               SM sub-partition, enough to cover the integer epilogue's
-//               latencies), warp k takes column 2 c + (k & 1) of the chunks
+//               SM sub-partition, for the integer epilogue's latencies),
+//               warp k takes column 2 c + (k & 1) of the chunks
 //               c with c & 1 = k >> 1; weights -> fixed point, twiddle, DFT,
 //               FP64, then |X|^2 (the four warps' sums meet through tensor
 //               memory columns 448-495) or the store of X.
@@ -192,7 +192,8 @@ __device__ __forceinline__ int ot_scale_exp(int emax) {
   return t < -960 ? -960 : t;
 }
 
-// round(x 2^(55 - t)) for |x| < 2^t by integer operations on x's bits (x =
+// round(x 2^(55 - t)) for |x| 2^(55 - t) < 2^62 (digits: |x| < 2^t; the Q61
+// twiddles: t = -6, |x| <= 1) by integer operations on x's bits (x =
 // M 2^(E - 1075), M the 53-bit significand; halves round away from zero);
 // zero and subnormal x give 0
 __device__ __forceinline__ long long ot_fixed(double x, int t) {
@@ -200,7 +201,7 @@ __device__ __forceinline__ long long ot_fixed(double x, int t) {
   const int E = (int)((b >> 52) & 0x7ff);
   if (E == 0) return 0;
   const long long M = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
-  const int k = E - 1020 - t;  // x 2^(55 - t) = M 2^k, k <= 2
+  const int k = E - 1020 - t;  // x 2^(55 - t) = M 2^k (k <= 2 for |x| < 2^t, <= 9 for the twiddles)
   long long F = 0;
   if (k >= 0)
     F = M << k;
