@@ -130,11 +130,14 @@ typedef enum {
                                  /* nmat = 4 the fused schedule's 8-point     */
                                  /* levels of >= 128 pencils, the top level   */
                                  /* included (QPE_INFO_TC_TOP_LEVEL tells;    */
-                                 /* twiddles, DFT, |X|^2, readout in FP64);   */
-                                 /* with nmat >= 8 the plain schedule's       */
-                                 /* doubling levels of >= 128 rows (single-   */
-                                 /* instance and sharded plans); ignored      */
-                                 /* elsewhere                                 */
+                                 /* twiddles and DFT in 64-bit fixed point,   */
+                                 /* |X|^2 and readout in FP64; single-        */
+                                 /* instance and sharded plans); with         */
+                                 /* nmat >= 8 the plain schedule's doubling   */
+                                 /* levels of >= 128 rows (single-instance,   */
+                                 /* sharded and batched plans: one grouped    */
+                                 /* round per level across the instances);    */
+                                 /* ignored elsewhere                         */
 #define QPE_FLAG_CHECK_UNITARY 0x40u /* the POWERS stage first forms U^dagger */
                                      /* U in FP64; if any entry of            */
                                      /* U^dagger U - I exceeds 1e-8 in        */
